@@ -1,0 +1,451 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+Each test ties the oracle to something other than itself: a hand-derived worked
+example (Fig. 4 caption), the paper's index-propagation example (Sec. V-B), brute
+force with exact rationals, closed forms of the stream size, the error bound of
+Eq. 1 checked exactly on every value, and special cases whose answer is known
+without running the codec (lossless at a tiny bound, all-constant at a huge one).
+Runs on the CPU only.
+"""
+import math
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import oracle
+import szx_stream as ss
+from exact import exact_abs_diff_le, within_exact_scalar
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def read_golden(name):
+    out = {}
+    for line in open(os.path.join(GOLDEN, name)):
+        line = line.strip()
+        if not line or line.startswith("#"):
+            continue
+        k, v = line.split("=", 1)
+        out[k.strip()] = v.strip()
+    return out
+
+
+def hexwords_f32(s):
+    return np.array([int(h, 16) for h in s.split()], dtype=np.uint32).view(np.float32)
+
+
+def hexbytes(s):
+    return bytes.fromhex(s.replace(" ", ""))
+
+
+# ---------------------------------------------------------------------------
+# worked example (Fig. 4 caption, Sec. IV)
+
+
+def test_worked_example_fig4_stream_bytes():
+    g = read_golden("worked_example_fig4.txt")
+    x = hexwords_f32(g["values_f32_hex"])
+    s = oracle.compress(x, float(g["eb"]), int(g["block"]))
+    assert s.tobytes() == hexbytes(g["stream_hex"])
+    st = ss.parse(s)
+    b = st.blocks[0]
+    assert st.e_bits == int(g["e_bits"], 16)
+    assert b.mu_bits == int(g["mu_bits"], 16)
+    assert b.req == int(g["req"])
+    assert b.L[:4] == [0, 2, 1, 0]
+    y = oracle.decompress(s)
+    assert np.array_equal(y.view(np.uint32), hexwords_f32(g["decoded_f32_hex"]).view(np.uint32))
+
+
+# ---------------------------------------------------------------------------
+# index propagation (Sec. V-B, Fig. idx-prop): with 3 required bytes, a byte
+# that is "leading" (identical to the previous value's) must be read from the
+# nearest earlier value that stored it as a mid-byte: B33 and B34 read B32.
+
+
+def _f32(sign, mant):
+    return np.array([(sign << 31) | (127 << 23) | mant], dtype=np.uint32).view(np.float32)[0]
+
+
+def _index_block():
+    """Ten f32 values whose first eight have leading-byte codes 0,1,3,3,0,1,2,2.
+
+    Values lie in [1, 2) in magnitude; the last two are -max and +max so that
+    mu = 0 exactly and v = d.  With r = 1.999 (p(r) = 0) and e = 2^-12:
+    R = 12, reqBits = 21, s = 3, q = 3, and t = (bits >> 3) & 0xFFFFFF00 has
+    byte 0 = 0x07 (positive) or 0x17 (negative), byte 1 = 0xF0 | the top four
+    mantissa bits, byte 2 = the next eight.
+    """
+    def m(b1, b2, low):
+        return (b1 << 19) | (b2 << 11) | low
+    vals = [_f32(0, m(1, 0x10, 5)),   # L = 0 (t_{-1} = 0)
+            _f32(0, m(2, 0x10, 1)),   # byte 1 differs: L = 1
+            _f32(0, m(2, 0x10, 99)),  # same kept bytes: L = 3
+            _f32(0, m(2, 0x10, 7)),   # L = 3
+            _f32(1, m(3, 0x20, 0)),   # sign flips byte 0: L = 0
+            _f32(1, m(4, 0x20, 0)),   # L = 1
+            _f32(1, m(4, 0x30, 0)),   # byte 2 differs: L = 2
+            _f32(1, m(4, 0x40, 0)),   # L = 2
+            np.float32(-1.9990234375), np.float32(1.9990234375)]
+    return np.array(vals, dtype=np.float32)
+
+
+def test_index_propagation_example():
+    # 8 values, 3 required bytes; values 3 and 4 (1-based) repeat all three
+    # bytes, values 7 and 8 repeat the first two bytes.
+    L_target = [0, 1, 3, 3, 0, 1, 2, 2]
+    s = oracle.compress(_index_block(), 2.0 ** -12, 32)
+    st = ss.parse(s)
+    b = st.blocks[0]
+    assert b.mu_bits == 0 and b.req == 21
+    assert b.L[:8] == L_target
+    # index propagation as the paper states it: every byte starts with the
+    # index of the value that owns it as a mid-byte, or 0 for a leading byte,
+    # and a max-scan with strides 1, 2, 4 spreads the owners forward.
+    q = 3
+    src = [[i if b.L[i] <= j else -1 for j in range(q)] for i in range(8)]
+    for stride in (1, 2, 4):
+        src = [[max(src[i][j], src[i - stride][j]) if i >= stride else src[i][j]
+                for j in range(q)] for i in range(8)]
+    # B33 and B34 (byte 3 of values 3 and 4, 1-based) read from value 2
+    assert src[2][2] == 1 and src[3][2] == 1
+    # B27 and B28 read from value 6
+    assert src[6][1] == 5 and src[7][1] == 5
+    # the oracle's decode equals the propagated reads
+    y = oracle.decompress(s)
+    own = {}
+    for i in range(8):
+        for j in range(q):
+            if b.L[i] <= j:
+                own[(i, j)] = (b.t[i] >> (24 - 8 * j)) & 0xFF
+    for i in range(8):
+        word = 0
+        for j in range(q):
+            word |= own[(src[i][j], j)] << (24 - 8 * j)
+        expect = np.array([(word << 3) & 0xFFFFFFFF], dtype=np.uint32).view(np.float32)[0]
+        assert y[i] == expect
+
+
+# ---------------------------------------------------------------------------
+# constant-block test (Alg. 1) against exact rational brute force
+
+
+@pytest.mark.parametrize("dtype", [np.float32, np.float64])
+def test_constant_detection_bruteforce(dtype):
+    rng = np.random.default_rng(11)
+    w = 4 if dtype == np.float32 else 8
+    ftype = np.float32 if dtype == np.float32 else np.float64
+    checked = 0
+    for trial in range(400):
+        n = int(rng.integers(1, 9))
+        base = ftype(rng.normal() * 10.0 ** rng.integers(-3, 4))
+        span = ftype(abs(rng.normal()) * 10.0 ** rng.integers(-6, 1))
+        x = (base + span * rng.uniform(-1, 1, size=n)).astype(dtype)
+        # choose e on the boundary: |mx - mu| rounded down, up, or exactly
+        s0 = oracle.compress(x, 1e300 if dtype == np.float64 else 3e38, 32)
+        mu = ss.bits_to_float(ss.parse(s0).blocks[0].mu_bits, w)
+        dev = max(abs(Fraction(float(v)) - Fraction(mu)) for v in x.tolist())
+        for e in {float(ftype(float(dev))), float(np.nextafter(ftype(float(dev)), ftype(0))),
+                  float(np.nextafter(ftype(float(dev)), ftype(np.inf)))}:
+            if not (e > 0) or not math.isfinite(e):
+                continue
+            s = oracle.compress(x, e, 32)
+            st = ss.parse(s)
+            ee = ss.bits_to_float(st.e_bits, w)
+            b = st.blocks[0]
+            mu_b = ss.bits_to_float(b.mu_bits, w)
+            is_const = b.state == 0
+            truth = all(abs(Fraction(float(v)) - Fraction(mu_b)) <= Fraction(ee) for v in x.tolist())
+            if b.state == 1 and b.req != 0xFF:
+                # mu of a non-constant block is the same midpoint
+                assert mu_b == mu
+            assert is_const == truth, (x, e, mu_b)
+            checked += 1
+    assert checked > 600
+
+
+def test_minmax_total_order_signed_zero():
+    # -0 < +0 in the block statistics (reading R2): {+0, -0} has mn = -0,
+    # mx = +0, r = +0, mu = -0 + +0 = +0 under round-to-nearest.
+    x = np.array([0.0, -0.0, 0.0, -0.0], dtype=np.float32)
+    st = ss.parse(oracle.compress(x, 1e-3, 32))
+    assert st.blocks[0].state == 0
+    assert st.blocks[0].mu_bits == 0x00000000
+    # {-0, -0}: r = RN(-0 - -0) * 0.5 = +0 and mu = -0 + +0 = +0 as well; the
+    # decoded +0 is within any e of -0.
+    x = np.array([-0.0, -0.0], dtype=np.float32)
+    st = ss.parse(oracle.compress(x, 1e-3, 32))
+    assert st.blocks[0].mu_bits == 0x00000000
+
+
+# ---------------------------------------------------------------------------
+# Eq. 1: |d - d'| <= e on every value, checked exactly
+
+
+def _fields(dtype, n, rng):
+    t = np.linspace(0, 40 * np.pi, n)
+    yield "smooth", (np.sin(t) + 0.01 * rng.normal(size=n)).astype(dtype)
+    yield "walk", np.cumsum(rng.normal(size=n)).astype(dtype)
+    yield "spiky", (rng.standard_cauchy(size=n)).astype(dtype)
+    yield "tiny", (rng.normal(size=n) * 1e-38).astype(dtype)
+    yield "huge", (rng.normal(size=n) * (1e37 if dtype == np.float32 else 1e300)).astype(dtype)
+    yield "steps", np.repeat(rng.normal(size=n // 64 + 1), 64)[:n].astype(dtype)
+    yield "signs", (rng.choice([-1.0, 1.0], size=n) * rng.uniform(0.5, 1, size=n)).astype(dtype)
+    yield "zeros", np.where(rng.random(n) < 0.5, 0.0, -0.0).astype(dtype)
+
+
+@pytest.mark.parametrize("dtype", [np.float32, np.float64])
+@pytest.mark.parametrize("block", [32, 128, 256])
+def test_error_bound_every_value(dtype, block):
+    rng = np.random.default_rng(block)
+    n = 5000 + block // 3  # ragged tail
+    for name, x in _fields(dtype, n, rng):
+        rng_e = float(np.max(x) - np.min(x)) if np.all(np.isfinite(x)) else 1.0
+        for rel in (1e-1, 1e-3, 1e-6):
+            eb = rel * rng_e if rng_e > 0 else 1e-3
+            if not (eb > 0) or not math.isfinite(eb):
+                eb = 1e-3
+            s = oracle.compress(x, eb, block)
+            y = oracle.decompress(s)
+            e = oracle.error_bound(eb, oracle.F32 if dtype == np.float32 else oracle.F64)
+            ok = exact_abs_diff_le(x, y, e)
+            assert ok.all(), (name, rel, np.flatnonzero(~ok)[:5])
+
+
+@pytest.mark.parametrize("dtype", [np.float32, np.float64])
+def test_error_bound_power_of_two_bounds(dtype):
+    # e exactly a power of two is the tightest case for Eq. 3: the chop error
+    # can approach 2^p(e) = e, so rounding in v = d - mu and d' = v' + mu
+    # decides; the per-value check (reading R7) must keep every value within e.
+    rng = np.random.default_rng(3)
+    x = (np.cumsum(rng.normal(size=20000)) * 0.37).astype(dtype)
+    for p in (-20, -10, -4, 0, 3):
+        e = 2.0 ** p
+        s = oracle.compress(x, e, 128)
+        y = oracle.decompress(s)
+        assert exact_abs_diff_le(x, y, e).all()
+
+
+# ---------------------------------------------------------------------------
+# special cases with known answers
+
+
+@pytest.mark.parametrize("dtype", [np.float32, np.float64])
+def test_nonfinite_blocks_roundtrip_bit_exact(dtype):
+    rng = np.random.default_rng(5)
+    x = rng.normal(size=1000).astype(dtype)
+    x[[3, 200, 777]] = [np.nan, np.inf, -np.inf]
+    s = oracle.compress(x, 1e-2, 128)
+    st = ss.parse(s)
+    raw_blocks = {b.k for b in st.blocks if b.req == 0xFF}
+    assert raw_blocks == {0, 1, 6}
+    y = oracle.decompress(s)
+    uint = np.uint32 if dtype == np.float32 else np.uint64
+    for k in raw_blocks:
+        sl = slice(k * 128, min(1000, k * 128 + 128))
+        assert np.array_equal(y[sl].view(uint), x[sl].view(uint))
+
+
+@pytest.mark.parametrize("dtype", [np.float32, np.float64])
+def test_smallest_subnormal_bound_is_lossless(dtype):
+    rng = np.random.default_rng(9)
+    x = (rng.normal(size=3000) * 100).astype(dtype)
+    x[np.abs(x) < 1e-30] = 1.0
+    tiny = float(np.finfo(dtype).smallest_subnormal)
+    s = oracle.compress(x, tiny, 128)
+    y = oracle.decompress(s)
+    uint = np.uint32 if dtype == np.float32 else np.uint64
+    assert np.array_equal(y.view(uint), x.view(uint))
+
+
+@pytest.mark.parametrize("dtype,block", [(np.float32, 128), (np.float64, 128), (np.float64, 256), (np.float32, 32)])
+def test_huge_bound_all_constant_closed_form(dtype, block):
+    # e >= the whole range: every block is constant; the stream is the header,
+    # the state bitmap, the mu array and the tile index, nothing else.
+    rng = np.random.default_rng(1)
+    n = 1 << 16
+    x = rng.uniform(-1, 1, size=n).astype(dtype)
+    s = oracle.compress(x, 2.5, block)
+    w = np.dtype(dtype).itemsize
+    nb = n // block
+    G = max(8, 32768 // (block * w))
+    ntiles = -(-nb // G)
+    pad16 = ss.pad16
+    assert len(s) == 64 + pad16(-(-nb // 8)) + pad16(nb * w) + pad16(8 * (ntiles + 1))
+    st = ss.parse(s)
+    assert st.nn == 0 and st.nraw == 0
+    y = oracle.decompress(s)
+    # each block decodes to its midpoint (min + max) / 2, to within half an ulp
+    for k in range(0, nb, 97):
+        blk = x[k * block:(k + 1) * block].astype(np.float64)
+        mid = (blk.min() + blk.max()) / 2
+        assert np.all(y[k * block:(k + 1) * block] == y[k * block])
+        assert abs(float(y[k * block]) - mid) <= np.spacing(dtype(abs(mid)) + dtype(blk.max() - blk.min()))
+
+
+def test_all_constant_compression_ratio_f32_b128():
+    # One constant f32 block of 128 values costs its 4-byte mu and one state
+    # bit; the tile index adds 8 bytes per tile of G = 64 blocks.  So the ratio
+    # tends to 512 / (4 + 1/8 + 8/64) = 120.47 -- the same order as the
+    # paper's maximum field ratio of 124 (Table 3), whose format has no index.
+    n = 128 * 64 * 4096
+    x = np.zeros(n, dtype=np.float32)
+    s = oracle.compress(x, 1e-3, 128)
+    cr = x.nbytes / len(s)
+    assert abs(cr - 512 / (4 + 1 / 8 + 8 / 64)) < 0.01
+    assert 512 / (4 + 1 / 8) == pytest.approx(124.12, abs=0.01)
+
+
+# ---------------------------------------------------------------------------
+# what each stored field means (independent reader, tests/szx_stream.py)
+
+
+def _p(x, w):
+    bits = ss.float_bits(x, w)
+    E, bias, M = (8, 127, 23) if w == 4 else (11, 1023, 52)
+    return ((bits >> M) & ((1 << E) - 1)) - bias
+
+
+def _semantics_case(name, dtype):
+    rng = np.random.default_rng(21)
+    x = np.cumsum(rng.normal(size=3 * 4096 + 77))
+    if name == "walk":
+        x = x.astype(dtype)
+        x[4000:4200] = 5.0  # constant stretch
+        return x, 1e-3 * float(x.max() - x.min())
+    # subnormal bound: p(e) of Eq. 3 is the exponent field's minimum, which
+    # overstates e, so the per-value check must escalate reqBits (reading R7)
+    if dtype == np.float32:
+        return (x * 1e-36).astype(dtype), 1e-42
+    return (x * 1e-305).astype(dtype), 1e-318
+
+
+@pytest.mark.parametrize("case", ["walk", "subnormal_e"])
+@pytest.mark.parametrize("dtype", [np.float32, np.float64])
+def test_stream_semantics(dtype, case):
+    w = np.dtype(dtype).itemsize
+    W, E, M = (32, 8, 23) if w == 4 else (64, 11, 52)
+    x, eb = _semantics_case(case, dtype)
+    s = oracle.compress(x, eb, 128)
+    st = ss.parse(s)
+    e = ss.bits_to_float(st.e_bits, w)
+    y = oracle.decompress(s)
+    nn = nraw = nesc = 0
+    mid_total = 0
+    for b in st.blocks:
+        seg = x[b.k * 128: b.k * 128 + b.length]
+        if b.state == 0:
+            assert np.all(y[b.k * 128: b.k * 128 + b.length] == ss.bits_to_float(b.mu_bits, w))
+            continue
+        nn += 1
+        if b.req == 0xFF:
+            nraw += 1
+            continue
+        mu = ss.bits_to_float(b.mu_bits, w)
+        mn, mx = float(seg.min()), float(seg.max())
+        r = float(dtype(dtype(mx) - dtype(mn)) * dtype(0.5))
+        # Eq. 3 (reading R5): reqBits = 1 + E + clamp(p(r) - p(e), 0, M), possibly
+        # escalated (reading R7)
+        req0 = 1 + E + min(max(_p(r, w) - _p(e, w), 0), M)
+        assert b.req >= req0
+        if b.req > req0:
+            nesc += 1
+        sft = (8 - b.req % 8) % 8
+        q = (b.req + sft) // 8
+        assert (b.req + sft) % 8 == 0  # Eq. 4: kept bits fill whole bytes
+        # the truncated words keep exactly the top reqBits bits of v = d - mu
+        v_bits = [ss.float_bits(dtype(dtype(d) - dtype(mu)), w) for d in seg.tolist()]
+        keep = ((1 << W) - 1) ^ ((1 << (W - b.req)) - 1)
+        for i, vb in enumerate(v_bits):
+            assert (b.t[i] << sft) & ((1 << W) - 1) == vb & keep
+        # L_i: identical leading bytes against the previous truncated word
+        prev = 0
+        for i, t in enumerate(b.t):
+            x_or = t ^ prev
+            lz = 0
+            while lz < w and (x_or >> (W - 8 - 8 * lz)) & 0xFF == 0:
+                lz += 1
+            assert b.L[i] == min(lz, 3, q)
+            prev = t
+        assert all(c == 0 for c in b.L[b.length:])
+        assert b.mid_bytes == sum(q - l for l in b.L[: b.length])
+        mid_total += b.mid_bytes
+        # minimality of escalation: one bit fewer fails for some value
+        if b.req > req0:
+            rq = b.req - 1
+            sft2 = (8 - rq % 8) % 8
+            keep2 = ((1 << W) - 1) ^ ((1 << (W - rq)) - 1)
+            fails = 0
+            for d, vb in zip(seg.tolist(), v_bits):
+                vp = ss.bits_to_float(vb & keep2, w)
+                dp = float(dtype(dtype(vp) + dtype(mu)))
+                fails += not within_exact_scalar(d, dp, e)
+            assert fails > 0
+    assert (nn, nraw, nesc) == (st.nn, st.nraw, st.nesc)
+    if case == "subnormal_e":
+        assert nesc > 0
+    assert exact_abs_diff_le(x, y, e).all()
+    # byte-count formula: header + padded sections + per-tile records
+    rec = 0
+    for tile in range(st.ntiles):
+        blocks = st.blocks[tile * st.G:(tile + 1) * st.G]
+        nn_t = sum(b.state for b in blocks)
+        rec += ss.pad16(nn_t * (128 // 4 + 1) + sum(b.mid_bytes for b in blocks if b.state))
+    assert st.total == st.off_rec + rec == len(s)
+
+
+def test_error_bound_conversion_f32_rounds_toward_zero():
+    for eb in (1e-3, 0.1, 1.0 / 3, 1e-40, 3.4e38, 7.0):
+        e = oracle.error_bound(eb, oracle.F32)
+        assert e <= eb
+        assert float(np.nextafter(np.float32(e), np.float32(np.inf))) > eb or e == eb
+    assert oracle.error_bound(1e-3, oracle.F64) == 1e-3
+
+
+# ---------------------------------------------------------------------------
+# robustness: malformed streams are rejected, never read out of bounds
+
+
+def test_corrupt_streams_rejected():
+    rng = np.random.default_rng(2)
+    x = np.cumsum(rng.normal(size=20000)).astype(np.float32)
+    s = oracle.compress(x, 1e-2, 128)
+    assert oracle.decompress_status(s) == oracle.OK
+    assert oracle.decompress_status(s[:40]) == oracle.ERR_CORRUPT
+    assert oracle.decompress_status(s[:-16]) == oracle.ERR_CORRUPT
+    bad = s.copy()
+    bad[0] ^= 1
+    assert oracle.decompress_status(bad) == oracle.ERR_CORRUPT
+    # flipped bytes anywhere: either detected or decoded, never a crash
+    for _ in range(200):
+        bad = s.copy()
+        bad[int(rng.integers(64, len(s)))] ^= np.uint8(1 << int(rng.integers(0, 8)))
+        assert oracle.decompress_status(bad) in (oracle.OK, oracle.ERR_CORRUPT)
+
+
+def test_invalid_arguments():
+    x = np.ones(10, dtype=np.float32)
+    for eb in (0.0, -1.0, float("nan"), float("inf")):
+        with pytest.raises(oracle.OracleError):
+            oracle.compress(x, eb)
+    for block in (0, 16, 48, 2048):
+        with pytest.raises(oracle.OracleError):
+            oracle.compress(x, 1e-3, block)
+
+
+def test_shift_overhead_eq5_is_small_on_smooth_data():
+    # Sec. V-A.1: the right shift of Eq. 4 costs some space (the paper reports
+    # < 12% of the compressed size on its ~100 real fields).  On this synthetic
+    # field it must at least stay positive and well below the at most 7 extra
+    # bits a value can carry.
+    rng = np.random.default_rng(4)
+    t = np.linspace(0, 60, 1 << 18)
+    x = (np.sin(t) + np.sin(3.1 * t) * 0.3 + 0.001 * rng.normal(size=t.size)).astype(np.float32)
+    for rel in (1e-3, 1e-4):
+        eb = rel * float(x.max() - x.min())
+        c, ab = oracle.shift_overhead_bits(x, eb)
+        size = len(oracle.compress(x, eb))
+        overhead = (c - ab) / 8 / size
+        assert 0.0 < overhead < 0.4
