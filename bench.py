@@ -1,0 +1,359 @@
+#!/usr/bin/env python3
+"""Benchmark of the B300 SZx codec (one JSON line on rank 0).
+
+Workload: the 512^3 f32 Gaussian random field (power spectrum |k|^-5/3, 25% of
+the volume zeroed in four 32-plane z-slabs), value-range relative bound 1e-3,
+block 128.  One step = compress the field and decompress the stream (every
+step of the hot path), with inputs resident in HBM; the field (512 MiB) is
+larger than L2, so no flush is needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+`value` is whole-job throughput in GB/s of input bytes (Eq. 2-3 of the paper:
+N * b / T) per round trip; compress and decompress rates are reported beside
+it.  The reference arm times the CPU oracle on a bounded slice of the same
+field on the host cores.  With N > 1 (torchrun) every rank codes its own field
+(independent problems: weak scaling, no collective on the data path).
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "SZx compress/decompress GB/s and % HBM peak at rel-eb 1e-3; ratio; p99 ms"
+SHAPE = (512, 512, 512)
+SHAPE_RUN = list(SHAPE)  # --size changes the cube edge (profiling captures)
+REL = 1e-3
+BLOCK = 128
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6400.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            time.sleep(0.2)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, flag in zip(names, parts[5:9]):
+                if flag.lower() in ("active", "1", "yes"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def cpu_model():
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return "unknown"
+
+
+def time_oracle(x_host, eb, max_seconds=12.0):
+    """The oracle (as it stands, one thread) on a bounded slice of the field."""
+    import numpy as np
+
+    import oracle
+    plane = x_host.size // SHAPE_RUN[0]
+    slab = 32 * plane  # 32 z-planes
+    best = None
+    used = 0
+    t_c = t_d = 0.0
+    start = time.perf_counter()
+    for z0 in range(0, x_host.size, slab):
+        part = np.ascontiguousarray(x_host[z0:z0 + slab])
+        t0 = time.perf_counter()
+        s = oracle.compress(part, eb, BLOCK)
+        t1 = time.perf_counter()
+        oracle.decompress(s)
+        t2 = time.perf_counter()
+        t_c += t1 - t0
+        t_d += t2 - t1
+        used += part.nbytes
+        if time.perf_counter() - start > max_seconds:
+            break
+    best = used / 1e9 / (t_c + t_d)
+    return {"value": best, "unit": "GB/s", "cores": 1, "kind": "oracle",
+            "sample": f"{used >> 20} MiB of the field ({used // (plane * 4)} z-planes), one thread, "
+                      f"compress {used / 1e6 / t_c:.0f} MB/s, decompress {used / 1e6 / t_d:.0f} MB/s",
+            "cpu": cpu_model(), "seconds": t_c + t_d}
+
+
+def make_field(device, seed):
+    from paper_2201_13020_b300 import inputs
+    g = inputs.grf_3d(tuple(SHAPE_RUN), -5.0 / 3.0, seed=seed, device=device)
+    g = inputs.zero_slabs(g, 0.25, 32, seed=seed)
+    return g.reshape(-1).contiguous()
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return 0
+    import torch
+    x = make_field("cuda" if torch.cuda.is_available() else "cpu", seed=2)
+    from paper_2201_13020_b300 import inputs
+    eb = inputs.rel_to_abs(x, REL)
+    xh = x.cpu().numpy()
+    del x
+    per_step = []
+    samples = []
+    for i in range(args.warmup + args.steps):
+        r = time_oracle(xh, eb, max_seconds=args.ref_seconds)
+        if i >= args.warmup:
+            per_step.append(r)
+            samples.append(r["value"])
+    v = statistics.median(samples)
+    last = per_step[-1]
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "GB/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * last["seconds"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic", "config": config_block(world),
+            "cpu_baseline": {"value": v, "unit": "GB/s", "cores": 1, "kind": "oracle", "sample": last["sample"]},
+            "e2e": {"value": v, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def config_block(world):
+    edge = SHAPE_RUN[0]
+    return {"workload": f"grf{edge}_f32_k-5/3_zero-slabs25_rel1e-3_block128", "shape": list(SHAPE_RUN),
+            "dtype": "f32", "block": BLOCK, "rel_eb": REL, "spectrum": "k^-5/3", "zero_slabs": 0.25,
+            "l2": "no flush: the 512 MiB field and its stream exceed the 126 MB L2",
+            "parallelism": f"replicas{world}"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--ref-seconds", type=float, default=10.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--size", type=int, default=512, help="cube edge (default 512; smaller only for captures)")
+    args = ap.parse_args()
+    SHAPE_RUN[:] = [args.size] * 3
+    args.warmup = max(args.warmup, 3)
+
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        return run_reference(args, world, rank)
+
+    import numpy as np
+    import torch
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    import paper_2201_13020_b300 as szx
+    from paper_2201_13020_b300 import inputs
+
+    x = make_field("cuda", seed=2 + rank)
+    n = x.numel()
+    eb = inputs.rel_to_abs(x, REL)
+    cap = szx.compress_bound(n, szx.SZX_F32, BLOCK)
+    out = torch.empty(cap, dtype=torch.uint8, device="cuda")
+    res = torch.zeros(2, dtype=torch.int64, device="cuda")
+    y = torch.empty_like(x)
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    # one synchronous round trip gives the header (the stream layout is
+    # deterministic, so every later step writes the same bytes)
+    s0 = szx.compress(x, eb, BLOCK, out=out)
+    nbytes = s0.numel()
+    h = szx.header(out[:nbytes])
+    cr = n * 4 / nbytes
+
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+
+    def step(events=None):
+        if events:
+            events[0].record(stream)
+        szx.compress_async(x, eb, BLOCK, out, res)
+        if events:
+            events[1].record(stream)
+        szx.decompress_async(out[:nbytes], h, y, status)
+        if events:
+            events[2].record(stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clocks:
+        torch.cuda.profiler.start()
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for i in range(args.steps):
+            step(ev[i])
+        t1.record(stream)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
+    if world > 1:
+        torch.distributed.barrier()
+    total_ms = t0.elapsed_time(t1)
+    comp_ms = [e[0].elapsed_time(e[1]) for e in ev]
+    deco_ms = [e[1].elapsed_time(e[2]) for e in ev]
+    step_ms = [c + d for c, d in zip(comp_ms, deco_ms)]
+    r = res.cpu().tolist()
+    if r[1] != 0 or int(status.item()) != 0 or r[0] != nbytes:
+        raise RuntimeError(f"device status: compress {r}, decompress {int(status.item())}")
+    if world > 1:
+        t = torch.tensor([total_ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+
+    in_bytes = n * 4
+    value = world * in_bytes * args.steps / (total_ms * 1e-3) / 1e9
+    comp_gbs = in_bytes / (statistics.median(comp_ms) * 1e-3) / 1e9
+    deco_gbs = in_bytes / (statistics.median(deco_ms) * 1e-3) / 1e9
+    alg_bytes = in_bytes + nbytes  # read the field + write the stream (and the reverse)
+    peak, peak_kind = peaks()
+    comp_alg = alg_bytes / (statistics.mean(comp_ms) * 1e-3) / 1e9
+    deco_alg = alg_bytes / (statistics.mean(deco_ms) * 1e-3) / 1e9
+    dominant = "compress_kernel" if statistics.mean(comp_ms) >= statistics.mean(deco_ms) else "decompress_kernel"
+    achieved = comp_alg if dominant == "compress_kernel" else deco_alg
+    # ncu DRAM traffic per launch of the dominant kernel, if a capture of the
+    # current build is recorded
+    traffic = None
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            tj = json.load(f)
+        traffic = tj.get(dominant)
+    except Exception:
+        pass
+
+    # end to end through the C ABI with host buffers (pinned): H2D, compress,
+    # decompress, D2H, every step
+    e2e = None
+    if args.e2e_steps > 0:
+        xh = torch.empty(n, dtype=torch.float32, pin_memory=True)
+        xh.copy_(x)
+        yh = torch.empty(n, dtype=torch.float32, pin_memory=True)
+        xd = torch.empty_like(x)
+        times = []
+        for i in range(args.e2e_steps + 1):
+            torch.cuda.synchronize()
+            a = time.perf_counter()
+            xd.copy_(xh, non_blocking=True)
+            s = szx.compress(xd, eb, BLOCK, out=out)
+            yd = szx.decompress(s, out=y)
+            yh.copy_(yd, non_blocking=True)
+            torch.cuda.synchronize()
+            if i:
+                times.append(time.perf_counter() - a)
+        e2e = {"value": in_bytes / statistics.median(times) / 1e9, "unit": "GB/s",
+               "h2d_bytes_per_step": in_bytes, "d2h_bytes_per_step": in_bytes + 16}
+        ok = torch.equal(yh, y.cpu())
+        if not ok:
+            raise RuntimeError("e2e decode differs from the device-resident decode")
+
+    cpu_base = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu_base = time_oracle(x.cpu().numpy(), eb, max_seconds=args.ref_seconds)
+        cpu_base.pop("seconds", None)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": config_block(world),
+            "compress_gbs": comp_gbs, "decompress_gbs": deco_gbs, "cr": cr,
+            "compress_ms_median": statistics.median(comp_ms), "decompress_ms_median": statistics.median(deco_ms),
+            "p50_ms": statistics.median(step_ms),
+            "p99_ms": float(np.percentile(step_ms, 99)),
+            "hbm_frac_input": {"compress": comp_gbs / peak, "decompress": deco_gbs / peak},
+            "hbm_frac_algorithmic": {"compress": comp_alg / peak, "decompress": deco_alg / peak},
+            "roofline": {"kernel": dominant, "bound": "hbm", "achieved": achieved, "peak": peak,
+                         "peak_kind": f"hbm_gbs of {peak_kind}", "unit": "GB/s", "frac": achieved / peak,
+                         "traffic": traffic, "algorithmic_bytes_per_launch": alg_bytes},
+            "cpu_baseline": cpu_base, "e2e": e2e, "clocks": clocks.summary(),
+            "gpu_launches": 2 * args.steps,
+            "stream": {"bytes": nbytes, "nonconst": h.nonconst, "raw": h.raw, "escalated": h.escalated,
+                       "blocks": -(-n // BLOCK)},
+            "gpu": torch.cuda.get_device_name(local),
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,160 @@
+/*
+ * szx.h -- C ABI of the B300 (sm_103a) SZx block compressor / decompressor.
+ *
+ * The codec is the ultra-fast error-bounded lossy compressor of Yu et al.,
+ * "SZx: an Ultra-fast Error-bounded Lossy Compressor for Scientific Datasets"
+ * (arXiv 2201.13020).  The problem it solves is stated in Sec. III, Eq. 1:
+ * given N values d_i and an absolute error bound e, produce a byte stream whose
+ * decompression d'_i satisfies |d_i - d'_i| <= e for every i, as fast as
+ * possible (compression and decompression throughput, Eq. 2 and Eq. 3, count
+ * input bytes N * b per second).
+ *
+ * Method (Sec. IV, Algorithm 1): the array is cut into consecutive blocks of
+ * `block` values (128 by default, Sec. V-A.2).  A block whose values all lie
+ * within e of mu, the mean of its min and max, is "constant" and stores only
+ * mu.  Other blocks are normalised by mu, each value keeps the bits Eq. 3
+ * requires, right-shifted by Eq. 4 so they fill whole bytes, and only the bytes
+ * that differ from the previous value ("mid-bytes") are stored, with a 2-bit
+ * code per value counting the identical leading bytes.
+ *
+ * Conventions for every call below:
+ *   - Pointers named d_* are CUDA device pointers on the current device and
+ *     must be 16-byte aligned; the caller allocates and owns all of them.
+ *     Nothing in this library allocates device memory in the compress or
+ *     decompress calls; their scratch space is the tail of the caller's
+ *     output buffer (see szx_compress_bound).
+ *   - `stream` is a cudaStream_t (0 = the legacy default stream).  All device
+ *     work is enqueued on it in order.
+ *   - Values are IEEE 754 binary32 (SZX_F32) or binary64 (SZX_F64), little
+ *     endian, contiguous.
+ *   - `block` is the block length b: a power of two in [32, 1024].
+ *   - `eb` is the absolute error bound: finite and > 0.  For SZX_F32 the bound
+ *     used is the largest float <= eb.  (A value-range relative bound REL of
+ *     the paper, Sec. IV footnote, is REL * (max - min), computed by the caller.)
+ *   - Every call returns a szx_status and never aborts the process.  On an
+ *     error the contents of the output buffer are unspecified.
+ *   - The compressed stream is deterministic: the same input, dtype, eb and
+ *     block give the same bytes on every run and every launch configuration.
+ */
+#ifndef SZX_H
+#define SZX_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum { SZX_F32 = 0, SZX_F64 = 1 } szx_dtype;
+
+typedef enum {
+    SZX_OK = 0,
+    SZX_ERR_INVALID = 1,     /* bad argument (null, misaligned, eb, block, n) */
+    SZX_ERR_TOO_SMALL = 2,   /* output capacity below what the call needs */
+    SZX_ERR_CORRUPT = 3,     /* compressed input is malformed or truncated */
+    SZX_ERR_NOMEM = 4,       /* a planning call could not allocate host memory */
+    SZX_ERR_CUDA = 5,        /* a CUDA runtime call failed */
+    SZX_ERR_TIMEOUT = 6      /* a bounded device-side wait ran out */
+} szx_status;
+
+/* Opaque CUDA stream handle (binary-compatible with cudaStream_t). */
+typedef struct CUstream_st *szx_stream_t;
+
+/* Parsed 64-byte stream header. */
+typedef struct {
+    uint32_t block;        /* b */
+    uint32_t tile_blocks;  /* G: blocks per tile record */
+    uint64_t n;            /* number of values */
+    szx_dtype dtype;
+    uint64_t e_bits;       /* bit pattern of the bound used (f32 in the low 32 bits) */
+    uint64_t nonconst;     /* non-constant blocks, raw ones included */
+    uint64_t raw;          /* blocks stored verbatim */
+    uint64_t escalated;    /* blocks whose reqBits grew past Eq. 3 to meet e */
+    uint64_t total_bytes;  /* stream size */
+} szx_header;
+
+/*
+ * Bytes the output buffer of szx_compress / szx_compress_async must hold for n
+ * values: the largest possible stream (every block stored verbatim plus the
+ * per-block metadata) followed by the call's device scratch space (tile
+ * tickets and the look-back status words of the offset scan).  Returns 0 for
+ * invalid arguments.  Host-only; no CUDA call.
+ */
+size_t szx_compress_bound(size_t n, szx_dtype dtype, uint32_t block);
+
+/* Largest possible stream size alone (no scratch tail).  Host-only. */
+size_t szx_stream_max_bytes(size_t n, szx_dtype dtype, uint32_t block);
+
+/*
+ * Compress n values at d_in into the stream at d_out (Algorithm 1 with the
+ * Eq. 3 / Eq. 4 byte-aligned packing; Sec. V-B for the GPU design it
+ * replaces).  out_capacity must be >= szx_compress_bound(n, dtype, block).
+ * On SZX_OK, *out_bytes holds the stream size; the stream occupies
+ * d_out[0 .. *out_bytes), and the bytes after it up to out_capacity are
+ * scratch that the call overwrote.  Synchronous: returns after the stream
+ * and its size are complete (one small device-to-host copy and a stream
+ * synchronisation).  Errors: SZX_ERR_INVALID, SZX_ERR_TOO_SMALL, SZX_ERR_CUDA,
+ * SZX_ERR_TIMEOUT.
+ */
+szx_status szx_compress(const void *d_in, size_t n, szx_dtype dtype, double eb,
+                        uint32_t block, void *d_out, size_t out_capacity,
+                        size_t *out_bytes, szx_stream_t stream);
+
+/*
+ * Asynchronous form of szx_compress: enqueues the work and returns without
+ * synchronising.  When the work completes, d_result[0] holds the stream size
+ * and d_result[1] a szx_status (SZX_OK or SZX_ERR_TIMEOUT); d_result is a
+ * device (or mapped pinned) pointer to two uint64_t, or NULL.  The stream size
+ * is also in the stream header (bytes 56..63).  Safe to capture in a CUDA
+ * graph.  Host-side argument errors are returned immediately.
+ */
+szx_status szx_compress_async(const void *d_in, size_t n, szx_dtype dtype,
+                              double eb, uint32_t block, void *d_out,
+                              size_t out_capacity, uint64_t *d_result,
+                              szx_stream_t stream);
+
+/*
+ * Read and check the 64-byte header of the stream at d_in (device pointer;
+ * one 64-byte device-to-host copy, synchronous on `stream`).  Errors:
+ * SZX_ERR_INVALID (null), SZX_ERR_CORRUPT (bad magic, version, dtype, block,
+ * tile size, or total_bytes > in_bytes), SZX_ERR_CUDA.
+ */
+szx_status szx_header_read(const void *d_in, size_t in_bytes, szx_header *h,
+                           szx_stream_t stream);
+
+/*
+ * Decompress the stream d_in[0 .. in_bytes) into d_out (n values of the
+ * stream's dtype; out_capacity >= n * 4 or n * 8 bytes).  *n_out and
+ * *dtype_out receive the header's values (either may be NULL).  Every read
+ * of the stream is bounds-checked on the device; a malformed stream returns
+ * SZX_ERR_CORRUPT.  Synchronous.  The device status word it uses is one of a
+ * fixed set inside the library (no allocation); concurrent calls from up to
+ * 256 host threads get distinct words.
+ */
+szx_status szx_decompress(const void *d_in, size_t in_bytes, void *d_out,
+                          size_t out_capacity, size_t *n_out,
+                          szx_dtype *dtype_out, szx_stream_t stream);
+
+/*
+ * Asynchronous decompression of a stream whose header the caller already
+ * holds (from szx_header_read, or from the compressing side).  The kernel
+ * re-checks the stream's header against *h.  On completion *d_status (device
+ * pointer, may be NULL) holds a szx_status; the call sets it to SZX_OK first.
+ * Safe to capture in a CUDA graph.
+ */
+szx_status szx_decompress_async(const void *d_in, size_t in_bytes,
+                                const szx_header *h, void *d_out,
+                                size_t out_capacity, uint32_t *d_status,
+                                szx_stream_t stream);
+
+/* Human-readable name of a status code. */
+const char *szx_status_string(szx_status s);
+
+/* Library version string. */
+const char *szx_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SZX_H */

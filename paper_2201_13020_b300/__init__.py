@@ -1,0 +1,121 @@
+"""B300-native SZx block compressor / decompressor (arXiv 2201.13020).
+
+Python binding of the C ABI in include/szx.h.  PyTorch supplies device memory
+and streams; the codec itself runs in the library's sm_103a CUDA kernels.
+
+    import paper_2201_13020_b300 as szx
+    stream = szx.compress(x, eb)          # x: contiguous CUDA float32/float64
+    y = szx.decompress(stream)            # |x - y| <= eb element-wise
+"""
+import ctypes
+
+from ._lib import SZX_F32, SZX_F64, STATUS, SzxHeader, lib
+
+__all__ = ["compress", "decompress", "compress_async", "decompress_async", "compress_bound",
+           "stream_max_bytes", "header", "SzxError", "SZX_F32", "SZX_F64"]
+
+
+class SzxError(RuntimeError):
+    def __init__(self, status, what):
+        name = STATUS.get(status, str(status))
+        super().__init__(f"{what}: {name}")
+        self.status = status
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _dtype_code(t):
+    torch = _torch()
+    if t.dtype == torch.float32:
+        return SZX_F32
+    if t.dtype == torch.float64:
+        return SZX_F64
+    raise TypeError(f"unsupported dtype {t.dtype}: float32 or float64")
+
+
+def _stream_handle(stream):
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _check(status, what):
+    if status != 0:
+        raise SzxError(status, what)
+
+
+def compress_bound(n, dtype=SZX_F32, block=128):
+    """Output-buffer bytes szx_compress needs (largest stream + scratch tail)."""
+    return lib().szx_compress_bound(n, dtype, block)
+
+
+def stream_max_bytes(n, dtype=SZX_F32, block=128):
+    return lib().szx_stream_max_bytes(n, dtype, block)
+
+
+def compress(x, eb, block=128, out=None, stream=None):
+    """Compress a contiguous CUDA tensor; returns a uint8 view of the stream."""
+    torch = _torch()
+    if not x.is_cuda or not x.is_contiguous():
+        raise ValueError("x must be a contiguous CUDA tensor")
+    code = _dtype_code(x)
+    n = x.numel()
+    cap = compress_bound(n, code, block)
+    if cap == 0:
+        raise SzxError(1, "compress_bound")
+    if out is None:
+        out = torch.empty(cap, dtype=torch.uint8, device=x.device)
+    nbytes = ctypes.c_size_t(0)
+    _check(lib().szx_compress(ctypes.c_void_p(x.data_ptr()), n, code, float(eb), block,
+                              ctypes.c_void_p(out.data_ptr()), out.numel(), ctypes.byref(nbytes),
+                              _stream_handle(stream)), "szx_compress")
+    return out[:nbytes.value]
+
+
+def compress_async(x, eb, block, out, result, stream=None):
+    """Enqueue compression; result (CUDA uint64 tensor of 2) gets {bytes, status}."""
+    code = _dtype_code(x)
+    _check(lib().szx_compress_async(ctypes.c_void_p(x.data_ptr()), x.numel(), code, float(eb), block,
+                                    ctypes.c_void_p(out.data_ptr()), out.numel(),
+                                    ctypes.c_void_p(result.data_ptr() if result is not None else 0),
+                                    _stream_handle(stream)), "szx_compress_async")
+
+
+def header(buf, stream=None):
+    """Parse the header of a compressed CUDA uint8 tensor."""
+    h = SzxHeader()
+    _check(lib().szx_header_read(ctypes.c_void_p(buf.data_ptr()), buf.numel(), ctypes.byref(h),
+                                 _stream_handle(stream)), "szx_header_read")
+    return h
+
+
+def header_dict(h):
+    return {f: getattr(h, f) for f, _ in SzxHeader._fields_}
+
+
+def decompress(buf, out=None, stream=None):
+    """Decompress a CUDA uint8 tensor holding a stream; returns the values."""
+    torch = _torch()
+    if not buf.is_cuda:
+        raise ValueError("stream must be a CUDA tensor")
+    h = header(buf, stream)
+    dt = torch.float32 if h.dtype == SZX_F32 else torch.float64
+    if out is None:
+        out = torch.empty(h.n, dtype=dt, device=buf.device)
+    n = ctypes.c_size_t(0)
+    d = ctypes.c_int(0)
+    _check(lib().szx_decompress(ctypes.c_void_p(buf.data_ptr()), buf.numel(), ctypes.c_void_p(out.data_ptr()),
+                                out.numel() * out.element_size(), ctypes.byref(n), ctypes.byref(d),
+                                _stream_handle(stream)), "szx_decompress")
+    return out
+
+
+def decompress_async(buf, h, out, status=None, stream=None):
+    """Enqueue decompression with a known header; status: CUDA uint32/int32 tensor of 1 or None."""
+    _check(lib().szx_decompress_async(ctypes.c_void_p(buf.data_ptr()), buf.numel(), ctypes.byref(h),
+                                      ctypes.c_void_p(out.data_ptr()), out.numel() * out.element_size(),
+                                      ctypes.c_void_p(status.data_ptr() if status is not None else 0),
+                                      _stream_handle(stream)), "szx_decompress_async")

@@ -1,0 +1,61 @@
+"""ctypes binding of libszx.so (the C ABI in include/szx.h).
+
+Argument marshalling only: every step of compression and decompression runs in
+the library's CUDA kernels.  There is no CPU fallback; if the in-tree library
+is missing or cannot be loaded, every call raises.
+"""
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "lib", "libszx.so")
+
+SZX_F32, SZX_F64 = 0, 1
+STATUS = {0: "SZX_OK", 1: "SZX_ERR_INVALID", 2: "SZX_ERR_TOO_SMALL", 3: "SZX_ERR_CORRUPT",
+          4: "SZX_ERR_NOMEM", 5: "SZX_ERR_CUDA", 6: "SZX_ERR_TIMEOUT"}
+
+
+class SzxHeader(ctypes.Structure):
+    _fields_ = [("block", ctypes.c_uint32), ("tile_blocks", ctypes.c_uint32), ("n", ctypes.c_uint64),
+                ("dtype", ctypes.c_int), ("e_bits", ctypes.c_uint64), ("nonconst", ctypes.c_uint64),
+                ("raw", ctypes.c_uint64), ("escalated", ctypes.c_uint64), ("total_bytes", ctypes.c_uint64)]
+
+
+_lib = None
+
+
+def lib():
+    """Load libszx.so once; raise if it is not built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with `python -m paper_2201_13020_b300.build` "
+                           "(or __graft_entry__.build()); there is no CPU fallback")
+    L = ctypes.CDLL(LIB_PATH)
+    sz, u32, u64, dbl, vp, i = (ctypes.c_size_t, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_double,
+                               ctypes.c_void_p, ctypes.c_int)
+    L.szx_compress_bound.restype = sz
+    L.szx_compress_bound.argtypes = [sz, i, u32]
+    L.szx_stream_max_bytes.restype = sz
+    L.szx_stream_max_bytes.argtypes = [sz, i, u32]
+    L.szx_compress.restype = i
+    L.szx_compress.argtypes = [vp, sz, i, dbl, u32, vp, sz, ctypes.POINTER(sz), vp]
+    L.szx_compress_async.restype = i
+    L.szx_compress_async.argtypes = [vp, sz, i, dbl, u32, vp, sz, vp, vp]
+    L.szx_header_read.restype = i
+    L.szx_header_read.argtypes = [vp, sz, ctypes.POINTER(SzxHeader), vp]
+    L.szx_decompress.restype = i
+    L.szx_decompress.argtypes = [vp, sz, vp, sz, ctypes.POINTER(sz), ctypes.POINTER(i), vp]
+    L.szx_decompress_async.restype = i
+    L.szx_decompress_async.argtypes = [vp, sz, ctypes.POINTER(SzxHeader), vp, sz, vp, vp]
+    L.szx_status_string.restype = ctypes.c_char_p
+    L.szx_status_string.argtypes = [i]
+    L.szx_version.restype = ctypes.c_char_p
+    L.szx_version.argtypes = []
+    _lib = L
+    return L
+
+
+EXPORTED = ["szx_compress_bound", "szx_stream_max_bytes", "szx_compress", "szx_compress_async",
+            "szx_header_read", "szx_decompress", "szx_decompress_async", "szx_status_string", "szx_version"]

@@ -1,0 +1,216 @@
+// api.cu -- the extern "C" surface declared in include/szx.h.
+//
+// Host-side argument checks, the stream geometry, and the launch sequence on
+// the caller's stream.  Every device step is one of this library's kernels
+// (plus a cudaMemsetAsync of the compress scratch words); there is no host or
+// CPU fallback: if the kernels cannot run, the call returns SZX_ERR_CUDA.
+#include "szx.h"
+#include "szx_device.cuh"
+#include "szx_launch.h"
+
+#include <atomic>
+#include <cmath>
+#include <cstring>
+#include <mutex>
+
+using namespace szx;
+
+namespace {
+
+constexpr uint64_t kMaxValues = 1ull << 40;
+
+bool block_ok(uint32_t b) { return b >= 32 && b <= 1024 && (b & (b - 1)) == 0; }
+bool dtype_ok(szx_dtype d) { return d == SZX_F32 || d == SZX_F64; }
+uint32_t width(szx_dtype d) { return d == SZX_F32 ? 4u : 8u; }
+bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+uint64_t align256(uint64_t x) { return (x + 255) & ~uint64_t(255); }
+
+// The bound actually used: f32 takes the largest float <= eb.
+uint64_t bound_bits(double eb, szx_dtype d) {
+    if (d == SZX_F64) {
+        uint64_t u;
+        std::memcpy(&u, &eb, 8);
+        return u;
+    }
+    float f = static_cast<float>(eb);
+    if (static_cast<double>(f) > eb) f = std::nextafterf(f, 0.0f);
+    uint32_t u;
+    std::memcpy(&u, &f, 4);
+    return u;
+}
+
+uint64_t stream_max(uint64_t n, uint32_t b, uint32_t w) {
+    const Geometry g = make_geometry(n, b, w);
+    const uint64_t full = g.ntiles - 1;
+    const uint64_t last_blocks = g.nb - full * g.G;
+    const uint64_t last_vals = n - full * g.G * b;
+    return g.off_rec + full * record_max_bytes(g.G, b, w) +
+           pad16(last_blocks * (b / 4 + 1) + last_vals * w);
+}
+
+szx_status from_cuda(cudaError_t e) { return e == cudaSuccess ? SZX_OK : SZX_ERR_CUDA; }
+
+// Per-device status words for the synchronous decompress (allocated once per
+// device on first use, kept until exit).
+constexpr int kSlots = 256;
+std::mutex g_ctx_mu;
+uint32_t *g_status[64] = {};
+std::atomic<uint32_t> g_slot{0};
+
+uint32_t *status_slot(szx_status *st) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+        *st = SZX_ERR_CUDA;
+        return nullptr;
+    }
+    std::lock_guard<std::mutex> lock(g_ctx_mu);
+    if (!g_status[dev]) {
+        if (cudaMalloc(&g_status[dev], kSlots * sizeof(uint32_t)) != cudaSuccess) {
+            *st = SZX_ERR_CUDA;
+            return nullptr;
+        }
+    }
+    *st = SZX_OK;
+    return g_status[dev] + (g_slot.fetch_add(1) % kSlots);
+}
+
+szx_status parse_header(const uint8_t *h, uint64_t in_bytes, szx_header *out) {
+    uint32_t h32[4];
+    uint64_t h64[8];
+    std::memcpy(h32, h, 16);
+    std::memcpy(h64, h, 64);
+    if (h32[0] != kMagic || (h32[1] & 0xFFu) != kVersion || (h32[1] >> 16) != 0) return SZX_ERR_CORRUPT;
+    const uint32_t dt = (h32[1] >> 8) & 0xFFu;
+    if (dt > 1) return SZX_ERR_CORRUPT;
+    const szx_dtype d = (szx_dtype)dt;
+    const uint32_t b = h32[2];
+    if (!block_ok(b) || h32[3] != tile_blocks(b, width(d))) return SZX_ERR_CORRUPT;
+    const uint64_t n = h64[2];
+    if (n == 0 || n > kMaxValues) return SZX_ERR_CORRUPT;
+    const Geometry g = make_geometry(n, b, width(d));
+    const uint64_t total = h64[7];
+    if (total > in_bytes || total < g.off_rec || (total & 15)) return SZX_ERR_CORRUPT;
+    out->block = b;
+    out->tile_blocks = h32[3];
+    out->n = n;
+    out->dtype = d;
+    out->e_bits = h64[3];
+    out->nonconst = h64[4];
+    out->raw = h64[5];
+    out->escalated = h64[6];
+    out->total_bytes = total;
+    return SZX_OK;
+}
+
+szx_status check_compress_args(const void *d_in, size_t n, szx_dtype dtype, double eb, uint32_t block,
+                               const void *d_out, size_t out_capacity) {
+    if (!d_in || !d_out || !dtype_ok(dtype) || !block_ok(block)) return SZX_ERR_INVALID;
+    if (n == 0 || n > kMaxValues) return SZX_ERR_INVALID;
+    if (!(eb > 0.0) || !std::isfinite(eb)) return SZX_ERR_INVALID;
+    if (!aligned16(d_in) || !aligned16(d_out)) return SZX_ERR_INVALID;
+    if (out_capacity < szx_compress_bound(n, dtype, block)) return SZX_ERR_TOO_SMALL;
+    return SZX_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t szx_stream_max_bytes(size_t n, szx_dtype dtype, uint32_t block) {
+    if (!dtype_ok(dtype) || !block_ok(block) || n == 0 || n > kMaxValues) return 0;
+    return (size_t)stream_max(n, block, width(dtype));
+}
+
+size_t szx_compress_bound(size_t n, szx_dtype dtype, uint32_t block) {
+    const size_t smax = szx_stream_max_bytes(n, dtype, block);
+    if (!smax) return 0;
+    const Geometry g = make_geometry(n, block, width(dtype));
+    return (size_t)(align256(smax) + workspace_bytes(g.ntiles));
+}
+
+szx_status szx_compress_async(const void *d_in, size_t n, szx_dtype dtype, double eb, uint32_t block,
+                              void *d_out, size_t out_capacity, uint64_t *d_result, szx_stream_t stream) {
+    szx_status st = check_compress_args(d_in, n, dtype, eb, block, d_out, out_capacity);
+    if (st != SZX_OK) return st;
+    const uint64_t ws = align256(stream_max(n, block, width(dtype)));
+    return from_cuda(launch_compress(d_in, n, (int)dtype, bound_bits(eb, dtype), block, d_out, ws, d_result,
+                                     (cudaStream_t)stream));
+}
+
+szx_status szx_compress(const void *d_in, size_t n, szx_dtype dtype, double eb, uint32_t block, void *d_out,
+                        size_t out_capacity, size_t *out_bytes, szx_stream_t stream) {
+    if (!out_bytes) return SZX_ERR_INVALID;
+    szx_status st = szx_compress_async(d_in, n, dtype, eb, block, d_out, out_capacity, nullptr, stream);
+    if (st != SZX_OK) return st;
+    const uint64_t ws = align256(stream_max(n, block, width(dtype)));
+    const Workspace *w = reinterpret_cast<const Workspace *>(static_cast<const uint8_t *>(d_out) + ws);
+    unsigned long long result[2] = {0, 0};
+    cudaStream_t s = (cudaStream_t)stream;
+    if (cudaMemcpyAsync(result, &w->result, sizeof(result), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        return SZX_ERR_CUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return SZX_ERR_CUDA;
+    if (result[1] != 0) return (szx_status)result[1];
+    *out_bytes = (size_t)result[0];
+    return SZX_OK;
+}
+
+szx_status szx_header_read(const void *d_in, size_t in_bytes, szx_header *h, szx_stream_t stream) {
+    if (!d_in || !h) return SZX_ERR_INVALID;
+    if (in_bytes < (size_t)kHeaderBytes) return SZX_ERR_CORRUPT;
+    uint8_t buf[kHeaderBytes];
+    cudaStream_t s = (cudaStream_t)stream;
+    if (cudaMemcpyAsync(buf, d_in, kHeaderBytes, cudaMemcpyDeviceToHost, s) != cudaSuccess) return SZX_ERR_CUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return SZX_ERR_CUDA;
+    return parse_header(buf, in_bytes, h);
+}
+
+szx_status szx_decompress_async(const void *d_in, size_t in_bytes, const szx_header *h, void *d_out,
+                                size_t out_capacity, uint32_t *d_status, szx_stream_t stream) {
+    if (!d_in || !h || !d_out) return SZX_ERR_INVALID;
+    if (!aligned16(d_in) || !aligned16(d_out)) return SZX_ERR_INVALID;
+    if (!dtype_ok(h->dtype) || !block_ok(h->block) || h->n == 0 || h->n > kMaxValues) return SZX_ERR_INVALID;
+    if (h->tile_blocks != tile_blocks(h->block, width(h->dtype))) return SZX_ERR_INVALID;
+    const Geometry g = make_geometry(h->n, h->block, width(h->dtype));
+    if (h->total_bytes > in_bytes || h->total_bytes < g.off_rec) return SZX_ERR_CORRUPT;
+    if (out_capacity < h->n * width(h->dtype)) return SZX_ERR_TOO_SMALL;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (d_status && cudaMemsetAsync(d_status, 0, sizeof(uint32_t), s) != cudaSuccess) return SZX_ERR_CUDA;
+    return from_cuda(launch_decompress(d_in, in_bytes, h->total_bytes, h->n, (int)h->dtype, h->block, d_out,
+                                       d_status, true, s));
+}
+
+szx_status szx_decompress(const void *d_in, size_t in_bytes, void *d_out, size_t out_capacity, size_t *n_out,
+                          szx_dtype *dtype_out, szx_stream_t stream) {
+    szx_header h;
+    szx_status st = szx_header_read(d_in, in_bytes, &h, stream);
+    if (st != SZX_OK) return st;
+    if (n_out) *n_out = (size_t)h.n;
+    if (dtype_out) *dtype_out = h.dtype;
+    if (!d_out) return SZX_ERR_INVALID;
+    uint32_t *slot = status_slot(&st);
+    if (!slot) return st;
+    st = szx_decompress_async(d_in, in_bytes, &h, d_out, out_capacity, slot, stream);
+    if (st != SZX_OK) return st;
+    uint32_t code = 0;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (cudaMemcpyAsync(&code, slot, sizeof(code), cudaMemcpyDeviceToHost, s) != cudaSuccess) return SZX_ERR_CUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return SZX_ERR_CUDA;
+    return (szx_status)code;
+}
+
+const char *szx_status_string(szx_status s) {
+    switch (s) {
+        case SZX_OK: return "ok";
+        case SZX_ERR_INVALID: return "invalid argument";
+        case SZX_ERR_TOO_SMALL: return "output buffer too small";
+        case SZX_ERR_CORRUPT: return "corrupt or truncated stream";
+        case SZX_ERR_NOMEM: return "out of host memory";
+        case SZX_ERR_CUDA: return "CUDA runtime error";
+        case SZX_ERR_TIMEOUT: return "device wait timed out";
+    }
+    return "unknown status";
+}
+
+const char *szx_version(void) { return "szx-b300 1.0 (sm_103a)"; }
+
+}  // extern "C"

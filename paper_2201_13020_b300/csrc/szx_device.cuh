@@ -1,0 +1,328 @@
+// szx_device.cuh -- device-side building blocks of the sm_103a SZx codec.
+//
+// Formats, the exact |a - b| <= e test, warp reductions/scans, inline PTX for
+// the Blackwell bulk-copy engine (cp.async.bulk + mbarrier), and the stream
+// geometry shared by the compress and decompress kernels.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace szx {
+
+constexpr uint32_t kFull = 0xFFFFFFFFu;
+constexpr uint32_t kMagic = 0x42585A53u;  // "SZXB"
+constexpr uint32_t kVersion = 1;
+constexpr int kHeaderBytes = 64;
+constexpr int kWarps = 8;  // warps per CTA in both kernels
+constexpr int kThreads = kWarps * 32;
+
+// Block kinds (Algorithm 1: constant / non-constant; plus verbatim "raw").
+enum : uint8_t { kConst = 0, kNonConst = 1, kRaw = 2 };
+
+// Device error bits (compress workspace and decompress status word).
+enum : uint32_t { kErrTimeout = 1u, kErrCorrupt = 2u };
+
+// ---------------------------------------------------------------------------
+// IEEE formats
+
+template <typename T>
+struct Fmt;
+
+template <>
+struct Fmt<float> {
+    using U = uint32_t;
+    using S = int32_t;
+    static constexpr int w = 4, W = 32, E = 8, M = 23, bias = 127;
+    __device__ __forceinline__ static float from(U u) { return __uint_as_float(u); }
+    __device__ __forceinline__ static U bits(float f) { return __float_as_uint(f); }
+    __device__ __forceinline__ static float add(float a, float b) { return __fadd_rn(a, b); }
+    __device__ __forceinline__ static float sub(float a, float b) { return __fsub_rn(a, b); }
+    __device__ __forceinline__ static float half(float a) { return __fmul_rn(a, 0.5f); }
+    __device__ __forceinline__ static int clz(U x) { return __clz(x); }
+    __device__ __forceinline__ static bool finite(U u) { return ((u >> 23) & 0xFFu) != 0xFFu; }
+    __device__ __forceinline__ static int expo(U u) { return (int)((u >> 23) & 0xFFu) - 127; }
+    // order-preserving signed key: totalOrder on finite values (-0 < +0)
+    __device__ __forceinline__ static S key(U u) { return (S)(u ^ ((U)((S)u >> 31) & 0x7FFFFFFFu)); }
+    __device__ __forceinline__ static U unkey(S k) { return (U)k ^ ((U)(k >> 31) & 0x7FFFFFFFu); }
+    static constexpr S kKeyPosInf = 0x7F800000;
+    static constexpr S kKeyNegInf = (S)0x807FFFFF;
+};
+
+template <>
+struct Fmt<double> {
+    using U = uint64_t;
+    using S = int64_t;
+    static constexpr int w = 8, W = 64, E = 11, M = 52, bias = 1023;
+    __device__ __forceinline__ static double from(U u) { return __longlong_as_double((long long)u); }
+    __device__ __forceinline__ static U bits(double f) { return (U)__double_as_longlong(f); }
+    __device__ __forceinline__ static double add(double a, double b) { return __dadd_rn(a, b); }
+    __device__ __forceinline__ static double sub(double a, double b) { return __dsub_rn(a, b); }
+    __device__ __forceinline__ static double half(double a) { return __dmul_rn(a, 0.5); }
+    __device__ __forceinline__ static int clz(U x) { return __clzll((long long)x); }
+    __device__ __forceinline__ static bool finite(U u) { return ((u >> 52) & 0x7FFull) != 0x7FFull; }
+    __device__ __forceinline__ static int expo(U u) { return (int)((u >> 52) & 0x7FFull) - 1023; }
+    __device__ __forceinline__ static S key(U u) {
+        return (S)(u ^ ((U)((S)u >> 63) & 0x7FFFFFFFFFFFFFFFull));
+    }
+    __device__ __forceinline__ static U unkey(S k) {
+        return (U)k ^ ((U)(k >> 63) & 0x7FFFFFFFFFFFFFFFull);
+    }
+    static constexpr S kKeyPosInf = 0x7FF0000000000000ll;
+    static constexpr S kKeyNegInf = (S)0x800FFFFFFFFFFFFFull;
+};
+
+// Mask of the top 8q bits of a W-bit word (q in [1, W/8]).
+template <typename U>
+__device__ __forceinline__ U top_bytes_mask(int q) {
+    constexpr int W = 8 * sizeof(U);
+    return q * 8 >= W ? ~(U)0 : ~(U)0 << (W - 8 * q);
+}
+
+// Exact |a - b| <= e for finite a, b and finite e >= 0 (Eq. 1 as an exact
+// predicate).  RN(a - b) decides every case except |RN(a - b)| == e, where the
+// sign of the rounding error, recovered exactly by Knuth's TwoSum, decides.
+template <typename T>
+__device__ __forceinline__ bool within(T a, T b, T e) {
+    using F = Fmt<T>;
+    T s = F::sub(a, b);
+    T as = fabs(s);
+    if (as < e) return true;
+    if (!(as == e)) return false;  // > e, or an overflow to infinity
+    T y = -b;
+    T bv = F::sub(s, a);
+    T av = F::sub(s, bv);
+    T t = F::add(F::sub(a, av), F::sub(y, bv));
+    if (s > T(0)) return t <= T(0);
+    if (s < T(0)) return t >= T(0);
+    return t == T(0);
+}
+
+// ---------------------------------------------------------------------------
+// warp helpers
+
+__device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
+
+__host__ __device__ __forceinline__ uint64_t min_u64(uint64_t a, uint64_t b) { return a < b ? a : b; }
+
+__device__ __forceinline__ int32_t warp_min(int32_t v) { return __reduce_min_sync(kFull, v); }
+__device__ __forceinline__ int32_t warp_max(int32_t v) { return __reduce_max_sync(kFull, v); }
+__device__ __forceinline__ int64_t warp_min(int64_t v) {
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) {
+        int64_t o = __shfl_xor_sync(kFull, v, d);
+        v = o < v ? o : v;
+    }
+    return v;
+}
+__device__ __forceinline__ int64_t warp_max(int64_t v) {
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) {
+        int64_t o = __shfl_xor_sync(kFull, v, d);
+        v = o > v ? o : v;
+    }
+    return v;
+}
+
+// Exclusive prefix sum over the warp; *total receives the warp's sum.
+template <typename V>
+__device__ __forceinline__ V warp_exclusive_scan(V v, V *total) {
+    const int lane = lane_id();
+    V x = v;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        V y = __shfl_up_sync(kFull, x, d);
+        if (lane >= d) x += y;
+    }
+    *total = __shfl_sync(kFull, x, 31);
+    return x - v;
+}
+
+// ---------------------------------------------------------------------------
+// Blackwell bulk-copy engine (TMA, non-tensor form) and mbarriers
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile(
+        "{\n\t.reg .b64 st;\n\t"
+        "mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(smem_addr(bar)),
+        "r"(bytes)
+        : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait on an mbarrier phase; returns false if the limit ran out.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, uint32_t limit) {
+    for (uint32_t i = 0; i < limit; ++i) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (i > 64) __nanosleep(64);
+    }
+    return false;
+}
+
+// global -> shared bulk copy, completion counted on the mbarrier.
+// dst, src 16-byte aligned; bytes a multiple of 16.
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+
+// shared -> global bulk copy (bulk-group completion).
+__device__ __forceinline__ void bulk_s2g(void *dst, const void *src, uint32_t bytes) {
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst),
+                 "r"(smem_addr(src)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read_all() {
+    asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+}
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+
+// Make generic-proxy shared-memory writes visible to the async proxy.
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ uint64_t ld_acquire_u64(const uint64_t *p) {
+    uint64_t v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_u64(uint64_t *p, uint64_t v) {
+    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+// ---------------------------------------------------------------------------
+// stream geometry (host and device)
+
+__host__ __device__ __forceinline__ uint64_t pad16(uint64_t x) { return (x + 15) & ~uint64_t(15); }
+
+__host__ __device__ __forceinline__ uint32_t tile_blocks(uint32_t b, uint32_t w) {
+    uint32_t g = 32768u / (b * w);
+    return g < 8 ? 8 : g;
+}
+
+struct Geometry {
+    uint64_t n, nb, ntiles;
+    uint32_t b, G, w;
+    uint64_t off_state, off_mu, off_index, off_rec;
+};
+
+__host__ __device__ inline Geometry make_geometry(uint64_t n, uint32_t b, uint32_t w) {
+    Geometry g;
+    g.n = n;
+    g.b = b;
+    g.w = w;
+    g.G = tile_blocks(b, w);
+    g.nb = (n + b - 1) / b;
+    g.ntiles = (g.nb + g.G - 1) / g.G;
+    g.off_state = kHeaderBytes;
+    g.off_mu = g.off_state + pad16((g.nb + 7) / 8);
+    g.off_index = g.off_mu + pad16(g.nb * w);
+    g.off_rec = g.off_index + pad16((g.ntiles + 1) * 8);
+    return g;
+}
+
+// Largest record of one tile: every block raw.
+__host__ __device__ __forceinline__ uint32_t record_max_bytes(uint32_t G, uint32_t b, uint32_t w) {
+    return (uint32_t)pad16((uint64_t)G * (b / 4 + 1) + (uint64_t)G * b * w);
+}
+
+// Compress workspace, at the 256-byte-aligned end of the largest stream.
+struct Workspace {
+    uint32_t ticket;  // next tile ticket (tiles are processed in ticket order)
+    uint32_t done;    // tiles finished
+    uint32_t err;     // kErr* bits
+    uint32_t pad0;
+    unsigned long long nn, nraw, nesc;
+    unsigned long long result[2];  // stream bytes, status (written by the last tile)
+    unsigned long long pad1;
+    // followed by ntiles look-back words
+};
+constexpr uint64_t kWsHeader = 64;
+static_assert(sizeof(Workspace) == kWsHeader, "workspace header layout");
+
+// look-back word: 2-bit flag | 62-bit record byte count
+constexpr uint64_t kFlagAgg = 1ull << 62;
+constexpr uint64_t kFlagPrefix = 2ull << 62;
+constexpr uint64_t kValueMask = (1ull << 62) - 1;
+
+__host__ __device__ __forceinline__ uint64_t workspace_bytes(uint64_t ntiles) {
+    return kWsHeader + 8 * ntiles;
+}
+
+// Shared-memory carve-up of the compress kernel.
+struct CompressSmem {
+    uint32_t in, rec, lead, mu, kind, req, mk, rank, midoff, total;
+};
+__host__ __device__ inline CompressSmem compress_smem(uint32_t G, uint32_t b, uint32_t w) {
+    CompressSmem s;
+    uint32_t o = 0;
+    auto take = [&](uint32_t bytes) {
+        uint32_t at = o;
+        o = (o + bytes + 127) & ~127u;
+        return at;
+    };
+    s.in = take(G * b * w);
+    s.rec = take(record_max_bytes(G, b, w));
+    s.lead = take(G * (b / 4));
+    s.mu = take(G * w);
+    s.kind = take(G);
+    s.req = take(G);
+    s.mk = take(G * 4);
+    s.rank = take(G * 4);
+    s.midoff = take(G * 4);
+    s.total = o;
+    return s;
+}
+
+// Shared-memory carve-up of the decompress kernel.
+struct DecompressSmem {
+    uint32_t rec, mu, state, req, mk, rank, midoff, total;
+};
+__host__ __device__ inline DecompressSmem decompress_smem(uint32_t G, uint32_t b, uint32_t w) {
+    DecompressSmem s;
+    uint32_t o = 0;
+    auto take = [&](uint32_t bytes) {
+        uint32_t at = o;
+        o = (o + bytes + 127) & ~127u;
+        return at;
+    };
+    s.rec = take(record_max_bytes(G, b, w));
+    s.mu = take(G * w);
+    s.state = take((G + 7) / 8 + 16);
+    s.req = take(G);
+    s.mk = take(G * 4);
+    s.rank = take(G * 4);
+    s.midoff = take(G * 4);
+    s.total = o;
+    return s;
+}
+
+}  // namespace szx

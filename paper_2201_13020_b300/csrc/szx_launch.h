@@ -1,0 +1,22 @@
+// szx_launch.h -- internal launchers behind the C ABI (not part of the ABI).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace szx {
+
+// Enqueue the compression of n values (dtype 0 = f32, 1 = f64) with bound bits
+// e_bits into the stream at out; the workspace starts ws_offset bytes into
+// out.  Optionally writes {stream bytes, status} to d_result on completion.
+cudaError_t launch_compress(const void *in, uint64_t n, int dtype, uint64_t e_bits, uint32_t block,
+                            void *out, uint64_t ws_offset, uint64_t *d_result, cudaStream_t stream);
+
+// Enqueue the decompression of a stream of total_bytes whose header says
+// (n, dtype, block).  Errors are folded into *d_status with atomicMax as
+// szx_status codes (d_status may be null).
+cudaError_t launch_decompress(const void *in, uint64_t in_bytes, uint64_t total_bytes, uint64_t n, int dtype,
+                              uint32_t block, void *out, uint32_t *d_status, bool check_header,
+                              cudaStream_t stream);
+
+}  // namespace szx
