@@ -10,6 +10,7 @@
 
 #include <atomic>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 
@@ -113,6 +114,15 @@ szx_status check_compress_args(const void *d_in, size_t n, szx_dtype dtype, doub
 }
 
 }  // namespace
+
+uint32_t szx::wait_limit_from_env(const char *name, uint32_t fallback) {
+    const char *v = std::getenv(name);
+    if (!v || !*v) return fallback;
+    char *end = nullptr;
+    const unsigned long long x = std::strtoull(v, &end, 10);
+    if (end == v || x == 0 || x > 0xFFFFFFFFull) return fallback;
+    return (uint32_t)x;
+}
 
 extern "C" {
 

@@ -1,30 +1,52 @@
 // compress.cu -- single-pass SZx compression kernel for sm_103a.
 //
-// One CTA compresses one tile of G consecutive blocks (32 KiB of input) and
-// emits the tile's record; tiles are taken in ticket order so that the
-// decoupled look-back over tile record sizes (the device-wide exclusive scan
-// that places each record, cf. the prefix scan of Sec. V-B) always waits on
-// tiles that are already running.  Per tile:
-//   1. one thread bulk-copies the tile's input into shared memory (TMA,
-//      cp.async.bulk + mbarrier);
-//   2. each warp encodes whole blocks (Algorithm 1): min/max of the block as
-//      order-preserving integer keys with warp reductions, mu and r, the exact
-//      constant test, reqBits (Eq. 3), the Eq. 4 shift and truncation with the
-//      exact per-value bound check, the XOR identical-leading-byte codes, and
-//      the block's mid-byte count; the truncated words overwrite the input in
-//      shared memory;
-//   3. warp 0 scans the blocks of the tile (non-constant rank, mid-byte
-//      offsets) and the tile publishes its record size;
-//   4. all warps write the record into shared memory: lead codes, reqBits
-//      bytes, and the mid-byte planes (plane j = byte j of each value whose
-//      identical-leading-byte count is <= j, ascending value index);
-//   5. one thread finishes the look-back, writes the tile index entry, and
-//      bulk-stores the record to its offset.
+// One CTA (8 warps) compresses one tile of G consecutive blocks (32 KiB of
+// input) into the tile's record.  Tiles are taken in ticket order, so the
+// decoupled look-back over tile record sizes -- the device-wide exclusive scan
+// that places each record (the prefix scan of Sec. V-B) -- only ever waits on
+// tiles that are already running.
+//
+// Work layout: every lane owns 128 contiguous input bytes (32 f32 or 16 f64
+// values); a block of b values is handled by LPB = b / VPL adjacent lanes
+// (4 lanes for f32, b = 128), so the per-block bookkeeping is spread over few
+// lanes and the serial previous-value dependency stays inside a lane except
+// at lane boundaries.
+//
+// Per tile:
+//   1. one thread loads the tile with a 2-D TMA tensor copy (rows of 128 B,
+//      128-byte swizzle), so each lane reads its row from shared memory
+//      without bank conflicts;
+//   2. block statistics (Algorithm 1): NaN-propagating min/max per lane,
+//      reduced over the block's lanes with shuffles; mu, r, the exact constant
+//      test, reqBits (Eq. 3), the Eq. 4 shift and truncation with a per-value
+//      bound check (a fast test; an exact slow path re-checks a block that
+//      fails it and raises reqBits while a value exceeds e), identical
+//      leading-byte codes against the previous value and the block's mid-byte
+//      count; the truncated words stay in registers;
+//   3. warp 0 scans the tile's blocks (non-constant rank, mid-byte offset)
+//      and publishes the tile's record size; the input buffer is cleared and
+//      reused for the record;
+//   4. lanes write lead codes, reqBits bytes and the mid-byte planes (plane j
+//      = byte j of every value whose code is <= j, ascending index): a 4x4
+//      byte transpose of four values gives their byte-j word, a 256-entry
+//      table compacts the selected bytes, and shared-memory OR writes place the
+//      run at its byte offset;
+//   5. one thread finishes the look-back, writes the tile index entry and
+//      bulk-stores the record (TMA, cp.async.bulk) to its offset.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <cstring>
+#include <limits>
+#include <mutex>
+#include <type_traits>
+
 #include "szx_device.cuh"
 #include "szx_launch.h"
 
-#include <limits>
-#include <type_traits>
+#ifndef SZX_CHECKS
+#define SZX_CHECKS 0  // 1: self-checks of every record write (diagnostic builds)
+#endif
 
 namespace szx {
 
@@ -36,279 +58,377 @@ struct CompressArgs {
     uint64_t *d_result;
     Geometry g;
     uint64_t e_bits;
+    uint64_t rows_full;  // 128-byte input rows fully inside the input
     uint32_t dtype;
-    uint32_t spin_limit;
+    uint64_t lookback_ns;  // wall-time limit of the look-back wait
+    uint64_t copy_ns;      // wall-time limit of the tile copy wait
+    uint32_t use_tma;
 };
 
-template <typename U, int VPL>
-__device__ __forceinline__ void load_lane(const U *p, U (&x)[VPL]) {
-    constexpr int bytes = VPL * (int)sizeof(U);
-    if constexpr (bytes % 16 == 0) {
-#pragma unroll
-        for (int i = 0; i < bytes / 16; ++i) {
-            uint4 v = reinterpret_cast<const uint4 *>(p)[i];
-            const U *u = reinterpret_cast<const U *>(&v);
-#pragma unroll
-            for (int j = 0; j < 16 / (int)sizeof(U); ++j) x[i * (16 / sizeof(U)) + j] = u[j];
+// ---------------------------------------------------------------------------
+// small device helpers
+
+__device__ __forceinline__ float min_nan(float a, float b) {
+    float r;
+    asm("min.NaN.f32 %0, %1, %2;" : "=f"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ float max_nan(float a, float b) {
+    float r;
+    asm("max.NaN.f32 %0, %1, %2;" : "=f"(r) : "f"(a), "f"(b));
+    return r;
+}
+
+__device__ __forceinline__ uint32_t prmt(uint32_t a, uint32_t b, uint32_t s) { return __byte_perm(a, b, s); }
+
+// OR a run of up to 4 bytes (little-endian in `run`) into the zero-initialised
+// byte buffer at byte offset p.  The buffer has 4 bytes of slack at the end.
+__device__ __forceinline__ void or_bytes(uint32_t *words, uint32_t p, uint32_t run) {
+    const uint32_t sh = (p & 3u) * 8u;
+    uint32_t *wp = words + (p >> 2);
+    atomicOr(wp, run << sh);
+    atomicOr(wp + 1, __funnelshift_l(run, 0u, sh));
+}
+
+// Record a failed self-check (first tile and check id).
+__device__ __forceinline__ void report_bad(Workspace *ws, uint32_t tile, uint32_t code) {
+    atomicOr(&ws->err, kErrInternal);
+    if (atomicCAS(&ws->first_bad_tile, 0u, tile + 1) == 0u) ws->bad_code = code;
+}
+
+// 4x4 byte transpose: W[j] holds byte j (most significant first) of the four
+// 32-bit words t0..t3, value k in byte k.
+__device__ __forceinline__ void transpose4(uint32_t t0, uint32_t t1, uint32_t t2, uint32_t t3, uint32_t (&W)[4]) {
+    const uint32_t a = prmt(t0, t1, 0x5140), b = prmt(t0, t1, 0x7362);
+    const uint32_t c = prmt(t2, t3, 0x5140), d = prmt(t2, t3, 0x7362);
+    W[3] = prmt(a, c, 0x5410);
+    W[2] = prmt(a, c, 0x7632);
+    W[1] = prmt(b, d, 0x5410);
+    W[0] = prmt(b, d, 0x7632);
+}
+
+// Compaction table: for plane j in 0..2 and the 2-bit codes of four values
+// (value k at bits 2k), entry = byte-permute selector taking the bytes of the
+// values with code <= j in order (unused nibbles select zero) | count << 16.
+__device__ __forceinline__ void build_lut(uint32_t *lut) {
+    for (uint32_t i = threadIdx.x; i < 3 * 256; i += blockDim.x) {
+        const uint32_t j = i >> 8, code = i & 255u;
+        uint32_t sel = 0x4444u, cnt = 0;
+        for (uint32_t k = 0; k < 4; ++k) {
+            if (((code >> (2 * k)) & 3u) <= j) {
+                sel = (sel & ~(0xFu << (4 * cnt))) | (k << (4 * cnt));
+                ++cnt;
+            }
         }
-    } else if constexpr (bytes == 8) {
-        uint2 v = *reinterpret_cast<const uint2 *>(p);
-        const U *u = reinterpret_cast<const U *>(&v);
-#pragma unroll
-        for (int j = 0; j < VPL; ++j) x[j] = u[j];
-    } else {
-        x[0] = p[0];
+        lut[i] = sel | (cnt << 16);
     }
 }
 
-template <typename U, int VPL>
-__device__ __forceinline__ void store_lane(U *p, const U (&x)[VPL]) {
-    constexpr int bytes = VPL * (int)sizeof(U);
-    if constexpr (bytes % 16 == 0) {
-#pragma unroll
-        for (int i = 0; i < bytes / 16; ++i) {
-            uint4 v;
-            U *u = reinterpret_cast<U *>(&v);
-#pragma unroll
-            for (int j = 0; j < 16 / (int)sizeof(U); ++j) u[j] = x[i * (16 / sizeof(U)) + j];
-            reinterpret_cast<uint4 *>(p)[i] = v;
-        }
-    } else if constexpr (bytes == 8) {
-        uint2 v;
-        U *u = reinterpret_cast<U *>(&v);
-#pragma unroll
-        for (int j = 0; j < VPL; ++j) u[j] = x[j];
-        *reinterpret_cast<uint2 *>(p) = v;
-    } else {
-        p[0] = x[0];
-    }
-}
-
-// Lead codes of one lane (2 bits per value, value m at bits 2m) to and from
-// the block's b/4-byte code slot (value i at byte i/4, bits 2(i%4)).
-template <int VPL>
-using CodeT = std::conditional_t<(VPL > 16), uint64_t, uint32_t>;
-
-template <int VPL>
-__device__ __forceinline__ void put_codes(uint8_t *slot, CodeT<VPL> c) {
-    const int lane = lane_id();
-    if constexpr (VPL >= 4) {
-        constexpr int nb = VPL / 4;
-        if constexpr (nb == 1) slot[lane] = (uint8_t)c;
-        else if constexpr (nb == 2) reinterpret_cast<uint16_t *>(slot)[lane] = (uint16_t)c;
-        else if constexpr (nb == 4) reinterpret_cast<uint32_t *>(slot)[lane] = (uint32_t)c;
-        else reinterpret_cast<uint64_t *>(slot)[lane] = (uint64_t)c;
-    } else if constexpr (VPL == 2) {
-        uint32_t hi = __shfl_down_sync(kFull, (uint32_t)c, 1);
-        if ((lane & 1) == 0) slot[lane >> 1] = (uint8_t)(c | (hi << 4));
-    } else {
-        uint32_t c1 = __shfl_down_sync(kFull, (uint32_t)c, 1);
-        uint32_t c2 = __shfl_down_sync(kFull, (uint32_t)c, 2);
-        uint32_t c3 = __shfl_down_sync(kFull, (uint32_t)c, 3);
-        if ((lane & 3) == 0) slot[lane >> 2] = (uint8_t)(c | (c1 << 2) | (c2 << 4) | (c3 << 6));
-    }
-}
-
-template <int VPL>
-__device__ __forceinline__ CodeT<VPL> get_codes(const uint8_t *slot) {
-    const int lane = lane_id();
-    if constexpr (VPL >= 4) {
-        constexpr int nb = VPL / 4;
-        if constexpr (nb == 1) return slot[lane];
-        else if constexpr (nb == 2) return reinterpret_cast<const uint16_t *>(slot)[lane];
-        else if constexpr (nb == 4) return reinterpret_cast<const uint32_t *>(slot)[lane];
-        else return reinterpret_cast<const uint64_t *>(slot)[lane];
-    } else if constexpr (VPL == 2) {
-        return (slot[lane >> 1] >> (4 * (lane & 1))) & 0xFu;
-    } else {
-        return (slot[lane >> 2] >> (2 * (lane & 3))) & 0x3u;
-    }
-}
-
-// Per-lane counts of values with L <= j for the three sparse planes j = 0,1,2,
-// packed in fields of PB bits (a plane of a block holds at most b <= 1024).
-template <int VPL>
-struct PlanePack {
-    using T = std::conditional_t<(VPL > 16), uint64_t, uint32_t>;
-    static constexpr int PB = VPL > 16 ? 16 : 10;
-    static constexpr T one3 = (T(1) << (2 * PB)) | (T(1) << PB) | T(1);
-    __device__ __forceinline__ static T inc(int L) { return (one3 >> (PB * L)) << (PB * L); }
-    __device__ __forceinline__ static uint32_t field(T v, int j) {
-        return (uint32_t)(v >> (PB * j)) & ((1u << PB) - 1);
-    }
+// Shared-memory layout of the compress kernel.
+struct CSmem2 {
+    uint32_t buf, buf_bytes, lut, kind, req, mk, mu, rank, midoff, total;
 };
-
-template <typename U>
-__device__ __forceinline__ uint32_t byte_of(U t, int j) {
-    constexpr int W = 8 * sizeof(U);
-    return (uint32_t)(t >> (W - 8 - 8 * j)) & 0xFFu;
+__host__ __device__ inline CSmem2 compress_smem2(uint32_t G, uint32_t b, uint32_t w) {
+    CSmem2 s;
+    uint32_t o = 0;
+    auto take = [&](uint32_t bytes, uint32_t align) {
+        o = (o + align - 1) & ~(align - 1);
+        const uint32_t at = o;
+        o += bytes;
+        return at;
+    };
+    const uint32_t tile = G * b * w;
+    const uint32_t rec = record_max_bytes(G, b, w);
+    s.buf_bytes = ((tile > rec ? tile : rec) + 16 + 15) & ~15u;
+    s.buf = take(s.buf_bytes, 1024);
+    s.lut = take(3 * 256 * 4, 16);
+    s.kind = take(G, 16);
+    s.req = take(G, 16);
+    s.mk = take(4 * G, 16);
+    s.mu = take(w * G, 16);
+    s.rank = take(4 * G, 16);
+    s.midoff = take(4 * G, 16);
+    s.total = ((o + 1023) & ~1023u) + 1024;  // + slack to realign the dynamic base
+    return s;
 }
 
-template <typename T, int VPL>
-__global__ void __launch_bounds__(kThreads) compress_kernel(CompressArgs a) {
+template <typename T, int LPB, int VPL>
+__global__ void __launch_bounds__(kThreads, (VPL * sizeof(T) > 128) ? 1 : (sizeof(T) == 8 ? 3 : 4)) compress_kernel(const __grid_constant__ CUtensorMap tmap,
+                                                            CompressArgs a) {
     using F = Fmt<T>;
     using U = typename F::U;
     using S = typename F::S;
     constexpr int w = F::w;
     constexpr int W = F::W;
+    constexpr int BPW = 32 / LPB;          // blocks per warp
+    constexpr int RPL = VPL * w / 128;     // 128-byte rows per lane
+    constexpr int NCODE = (2 * VPL + 31) / 32;
+    static_assert(RPL >= 1 && NCODE >= 1, "lane geometry");
 
-    extern __shared__ __align__(128) uint8_t smem[];
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
     __shared__ __align__(8) uint64_t bar;
     __shared__ uint32_t s_tile, s_nn, s_mid, s_nraw, s_nesc, s_rec, s_fail;
     __shared__ uint64_t s_excl;
 
+    // the 128-byte swizzle of the tensor copy needs a 1024-byte aligned buffer
+    uint8_t *smem = smem_raw + ((1024u - (smem_addr(smem_raw) & 1023u)) & 1023u);
     const Geometry &g = a.g;
     const uint32_t b = g.b, G = g.G;
-    const CompressSmem L = compress_smem(G, b, w);
-    uint8_t *sm_in = smem + L.in;
-    uint8_t *sm_rec = smem + L.rec;
-    uint8_t *sm_lead = smem + L.lead;
-    U *sm_mu = reinterpret_cast<U *>(smem + L.mu);
+    const CSmem2 L = compress_smem2(G, b, w);
+    uint8_t *buf = smem + L.buf;
+    uint32_t *lut = reinterpret_cast<uint32_t *>(smem + L.lut);
     uint8_t *sm_kind = smem + L.kind;
     uint8_t *sm_req = smem + L.req;
     uint32_t *sm_mk = reinterpret_cast<uint32_t *>(smem + L.mk);
+    U *sm_mu = reinterpret_cast<U *>(smem + L.mu);
     uint32_t *sm_rank = reinterpret_cast<uint32_t *>(smem + L.rank);
     uint32_t *sm_midoff = reinterpret_cast<uint32_t *>(smem + L.midoff);
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
-    // ---- 1. ticket and bulk load of the tile's input ----------------------
+    // ---- 1. ticket, TMA load of the tile ------------------------------------
     if (tid == 0) {
         s_tile = atomicAdd(&a.ws->ticket, 1u);
+        if (SZX_CHECKS && s_tile >= a.g.ntiles) report_bad(a.ws, s_tile, 7);
         s_fail = 0;
         s_nesc = 0;
         mbar_init(&bar, 1);
         fence_mbar_init();
     }
+    build_lut(lut);
     __syncthreads();
     const uint32_t tile = s_tile;
     const uint64_t k0 = (uint64_t)tile * G;
     const uint32_t Gt = (uint32_t)min_u64(G, g.nb - k0);
-    const uint64_t v0 = k0 * b;
-    const uint32_t tile_vals = (uint32_t)min_u64((uint64_t)G * b, g.n - v0);
-    const uint32_t tile_bytes = tile_vals * w;
-    const uint32_t bulk_bytes = tile_bytes & ~15u;
-    if (tid == 0 && bulk_bytes) {
-        mbar_arrive_expect_tx(&bar, bulk_bytes);
-        bulk_g2s(sm_in, a.in + v0 * w, bulk_bytes, &bar);
+    const uint64_t row0 = (uint64_t)tile * 256 * RPL;
+    const bool tma = a.use_tma && row0 < a.rows_full;
+    if (tid == 0 && tma) {
+        mbar_arrive_expect_tx(&bar, 256u * 128u * RPL);
+#pragma unroll
+        for (int i = 0; i < RPL; ++i) {
+            const uint32_t dst = smem_addr(buf + i * 32768);
+            const int y = (int)(row0 + 256 * i);
+            asm volatile(
+                "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
+                "[%4];" ::"r"(dst),
+                "l"(reinterpret_cast<uint64_t>(&tmap)), "r"(0), "r"(y), "r"(smem_addr(&bar))
+                : "memory");
+        }
     }
-    // ragged tail (last tile only): plain loads, then zero the unused words
-    for (uint32_t i = bulk_bytes + tid; i < tile_bytes; i += kThreads) sm_in[i] = a.in[v0 * w + i];
-    for (uint32_t i = tile_bytes + tid; i < G * b * w; i += kThreads) sm_in[i] = 0;
-    if (bulk_bytes && !mbar_wait_bounded(&bar, 0, 1u << 24)) s_fail = 1;
+    if (tma && !mbar_wait_bounded(&bar, 0, a.copy_ns)) s_fail = 1;
+    // rows beyond the fully-covered ones (the input's ragged end, or every row
+    // when the tensor copy is not used): plain loads into the swizzled layout
+    {
+        const uint64_t tile_vals = min_u64((uint64_t)G * b, g.n - k0 * b);
+        const uint64_t first_plain = tma ? min_u64((a.rows_full - row0) * (128 / w), tile_vals) : 0;
+        const uint64_t in0 = k0 * b;
+        for (uint64_t i = first_plain + tid; i < tile_vals; i += kThreads) {
+            const uint32_t byte = (uint32_t)(i * w);
+            const uint32_t row = byte >> 7, chunk = (byte >> 4) & 7u;
+            const uint32_t phys = (row << 7) | ((chunk ^ (row & 7u)) << 4) | (byte & 15u);
+            *reinterpret_cast<U *>(buf + phys) = reinterpret_cast<const U *>(a.in)[in0 + i];
+        }
+    }
     __syncthreads();
-    // (a bulk copy that never completed leaves s_fail set: the tile then
-    // publishes an empty record and the call reports SZX_ERR_TIMEOUT)
 
     const T e = F::from((U)a.e_bits);
 
-    // ---- 2. per-warp block encoding ---------------------------------------
-    for (uint32_t kk = warp; kk < Gt && !s_fail; kk += kWarps) {
-        const uint64_t first = (k0 + kk) * b;
-        const int len = (int)min_u64(b, g.n - first);
-        U *vp = reinterpret_cast<U *>(sm_in) + (size_t)kk * b + lane * VPL;
-        U x[VPL];
-        load_lane<U, VPL>(vp, x);
-        bool valid[VPL];
-#pragma unroll
-        for (int m = 0; m < VPL; ++m) valid[m] = lane * VPL + m < len;
+    // ---- 2. block statistics and encoding (registers) -----------------------
+    const int sub = lane % LPB;
+    const uint32_t blk = (uint32_t)(warp * BPW + lane / LPB);
+    const bool exists = blk < Gt && !s_fail;
+    const uint64_t kg = k0 + blk;
+    const int len = exists ? (int)min_u64(b, g.n - kg * b) : 0;
+    int nvalid = len - sub * VPL;
+    nvalid = nvalid < 0 ? 0 : (nvalid > VPL ? VPL : nvalid);
+    const bool full = nvalid == VPL;
+    const uint32_t lane_row0 = (uint32_t)((warp * 32 + lane) * RPL);
 
-        // block statistics: min / max as order-preserving keys
-        S kmin = std::numeric_limits<S>::max(), kmax = std::numeric_limits<S>::min();
+    auto load_value = [&](int m) -> U {
+        const uint32_t byte = (uint32_t)(m * w);
+        const uint32_t rowi = lane_row0 + (byte >> 7), cb = byte & 127u;
+        const uint32_t phys = (rowi << 7) | ((((cb >> 4) ^ (rowi & 7u))) << 4) | (cb & 15u);
+        return *reinterpret_cast<const U *>(buf + phys);
+    };
+
+    U x[VPL];
+#pragma unroll
+    for (int rr = 0; rr < RPL; ++rr) {
+        const uint32_t rowi = lane_row0 + rr;
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            const uint4 v = *reinterpret_cast<const uint4 *>(buf + (rowi << 7) + ((c ^ (rowi & 7u)) << 4));
+            const U *u = reinterpret_cast<const U *>(&v);
+#pragma unroll
+            for (int k = 0; k < 16 / w; ++k) x[rr * (128 / w) + c * (16 / w) + k] = u[k];
+        }
+    }
+
+    // min / max (NaN and infinities propagate, so one test finds them)
+    S kmn = std::numeric_limits<S>::max(), kmx = std::numeric_limits<S>::min();
+    if constexpr (sizeof(T) == 4) {
+        float lmn = F::from(x[0]), lmx = F::from(x[0]);
+        if (full) {
+#pragma unroll
+            for (int m = 1; m < VPL; ++m) {
+                lmn = min_nan(lmn, F::from(x[m]));
+                lmx = max_nan(lmx, F::from(x[m]));
+            }
+        } else {
+#pragma unroll
+            for (int m = 1; m < VPL; ++m)
+                if (m < nvalid) {
+                    lmn = min_nan(lmn, F::from(x[m]));
+                    lmx = max_nan(lmx, F::from(x[m]));
+                }
+        }
+        if (nvalid > 0) {
+            kmn = F::key(F::bits(lmn));
+            kmx = F::key(F::bits(lmx));
+        }
+    } else {
 #pragma unroll
         for (int m = 0; m < VPL; ++m) {
-            if (valid[m]) {
-                S kx = F::key(x[m]);
-                kmin = kx < kmin ? kx : kmin;
-                kmax = kx > kmax ? kx : kmax;
+            if (m < nvalid) {
+                const S kx = F::key(x[m]);
+                kmn = kx < kmn ? kx : kmn;
+                kmx = kx > kmx ? kx : kmx;
             }
         }
-        kmin = warp_min(kmin);
-        kmax = warp_max(kmax);
-        const bool all_finite = kmin > F::kKeyNegInf && kmax < F::kKeyPosInf;
-        const T mn = F::from(F::unkey(kmin)), mx = F::from(F::unkey(kmax));
-        const T r = F::half(F::sub(mx, mn));
-        const T mu = F::add(mn, r);
+    }
+#pragma unroll
+    for (int d = 1; d < LPB; d <<= 1) {
+        const S omn = __shfl_xor_sync(kFull, kmn, d), omx = __shfl_xor_sync(kFull, kmx, d);
+        kmn = omn < kmn ? omn : kmn;
+        kmx = omx > kmx ? omx : kmx;
+    }
+    // a NaN's key lies above +inf (or, for f64 negative NaNs, below -inf)
+    const bool all_finite = kmn > F::kKeyNegInf && kmn < F::kKeyPosInf && kmx > F::kKeyNegInf &&
+                            kmx < F::kKeyPosInf;
+    const T mn = F::from(F::unkey(kmn)), mx = F::from(F::unkey(kmx));
+    const T r = F::half(F::sub(mx, mn));
+    const T mu = F::add(mn, r);
 
-        int kind = kRaw, req = 0xFF, escalated = 0;
-        uint32_t mk = (uint32_t)len * w;
-        if (all_finite && F::finite(F::bits(r)) && F::finite(F::bits(mu))) {
-            if (within(mx, mu, e) && within(mn, mu, e)) {
-                kind = kConst;
-                mk = 0;
-            } else {
-                // Eq. 3 with sign and exponent always kept
-                int R = F::expo(F::bits(r)) - F::expo(F::bits(e));
-                R = R < 0 ? 0 : (R > F::M ? F::M : R);
-                const int req0 = 1 + F::E + R;
-                U v[VPL];
+    int kind = kConst;
+    if (!exists) kind = 0xFF;
+    else if (!all_finite || !F::finite(F::bits(r)) || !F::finite(F::bits(mu))) kind = kRaw;
+    else if (!(within(mx, mu, e) && within(mn, mu, e))) kind = kNonConst;
+
+    int R = F::expo(F::bits(r)) - F::expo(F::bits(e));
+    R = R < 0 ? 0 : (R > F::M ? F::M : R);
+    const int req0 = 1 + F::E + R;
+    int req = req0;
+
+    // fast pass: truncate, and test every value against e with one rounding
+    bool ok = true;
+    {
+        const int s = (8 - (req & 7)) & 7;
+        const U mask = top_bytes_mask<U>((req + s) >> 3);
 #pragma unroll
-                for (int m = 0; m < VPL; ++m) v[m] = F::bits(F::sub(F::from(x[m]), mu));
-                int rq = req0;
-                for (; rq <= W; ++rq) {
-                    const int s = (8 - (rq & 7)) & 7;
-                    const U mask = top_bytes_mask<U>((rq + s) >> 3);
-                    bool ok = true;
+        for (int m = 0; m < VPL; ++m) {
+            if (full || m < nvalid) {
+                const T xv = F::from(x[m]);
+                const U t = (F::bits(F::sub(xv, mu)) >> s) & mask;
+                const T dp = F::add(F::from((U)(t << s)), mu);
+                ok = ok && fabs(F::sub(xv, dp)) < e;
+                x[m] = t;
+            }
+        }
+    }
+    const uint32_t segmask = (LPB == 32 ? kFull : ((1u << LPB) - 1u)) << (lane & ~(LPB - 1));
+    {
+        const uint32_t bal = __ballot_sync(kFull, ok || kind != kNonConst);
+        ok = (bal & segmask) == segmask;
+    }
+    // exact slow path: ties with e and real failures (reqBits grows, or the
+    // block is stored raw at full width)
+    bool pending = kind == kNonConst && !ok;
+    if (pending && sub == 0) atomicAdd(&a.ws->diag[0], 1u);
+    int rounds = 0;
+    while (__any_sync(kFull, pending)) {
+        if (SZX_CHECKS && ++rounds > 40) {
+            if (lane == 0) report_bad(a.ws, tile, 3);
+            if (pending) kind = kRaw;
+            break;
+        }
+        bool ok2 = true;
+        if (pending) {
+            const int s = (8 - (req & 7)) & 7;
+            const U mask = top_bytes_mask<U>((req + s) >> 3);
 #pragma unroll
-                    for (int m = 0; m < VPL; ++m) {
-                        if (valid[m]) {
-                            const U t = (v[m] >> s) & mask;
-                            const T dp = F::add(F::from((U)(t << s)), mu);
-                            ok = ok && within(F::from(x[m]), dp, e);
-                        }
-                    }
-                    if (__all_sync(kFull, ok)) break;
-                }
-                if (rq <= W) {
-                    kind = kNonConst;
-                    req = rq;
-                    escalated = rq > req0;
-                    const int s = (8 - (rq & 7)) & 7;
-                    const int q = (rq + s) >> 3;
-                    const U mask = top_bytes_mask<U>(q);
-                    const int lmax = q < 3 ? q : 3;
-                    U t[VPL];
-#pragma unroll
-                    for (int m = 0; m < VPL; ++m) t[m] = valid[m] ? (v[m] >> s) & mask : U(0);
-                    U prev = __shfl_up_sync(kFull, t[VPL - 1], 1);
-                    if (lane == 0) prev = 0;
-                    CodeT<VPL> codes = 0;
-                    uint32_t cnt = 0;
-#pragma unroll
-                    for (int m = 0; m < VPL; ++m) {
-                        int l = F::clz(t[m] ^ prev) >> 3;
-                        l = l < lmax ? l : lmax;
-                        if (!valid[m]) l = 0;
-                        codes |= (CodeT<VPL>)l << (2 * m);
-                        cnt += valid[m] ? (uint32_t)(q - l) : 0u;
-                        prev = t[m];
-                    }
-                    put_codes<VPL>(sm_lead + (size_t)kk * (b / 4), codes);
-                    store_lane<U, VPL>(vp, t);
-                    mk = __reduce_add_sync(kFull, cnt);
+            for (int m = 0; m < VPL; ++m) {
+                if (m < nvalid) {
+                    const T xv = F::from(load_value(m));
+                    const U t = (F::bits(F::sub(xv, mu)) >> s) & mask;
+                    ok2 = ok2 && within(xv, F::add(F::from((U)(t << s)), mu), e);
+                    x[m] = t;
                 }
             }
         }
-        if (lane == 0) {
-            sm_kind[kk] = (uint8_t)kind;
-            sm_req[kk] = (uint8_t)req;
-            sm_mk[kk] = mk;
-            sm_mu[kk] = (kind == kRaw) ? U(0) : F::bits(mu);
-            if (escalated) atomicAdd(&s_nesc, 1u);
+        const uint32_t bal = __ballot_sync(kFull, ok2);
+        if (pending) {
+            if ((bal & segmask) == segmask) {
+                pending = false;
+            } else if (++req > W) {
+                kind = kRaw;
+                pending = false;
+            }
         }
+    }
+
+    // identical-leading-byte codes against the previous truncated word
+    const int s = (8 - (req & 7)) & 7;
+    const int q = (req + s) >> 3;
+    const int lmax = q < 3 ? q : 3;
+    uint32_t codes[NCODE];
+#pragma unroll
+    for (int i = 0; i < NCODE; ++i) codes[i] = 0;
+    {
+        U prev = __shfl_up_sync(kFull, x[VPL - 1], 1);
+        if (sub == 0) prev = 0;
+#pragma unroll
+        for (int m = 0; m < VPL; ++m) {
+            int l = F::clz(x[m] ^ prev) >> 3;
+            l = l < lmax ? l : lmax;
+            if (!full && m >= nvalid) l = 0;
+            codes[m >> 4] |= (uint32_t)l << (2 * (m & 15));
+            prev = x[m];
+        }
+    }
+    uint32_t suml = 0;
+#pragma unroll
+    for (int i = 0; i < NCODE; ++i) suml += __popc(codes[i] & 0x55555555u) + 2 * __popc(codes[i] & 0xAAAAAAAAu);
+    uint32_t mk = kind == kNonConst ? (uint32_t)(nvalid * q) - suml : (kind == kRaw ? (uint32_t)nvalid * w : 0u);
+#pragma unroll
+    for (int d = 1; d < LPB; d <<= 1) mk += __shfl_xor_sync(kFull, mk, d);
+
+    if (SZX_CHECKS && exists && sub == 0 && mk > (uint32_t)len * w) report_bad(a.ws, tile, 4);
+    if (exists && sub == 0) {
+        sm_kind[blk] = (uint8_t)kind;
+        sm_req[blk] = kind == kNonConst ? (uint8_t)req : (uint8_t)0xFF;
+        sm_mk[blk] = mk;
+        sm_mu[blk] = kind == kRaw ? U(0) : F::bits(mu);
+        if (kind == kNonConst && req > req0) atomicAdd(&s_nesc, 1u);
     }
     __syncthreads();
 
-    // ---- 3. tile scan: non-constant ranks and mid-byte offsets -------------
+    // ---- 3. clear the buffer for the record; tile scan ---------------------
+    {
+        uint4 *p = reinterpret_cast<uint4 *>(buf);
+        const uint4 z = make_uint4(0, 0, 0, 0);
+        for (uint32_t i = tid; i < L.buf_bytes / 16; i += kThreads) p[i] = z;
+    }
     if (warp == 0) {
         const uint32_t per = (Gt + 31) / 32;
         const uint32_t lo = min(lane * per, Gt), hi = min(lo + per, Gt);
         uint32_t c_nn = 0, c_mid = 0, c_raw = 0;
-        for (uint32_t kk = lo; kk < hi; ++kk) {
-            if (sm_kind[kk] != kConst) {
-                c_nn += 1;
-                c_mid += sm_mk[kk];
-                c_raw += sm_kind[kk] == kRaw;
+        if (!s_fail) {
+            for (uint32_t kk = lo; kk < hi; ++kk) {
+                if (sm_kind[kk] != kConst) {
+                    c_nn += 1;
+                    c_mid += sm_mk[kk];
+                    c_raw += sm_kind[kk] == kRaw;
+                }
             }
         }
         uint32_t t_nn, t_mid, t_raw;
@@ -318,7 +438,7 @@ __global__ void __launch_bounds__(kThreads) compress_kernel(CompressArgs a) {
         for (uint32_t kk = lo; kk < hi; ++kk) {
             sm_rank[kk] = e_nn;
             sm_midoff[kk] = e_mid;
-            if (sm_kind[kk] != kConst) {
+            if (!s_fail && sm_kind[kk] != kConst) {
                 e_nn += 1;
                 e_mid += sm_mk[kk];
             }
@@ -327,118 +447,188 @@ __global__ void __launch_bounds__(kThreads) compress_kernel(CompressArgs a) {
             s_nn = t_nn;
             s_mid = t_mid;
             s_nraw = t_raw;
-            const uint32_t used = t_nn * (b / 4 + 1) + t_mid;
-            s_rec = s_fail ? 0u : (uint32_t)pad16(used);
-            // publish this tile's aggregate so later tiles can look back
+            s_rec = s_fail ? 0u : (uint32_t)pad16((uint64_t)t_nn * (b / 4 + 1) + t_mid);
+            if (SZX_CHECKS && s_rec > record_max_bytes(G, b, w)) {
+                report_bad(a.ws, tile, 2);
+                s_rec = 0;
+            }
             st_release_u64(&a.lookback[tile], kFlagAgg | s_rec);
         }
     }
     __syncthreads();
 
-    // ---- 4. the record in shared memory ------------------------------------
+    // ---- 4. the record ------------------------------------------------------
+    // per-lane counts of values with code <= j (j = 0, 1, 2), packed in
+    // FB-bit fields, and their exclusive scan over the block's lanes.  Every
+    // lane runs this (the shuffles need the whole warp); lanes of constant or
+    // raw blocks contribute nothing.
+    using CntT = std::conditional_t<(LPB * VPL > 1023), unsigned long long, uint32_t>;
+    constexpr int FB = LPB * VPL > 1023 ? 16 : 10;
+    constexpr CntT FM = (CntT(1) << FB) - 1;
+    CntT cnt = 0;
+    if (exists && kind == kNonConst) {
+#pragma unroll
+        for (int i = 0; i < NCODE; ++i) {
+            const int nv = nvalid - 16 * i;
+            const uint32_t vm = nv >= 16 ? 0x55555555u : (nv <= 0 ? 0u : (0x55555555u >> (2 * (16 - nv))));
+            const uint32_t lo = codes[i] & 0x55555555u, hi = (codes[i] >> 1) & 0x55555555u;
+            cnt += (CntT)__popc(~(lo | hi) & vm) | ((CntT)__popc(~hi & vm) << FB) |
+                   ((CntT)__popc(~(lo & hi) & vm) << (2 * FB));
+        }
+    }
+    CntT incl = cnt;
+#pragma unroll
+    for (int d = 1; d < LPB; d <<= 1) {
+        const CntT y = __shfl_up_sync(kFull, incl, d);
+        if (sub >= d) incl += y;
+    }
+    const CntT tot = __shfl_sync(kFull, incl, (lane & ~(LPB - 1)) + LPB - 1);
+    const CntT off = incl - cnt;
+
     const uint32_t nn_t = s_nn;
-    const uint32_t mid_base = nn_t * (b / 4 + 1);
-    if (!s_fail) {
-        for (uint32_t kk = warp; kk < Gt; kk += kWarps) {
-            const int kind = sm_kind[kk];
-            if (kind == kConst) continue;
-            const uint32_t rank = sm_rank[kk];
-            const uint64_t first = (k0 + kk) * b;
-            const int len = (int)min_u64(b, g.n - first);
-            uint8_t *lead_dst = sm_rec + rank * (b / 4);
-            const uint8_t *lead_src = sm_lead + (size_t)kk * (b / 4);
-            for (uint32_t i = lane; i < b / 4; i += 32) lead_dst[i] = kind == kRaw ? 0 : lead_src[i];
-            if (lane == 0) sm_rec[nn_t * (b / 4) + rank] = sm_req[kk];
-            uint8_t *mid = sm_rec + mid_base + sm_midoff[kk];
-            if (kind == kRaw) {
-                const uint8_t *src = sm_in + (size_t)kk * b * w;
-                for (uint32_t i = lane; i < (uint32_t)len * w; i += 32) mid[i] = src[i];
-                continue;
-            }
-            const int rq = sm_req[kk];
-            const int s = (8 - (rq & 7)) & 7;
-            const int q = (rq + s) >> 3;
-            U t[VPL];
-            load_lane<U, VPL>(reinterpret_cast<const U *>(sm_in) + (size_t)kk * b + lane * VPL, t);
-            const CodeT<VPL> codes = get_codes<VPL>(lead_src);
-            int Lm[VPL];
-            bool valid[VPL];
-            typename PlanePack<VPL>::T cnt = 0;
+    uint32_t *words = reinterpret_cast<uint32_t *>(buf);
+    // every record write goes through put(): a self-checked build verifies
+    // that it lands inside the record
+    auto put = [&](uint32_t p, uint32_t run) {
+        if (SZX_CHECKS && (p + 8 > L.buf_bytes || p + 4 > s_rec + 16)) {
+            report_bad(a.ws, tile, 1);
+            return;
+        }
+        or_bytes(words, p, run);
+    };
+    if (exists && kind != kConst) {
+        const uint32_t rank = sm_rank[blk];
+        const uint32_t mbase = nn_t * (b / 4 + 1) + sm_midoff[blk];
+        if (sub == 0) {
+            // the reqBits byte's word may also hold mid bytes: OR it in too
+            const uint32_t p = nn_t * (b / 4) + rank;
+            atomicOr(words + (p >> 2), (kind == kNonConst ? (uint32_t)req : 0xFFu) << (8 * (p & 3u)));
+        }
+        if (kind == kRaw) {
+            // verbatim input bytes, value-major
+            const U *src = reinterpret_cast<const U *>(a.in) + kg * b + sub * VPL;
+            for (int m = 0; m < nvalid; ++m) {
+                const U v = src[m];
+                const uint32_t p = mbase + (uint32_t)(sub * VPL + m) * w;
 #pragma unroll
-            for (int m = 0; m < VPL; ++m) {
-                valid[m] = lane * VPL + m < len;
-                Lm[m] = (int)(codes >> (2 * m)) & 3;
-                if (valid[m]) cnt += PlanePack<VPL>::inc(Lm[m]);
+                for (int h = 0; h < w / 4; ++h) put(p + 4 * h, (uint32_t)(v >> (32 * h)));
             }
-            typename PlanePack<VPL>::T tot;
-            const typename PlanePack<VPL>::T off = warp_exclusive_scan(cnt, &tot);
-            const uint32_t n0 = PlanePack<VPL>::field(tot, 0), n1 = PlanePack<VPL>::field(tot, 1),
-                           n2 = PlanePack<VPL>::field(tot, 2);
-            const uint32_t P[3] = {0u, n0, n0 + n1};
-            const int sparse = q < 3 ? q : 3;
-            for (int j = 0; j < sparse; ++j) {
-                uint32_t pos = P[j] + PlanePack<VPL>::field(off, j);
+        } else {
+            // lead codes: this lane's values are bytes [sub*VPL/4, (sub+1)*VPL/4)
+            if (SZX_CHECKS && (rank + 1) * (b / 4) > nn_t * (b / 4)) report_bad(a.ws, tile, 6);
+            uint8_t *lead = buf + rank * (b / 4) + sub * (VPL / 4);
+            if constexpr (NCODE == 2) {
+                *reinterpret_cast<uint2 *>(lead) = make_uint2(codes[0], codes[1]);
+            } else {
+                *reinterpret_cast<uint32_t *>(lead) = codes[0];
+            }
+            const uint32_t n0 = (uint32_t)(tot & FM), n1 = (uint32_t)((tot >> FB) & FM),
+                           n2 = (uint32_t)((tot >> (2 * FB)) & FM);
+            uint32_t pos0 = mbase + (uint32_t)(off & FM);
+            uint32_t pos1 = mbase + n0 + (uint32_t)((off >> FB) & FM);
+            uint32_t pos2 = mbase + n0 + n1 + (uint32_t)((off >> (2 * FB)) & FM);
+            const uint32_t dense0 = mbase + n0 + n1 + n2 + (uint32_t)sub * VPL;
 #pragma unroll
-                for (int m = 0; m < VPL; ++m) {
-                    if (valid[m] && Lm[m] <= j) mid[pos++] = (uint8_t)byte_of(t[m], j);
+            for (int gq = 0; gq < VPL / 4; ++gq) {
+                // lookup codes: values past the end of a partial block never match
+                uint32_t code8 = (codes[gq >> 2] >> (8 * (gq & 3))) & 0xFFu;
+                uint32_t dense8 = 0;
+                if (!full) {
+                    const int nv = nvalid - 4 * gq;
+                    const uint32_t inval = nv >= 4 ? 0u : (nv <= 0 ? 0xFFu : (0xFFu << (2 * nv)) & 0xFFu);
+                    code8 |= inval;
+                    dense8 = inval;
+                }
+                uint32_t Wd[W / 8];
+                if constexpr (sizeof(T) == 4) {
+                    uint32_t Wq[4];
+                    transpose4((uint32_t)x[4 * gq], (uint32_t)x[4 * gq + 1], (uint32_t)x[4 * gq + 2],
+                               (uint32_t)x[4 * gq + 3], Wq);
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) Wd[j] = Wq[j];
+                } else {
+                    uint32_t Wh[4], Wl[4];
+                    transpose4((uint32_t)(x[4 * gq] >> 32), (uint32_t)(x[4 * gq + 1] >> 32),
+                               (uint32_t)(x[4 * gq + 2] >> 32), (uint32_t)(x[4 * gq + 3] >> 32), Wh);
+                    transpose4((uint32_t)x[4 * gq], (uint32_t)x[4 * gq + 1], (uint32_t)x[4 * gq + 2],
+                               (uint32_t)x[4 * gq + 3], Wl);
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        Wd[j] = Wh[j];
+                        Wd[4 + j] = Wl[j];
+                    }
+                }
+                {
+                    const uint32_t e0 = lut[code8];
+                    put(pos0, prmt(Wd[0], 0, e0));
+                    pos0 += e0 >> 16;
+                    const uint32_t e1 = lut[256 + code8];
+                    put(pos1, prmt(Wd[1], 0, e1));
+                    pos1 += e1 >> 16;
+                }
+                if (q >= 3) {
+                    const uint32_t e2 = lut[512 + code8];
+                    put(pos2, prmt(Wd[2], 0, e2));
+                    pos2 += e2 >> 16;
+                }
+                if (q >= 4) {
+                    const uint32_t sel = full ? 0x3210u : lut[512 + dense8];
+#pragma unroll
+                    for (int j = 3; j < W / 8; ++j) {
+                        if (j < q) put(dense0 + (uint32_t)(j - 3) * len + 4 * gq, prmt(Wd[j], 0, sel));
+                    }
                 }
             }
-            // planes j >= 3 hold every value (L <= 3 <= j)
-            for (int j = 3; j < q; ++j) {
-                uint8_t *plane = mid + n0 + n1 + n2 + (uint32_t)(j - 3) * len + lane * VPL;
-#pragma unroll
-                for (int m = 0; m < VPL; ++m)
-                    if (valid[m]) plane[m] = (uint8_t)byte_of(t[m], j);
-            }
         }
-        // zero pad of the record
-        const uint32_t used = mid_base + s_mid;
-        for (uint32_t i = used + tid; i < s_rec; i += kThreads) sm_rec[i] = 0;
     }
     __syncthreads();
 
     // ---- 5. look-back, index entry, record store ---------------------------
     if (tid == 0) {
-        if (s_fail) atomicOr(&a.ws->err, kErrTimeout);
+        if (s_fail) {
+            atomicOr(&a.ws->err, kErrTmaTimeout);
+            atomicAdd(&a.ws->tma_timeouts, 1u);
+            atomicCAS(&a.ws->first_tma_tile, 0u, tile + 1);
+        }
         uint64_t excl = 0;
-        uint32_t spins = 0;
         bool timed_out = false;
+        const uint64_t t0 = globaltimer_ns();
         for (int64_t j = (int64_t)tile - 1; j >= 0;) {
             const uint64_t wv = ld_acquire_u64(&a.lookback[j]);
             const uint64_t flag = wv & ~kValueMask;
             if (flag == 0) {
-                if (++spins > a.spin_limit) {
+                if (globaltimer_ns() - t0 > a.lookback_ns) {
                     timed_out = true;
                     break;
                 }
-                __nanosleep(32);
+                __nanosleep(64);
                 continue;
             }
             excl += wv & kValueMask;
             if (flag == kFlagPrefix) break;
             --j;
         }
-        if (timed_out) atomicOr(&a.ws->err, kErrTimeout);
+        if (timed_out) {
+            atomicOr(&a.ws->err, kErrTimeout);
+            atomicAdd(&a.ws->lookback_timeouts, 1ull);
+            atomicCAS(&a.ws->first_lb_tile, 0u, tile + 1);
+        }
         st_release_u64(&a.lookback[tile], kFlagPrefix | (excl + s_rec));
         s_excl = excl;
-        uint8_t *idx = a.out + g.off_index;
-        reinterpret_cast<uint64_t *>(idx)[tile] = excl;
+        uint64_t *idx = reinterpret_cast<uint64_t *>(a.out + g.off_index);
+        idx[tile] = excl;
         if (tile == g.ntiles - 1) {
-            const uint64_t rec_total = excl + s_rec;
-            reinterpret_cast<uint64_t *>(idx)[g.ntiles] = rec_total;
-            // zero pads of the fixed sections
+            idx[g.ntiles] = excl + s_rec;
             const uint64_t state_end = g.off_state + (g.nb + 7) / 8;
             for (uint64_t i = state_end; i < g.off_mu; ++i) a.out[i] = 0;
             for (uint64_t i = g.off_mu + g.nb * w; i < g.off_index; ++i) a.out[i] = 0;
             for (uint64_t i = g.off_index + 8 * (g.ntiles + 1); i < g.off_rec; ++i) a.out[i] = 0;
         }
-    }
-    __syncthreads();
-    const uint64_t excl = s_excl;
-    if (tid == 0 && s_rec) {
-        fence_proxy_async_smem();
-        bulk_s2g(a.out + g.off_rec + excl, sm_rec, s_rec);
-        bulk_commit();
+        if (s_rec) {
+            fence_proxy_async_smem();
+            bulk_s2g(a.out + g.off_rec + excl, buf, s_rec);
+            bulk_commit();
+        }
     }
     // state bits and mu values of the tile (fixed positions)
     {
@@ -454,7 +644,6 @@ __global__ void __launch_bounds__(kThreads) compress_kernel(CompressArgs a) {
         U *mu_dst = reinterpret_cast<U *>(a.out + g.off_mu) + k0;
         for (uint32_t i = tid; i < Gt; i += kThreads) mu_dst[i] = sm_mu[i];
     }
-    // counters and completion
     if (tid == 0) {
         atomicAdd(&a.ws->nn, (unsigned long long)s_nn);
         atomicAdd(&a.ws->nraw, (unsigned long long)s_nraw);
@@ -462,14 +651,12 @@ __global__ void __launch_bounds__(kThreads) compress_kernel(CompressArgs a) {
         __threadfence();
         const uint32_t done = atomicAdd(&a.ws->done, 1u);
         if (done == g.ntiles - 1) {
-            // last tile to finish: write the header and the result words
             __threadfence();
             volatile Workspace *ws = a.ws;
             const uint64_t rec_total = reinterpret_cast<volatile uint64_t *>(a.out + g.off_index)[g.ntiles];
             const uint64_t total = g.off_rec + rec_total;
-            uint8_t *h = a.out;
-            uint32_t *h32 = reinterpret_cast<uint32_t *>(h);
-            uint64_t *h64 = reinterpret_cast<uint64_t *>(h);
+            uint32_t *h32 = reinterpret_cast<uint32_t *>(a.out);
+            uint64_t *h64 = reinterpret_cast<uint64_t *>(a.out);
             h32[0] = kMagic;
             h32[1] = kVersion | (a.dtype << 8);
             h32[2] = b;
@@ -480,7 +667,7 @@ __global__ void __launch_bounds__(kThreads) compress_kernel(CompressArgs a) {
             h64[5] = ws->nraw;
             h64[6] = ws->nesc;
             h64[7] = total;
-            const uint64_t status = (ws->err & kErrTimeout) ? 6ull : 0ull;
+            const uint64_t status = (ws->err & (kErrTimeout | kErrTmaTimeout)) ? 6ull : (ws->err & kErrInternal) ? 5ull : 0ull;
             ws->result[0] = total;
             ws->result[1] = status;
             if (a.d_result) {
@@ -488,55 +675,94 @@ __global__ void __launch_bounds__(kThreads) compress_kernel(CompressArgs a) {
                 a.d_result[1] = status;
             }
         }
-    }
-    // the bulk store must have read the record before the CTA's shared memory
-    // is released; a bulk load that timed out gets one more bounded wait
-    if (tid == 0) {
         if (s_rec) bulk_wait_read_all();
-        if (s_fail) mbar_wait_bounded(&bar, 0, 1u << 24);
     }
 }
 
 // ---------------------------------------------------------------------------
+// host side
 
-template <typename T, int VPL>
-static cudaError_t launch_t(const CompressArgs &a, cudaStream_t stream) {
-    const CompressSmem L = compress_smem(a.g.G, a.g.b, Fmt<T>::w);
-    auto kern = compress_kernel<T, VPL>;
+namespace {
+
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    });
+    return fn;
+}
+
+template <typename T, int LPB, int VPL>
+cudaError_t launch_t(const CUtensorMap &tm, const CompressArgs &a, cudaStream_t stream) {
+    const CSmem2 L = compress_smem2(a.g.G, a.g.b, Fmt<T>::w);
+    auto kern = compress_kernel<T, LPB, VPL>;
     cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total);
     if (err != cudaSuccess) return err;
-    kern<<<(unsigned)a.g.ntiles, kThreads, L.total, stream>>>(a);
+    kern<<<(unsigned)a.g.ntiles, kThreads, L.total, stream>>>(tm, a);
     return cudaGetLastError();
 }
 
-template <typename T>
-static cudaError_t launch_vpl(const CompressArgs &a, cudaStream_t stream) {
-    switch (a.g.b) {
-        case 32: return launch_t<T, 1>(a, stream);
-        case 64: return launch_t<T, 2>(a, stream);
-        case 128: return launch_t<T, 4>(a, stream);
-        case 256: return launch_t<T, 8>(a, stream);
-        case 512: return launch_t<T, 16>(a, stream);
-        case 1024: return launch_t<T, 32>(a, stream);
-        default: return cudaErrorInvalidValue;
-    }
-}
+}  // namespace
 
 cudaError_t launch_compress(const void *in, uint64_t n, int dtype, uint64_t e_bits, uint32_t block,
                             void *out, uint64_t ws_offset, uint64_t *d_result, cudaStream_t stream) {
     CompressArgs a;
+    const uint32_t w = dtype == 0 ? 4 : 8;
     a.in = static_cast<const uint8_t *>(in);
     a.out = static_cast<uint8_t *>(out);
-    a.g = make_geometry(n, block, dtype == 0 ? 4 : 8);
+    a.g = make_geometry(n, block, w);
     a.ws = reinterpret_cast<Workspace *>(a.out + ws_offset);
     a.lookback = reinterpret_cast<uint64_t *>(a.out + ws_offset + kWsHeader);
     a.d_result = d_result;
     a.e_bits = e_bits;
     a.dtype = (uint32_t)dtype;
-    a.spin_limit = 1u << 22;
+    a.lookback_ns = 1000ull * wait_limit_from_env("SZX_LOOKBACK_US", 1000000u);
+    a.copy_ns = 1000ull * wait_limit_from_env("SZX_COPY_US", 1000000u);
+    a.rows_full = n * w / 128;
+    CUtensorMap tm;
+    std::memset(&tm, 0, sizeof(tm));
+    a.use_tma = 0;
+    if (a.rows_full > 0 && a.rows_full < (1ull << 31)) {
+        auto enc = tensor_map_encoder();
+        if (enc) {
+            cuuint64_t dims[2] = {32, a.rows_full};
+            cuuint64_t strides[1] = {128};
+            cuuint32_t box[2] = {32, 256};
+            cuuint32_t estr[2] = {1, 1};
+            CUresult r = enc(&tm, CU_TENSOR_MAP_DATA_TYPE_UINT32, 2, const_cast<void *>(in), dims, strides, box,
+                             estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+            a.use_tma = r == CUDA_SUCCESS ? 1u : 0u;
+        }
+    }
     cudaError_t err = cudaMemsetAsync(a.ws, 0, workspace_bytes(a.g.ntiles), stream);
     if (err != cudaSuccess) return err;
-    return dtype == 0 ? launch_vpl<float>(a, stream) : launch_vpl<double>(a, stream);
+    if (dtype == 0) {
+        switch (block) {
+            case 32: return launch_t<float, 1, 32>(tm, a, stream);
+            case 64: return launch_t<float, 2, 32>(tm, a, stream);
+            case 128: return launch_t<float, 4, 32>(tm, a, stream);
+            case 256: return launch_t<float, 8, 32>(tm, a, stream);
+            case 512: return launch_t<float, 16, 32>(tm, a, stream);
+            case 1024: return launch_t<float, 32, 32>(tm, a, stream);
+        }
+    } else {
+        switch (block) {
+            case 32: return launch_t<double, 2, 16>(tm, a, stream);
+            case 64: return launch_t<double, 4, 16>(tm, a, stream);
+            case 128: return launch_t<double, 8, 16>(tm, a, stream);
+            case 256: return launch_t<double, 16, 16>(tm, a, stream);
+            case 512: return launch_t<double, 32, 16>(tm, a, stream);
+            case 1024: return launch_t<double, 32, 32>(tm, a, stream);
+        }
+    }
+    return cudaErrorInvalidValue;
 }
 
 }  // namespace szx

@@ -34,6 +34,7 @@ struct DecompressArgs {
     uint64_t rec_total;
     uint32_t dtype;
     uint32_t check_header;  // re-check the stream header on the device
+    uint64_t copy_ns;       // wall-time limit of the record copy wait
     uint64_t total_bytes;
 };
 
@@ -160,7 +161,7 @@ __global__ void __launch_bounds__(kThreads) decompress_kernel(DecompressArgs a) 
     }
     __syncthreads();
     const uint32_t size = s_size;
-    if (size && !mbar_wait_bounded(&bar, 0, 1u << 24)) s_bad = 2;
+    if (size && !mbar_wait_bounded(&bar, 0, a.copy_ns)) s_bad = 2;
     __syncthreads();
 
     // ---- 2. ranks, mid-byte counts, offsets -------------------------------
@@ -251,7 +252,7 @@ __global__ void __launch_bounds__(kThreads) decompress_kernel(DecompressArgs a) 
     __syncthreads();
     if (s_bad) {
         if (tid == 0) flag_status(a.status, s_bad & 2 ? 6u : 3u);
-        if (tid == 0 && size && (s_bad & 2)) mbar_wait_bounded(&bar, 0, 1u << 24);
+        if (tid == 0 && size && (s_bad & 2)) mbar_wait_bounded(&bar, 0, a.copy_ns);
         return;
     }
 
@@ -394,6 +395,7 @@ cudaError_t launch_decompress(const void *in, uint64_t in_bytes, uint64_t total_
     a.dtype = (uint32_t)dtype;
     a.check_header = check_header ? 1u : 0u;
     a.total_bytes = total_bytes;
+    a.copy_ns = 1000ull * wait_limit_from_env("SZX_COPY_US", 1000000u);
     return dtype == 0 ? launch_vpl<float>(a, stream) : launch_vpl<double>(a, stream);
 }
 

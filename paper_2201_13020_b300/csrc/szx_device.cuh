@@ -21,7 +21,9 @@ constexpr int kThreads = kWarps * 32;
 enum : uint8_t { kConst = 0, kNonConst = 1, kRaw = 2 };
 
 // Device error bits (compress workspace and decompress status word).
-enum : uint32_t { kErrTimeout = 1u, kErrCorrupt = 2u };
+// kErrTimeout: the offset look-back gave up; kErrTmaTimeout: a bulk or
+// tensor copy did not complete within its wait limit.
+enum : uint32_t { kErrTimeout = 1u, kErrCorrupt = 2u, kErrTmaTimeout = 4u, kErrInternal = 8u };
 
 // ---------------------------------------------------------------------------
 // IEEE formats
@@ -173,13 +175,34 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
     return ok != 0;
 }
 
-// Bounded wait on an mbarrier phase; returns false if the limit ran out.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, uint32_t limit) {
-    for (uint32_t i = 0; i < limit; ++i) {
-        if (mbar_try_wait(bar, parity)) return true;
-        if (i > 64) __nanosleep(64);
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// One probe of an mbarrier phase; the thread may be suspended for up to about
+// 1 us (suspend-time hint) while the phase is pending.
+__device__ __forceinline__ bool mbar_try_wait_hint(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity), "r"(1000u)
+        : "memory");
+    return ok != 0;
+}
+
+// Wait on an mbarrier phase for at most limit_ns of wall time; returns false
+// if the deadline passed first.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, uint64_t limit_ns) {
+    const uint64_t t0 = globaltimer_ns();
+    while (!mbar_try_wait_hint(bar, parity)) {
+        if (globaltimer_ns() - t0 > limit_ns) return false;
     }
-    return false;
+    return true;
 }
 
 // global -> shared bulk copy, completion counted on the mbarrier.
@@ -259,13 +282,18 @@ struct Workspace {
     uint32_t ticket;  // next tile ticket (tiles are processed in ticket order)
     uint32_t done;    // tiles finished
     uint32_t err;     // kErr* bits
-    uint32_t pad0;
+    uint32_t tma_timeouts;  // tiles whose input copy did not complete
     unsigned long long nn, nraw, nesc;
     unsigned long long result[2];  // stream bytes, status (written by the last tile)
-    unsigned long long pad1;
+    unsigned long long lookback_timeouts;  // tiles whose look-back gave up
+    uint32_t first_tma_tile;  // 1 + the first tile whose copy timed out (0: none)
+    uint32_t first_lb_tile;   // 1 + the first tile whose look-back timed out
+    uint32_t first_bad_tile;  // 1 + the first tile that failed a self-check
+    uint32_t bad_code;        // which self-check failed
+    uint32_t diag[12];
     // followed by ntiles look-back words
 };
-constexpr uint64_t kWsHeader = 64;
+constexpr uint64_t kWsHeader = 128;
 static_assert(sizeof(Workspace) == kWsHeader, "workspace header layout");
 
 // look-back word: 2-bit flag | 62-bit record byte count

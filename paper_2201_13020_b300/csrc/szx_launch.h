@@ -6,6 +6,10 @@
 
 namespace szx {
 
+// Limit (microseconds) of a bounded device-side wait: the environment variable
+// `name` (a positive integer) if set, else `fallback`.  Read on every launch.
+uint32_t wait_limit_from_env(const char *name, uint32_t fallback);
+
 // Enqueue the compression of n values (dtype 0 = f32, 1 = f64) with bound bits
 // e_bits into the stream at out; the workspace starts ws_offset bytes into
 // out.  Optionally writes {stream bytes, status} to d_result on completion.

@@ -255,3 +255,25 @@ def test_invalid_arguments_are_rejected():
     with pytest.raises(szx.SzxError) as ei:
         szx.compress(misaligned, 1e-3)
     assert ei.value.status == 1
+
+
+@pytest.mark.parametrize("dtype", [np.float32, np.float64])
+@pytest.mark.parametrize("block", [32, 128, 256, 1024])
+def test_mixed_block_kinds_within_a_warp(dtype, block):
+    """Constant, non-constant and raw blocks interleaved block by block, so that
+    the lanes of one warp take different paths (a warp holds several blocks)."""
+    rng = np.random.default_rng(block)
+    nb = 3 * max(8, 32768 // (block * np.dtype(dtype).itemsize)) + 3
+    x = np.cumsum(rng.normal(size=nb * block)).astype(dtype)
+    kinds = rng.integers(0, 4, size=nb)
+    for k in range(nb):
+        sl = slice(k * block, (k + 1) * block)
+        if kinds[k] == 0:
+            x[sl] = x[k * block]                      # constant
+        elif kinds[k] == 1:
+            x[k * block + 3] = np.nan                 # raw
+        elif kinds[k] == 2:
+            x[sl] = x[k * block] + rng.normal(size=block) * 1e-9  # constant within e
+    x = x[: nb * block - block // 3]                  # ragged last block
+    finite = x[np.isfinite(x)]
+    assert_parity(x, 1e-3 * float(finite.max() - finite.min()), block)
