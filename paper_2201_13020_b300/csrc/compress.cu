@@ -1,38 +1,45 @@
 // compress.cu -- single-pass SZx compression kernel for sm_103a.
 //
-// One CTA (8 warps) compresses one tile of G consecutive blocks (32 KiB of
-// input) into the tile's record.  Tiles are taken in ticket order, so the
-// decoupled look-back over tile record sizes -- the device-wide exclusive scan
-// that places each record (the prefix scan of Sec. V-B) -- only ever waits on
-// tiles that are already running.
+// Persistent, warp-specialised CTAs take tiles of G consecutive blocks (32
+// KiB of input) by ticket and turn each into the tile's record.  Tickets are
+// processed in the order they were taken, so the decoupled look-back over
+// tile record sizes -- the device-wide exclusive scan that places each record
+// (the prefix scan of Sec. V-B) -- only ever waits on tiles that are running
+// or done.
 //
 // Work layout: every lane owns 128 contiguous input bytes (32 f32 or 16 f64
-// values); a block of b values is handled by LPB = b / VPL adjacent lanes
-// (4 lanes for f32, b = 128), so the per-block bookkeeping is spread over few
-// lanes and the serial previous-value dependency stays inside a lane except
-// at lane boundaries.
+// values); a block of b values is handled by LPB = b / VPL adjacent lanes (4
+// lanes for f32, b = 128).  The serial previous-value dependency stays inside
+// a lane except at lane boundaries.
 //
-// Per tile:
-//   1. one thread loads the tile with a 2-D TMA tensor copy (rows of 128 B,
-//      128-byte swizzle), so each lane reads its row from shared memory
-//      without bank conflicts;
-//   2. block statistics (Algorithm 1): NaN-propagating min/max per lane,
+// Per CTA: a ring of three tile buffers and three roles.  A producer warp
+// takes tickets and copies tiles in with the TMA unit (2-D tensor copy, rows
+// of 128 B, 128-byte swizzle, so that each lane reads its row without bank
+// conflicts); eight consumer warps encode a tile and build its record in
+// place; a storer warp places and stores records.  The roles hand stages to
+// each other through mbarriers (full / ready / empty), so encoding never waits
+// for a look-back or a store.  Per tile:
+//   1. block statistics (Algorithm 1): NaN-propagating min/max per lane,
 //      reduced over the block's lanes with shuffles; mu, r, the exact constant
-//      test, reqBits (Eq. 3), the Eq. 4 shift and truncation with a per-value
-//      bound check (a fast test; an exact slow path re-checks a block that
-//      fails it and raises reqBits while a value exceeds e), identical
-//      leading-byte codes against the previous value and the block's mid-byte
-//      count; the truncated words stay in registers;
-//   3. warp 0 scans the tile's blocks (non-constant rank, mid-byte offset)
-//      and publishes the tile's record size; the input buffer is cleared and
+//      test, reqBits (Eq. 3), the Eq. 4 shift and truncation.  The per-value
+//      bound check is skipped when a block-level bound proves it passes
+//      (see bound_check_needed); otherwise a fast test runs and an exact slow
+//      path re-checks a block that fails it, raising reqBits while a value
+//      exceeds e.  Then the identical-leading-byte codes against the previous
+//      value and the block's mid-byte count; the truncated words stay in
+//      registers;
+//   2. warp 0 scans the tile's blocks (non-constant rank, mid-byte offset)
+//      and publishes the tile's record size; the tile buffer is cleared and
 //      reused for the record;
-//   4. lanes write lead codes, reqBits bytes and the mid-byte planes (plane j
+//   3. lanes write lead codes, reqBits bytes and the mid-byte planes (plane j
 //      = byte j of every value whose code is <= j, ascending index): a 4x4
 //      byte transpose of four values gives their byte-j word, a 256-entry
 //      table compacts the selected bytes, and shared-memory OR writes place the
 //      run at its byte offset;
-//   5. one thread finishes the look-back, writes the tile index entry and
-//      bulk-stores the record (TMA, cp.async.bulk) to its offset.
+//   4. the storer finishes the look-back, writes the tile index entry, the
+//      tile's state bits and mu values, and bulk-stores the record (TMA,
+//      cp.async.bulk) to its offset; once the store has read the buffer, the
+//      producer refills it with the CTA's next tile.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -58,12 +65,38 @@ struct CompressArgs {
     uint64_t *d_result;
     Geometry g;
     uint64_t e_bits;
-    uint64_t rows_full;  // 128-byte input rows fully inside the input
-    uint32_t dtype;
+    uint64_t rows_full;    // 128-byte input rows fully inside the input
     uint64_t lookback_ns;  // wall-time limit of the look-back wait
-    uint64_t copy_ns;      // wall-time limit of the tile copy wait
+    uint64_t copy_ns;      // wall-time limit of a tile copy wait
+    uint32_t dtype;
     uint32_t use_tma;
 };
+
+// ---------------------------------------------------------------------------
+// compaction table: for plane j in 0..2 and the 2-bit codes of four values
+// (value k at bits 2k), entry = byte-permute selector taking, in order, the
+// bytes of the values whose code is <= j (unused nibbles select zero), plus
+// the number of such values << 16.  Built at compile time.
+
+struct PlaneLut {
+    uint32_t v[768];
+};
+constexpr PlaneLut make_plane_lut() {
+    PlaneLut t{};
+    for (uint32_t i = 0; i < 768; ++i) {
+        const uint32_t j = i >> 8, code = i & 255u;
+        uint32_t sel = 0x4444u, cnt = 0;
+        for (uint32_t k = 0; k < 4; ++k) {
+            if (((code >> (2 * k)) & 3u) <= j) {
+                sel = (sel & ~(0xFu << (4 * cnt))) | (k << (4 * cnt));
+                ++cnt;
+            }
+        }
+        t.v[i] = sel | (cnt << 16);
+    }
+    return t;
+}
+__device__ const PlaneLut kPlaneLut = make_plane_lut();
 
 // ---------------------------------------------------------------------------
 // small device helpers
@@ -81,13 +114,13 @@ __device__ __forceinline__ float max_nan(float a, float b) {
 
 __device__ __forceinline__ uint32_t prmt(uint32_t a, uint32_t b, uint32_t s) { return __byte_perm(a, b, s); }
 
-// OR a run of up to 4 bytes (little-endian in `run`) into the zero-initialised
-// byte buffer at byte offset p.  The buffer has 4 bytes of slack at the end.
-__device__ __forceinline__ void or_bytes(uint32_t *words, uint32_t p, uint32_t run) {
+// OR a run of cnt <= 4 bytes (little-endian in `run`) into the zero-initialised
+// byte buffer at byte offset p.
+__device__ __forceinline__ void or_bytes(uint32_t *words, uint32_t p, uint32_t run, uint32_t cnt) {
     const uint32_t sh = (p & 3u) * 8u;
     uint32_t *wp = words + (p >> 2);
     atomicOr(wp, run << sh);
-    atomicOr(wp + 1, __funnelshift_l(run, 0u, sh));
+    if ((p & 3u) + cnt > 4u) atomicOr(wp + 1, __funnelshift_l(run, 0u, sh));
 }
 
 // Record a failed self-check (first tile and check id).
@@ -107,189 +140,87 @@ __device__ __forceinline__ void transpose4(uint32_t t0, uint32_t t1, uint32_t t2
     W[0] = prmt(b, d, 0x7632);
 }
 
-// Compaction table: for plane j in 0..2 and the 2-bit codes of four values
-// (value k at bits 2k), entry = byte-permute selector taking the bytes of the
-// values with code <= j in order (unused nibbles select zero) | count << 16.
-__device__ __forceinline__ void build_lut(uint32_t *lut) {
-    for (uint32_t i = threadIdx.x; i < 3 * 256; i += blockDim.x) {
-        const uint32_t j = i >> 8, code = i & 255u;
-        uint32_t sel = 0x4444u, cnt = 0;
-        for (uint32_t k = 0; k < 4; ++k) {
-            if (((code >> (2 * k)) & 3u) <= j) {
-                sel = (sel & ~(0xFu << (4 * cnt))) | (k << (4 * cnt));
-                ++cnt;
-            }
-        }
-        lut[i] = sel | (cnt << 16);
-    }
+// Effective exponent: the unbiased exponent, with subnormals and zero at the
+// minimum normal exponent (their spacing is 2^(emin - M)).
+template <typename T>
+__device__ __forceinline__ int eff_expo(typename Fmt<T>::U u) {
+    using F = Fmt<T>;
+    const int f = (int)((u >> F::M) & ((1u << F::E) - 1));
+    return (f ? f : 1) - F::bias;
 }
 
-// Shared-memory layout of the compress kernel.
-struct CSmem2 {
-    uint32_t buf, buf_bytes, lut, kind, req, mk, mu, rank, midoff, total;
-};
-__host__ __device__ inline CSmem2 compress_smem2(uint32_t G, uint32_t b, uint32_t w) {
-    CSmem2 s;
-    uint32_t o = 0;
-    auto take = [&](uint32_t bytes, uint32_t align) {
-        o = (o + align - 1) & ~(align - 1);
-        const uint32_t at = o;
-        o += bytes;
-        return at;
-    };
-    const uint32_t tile = G * b * w;
-    const uint32_t rec = record_max_bytes(G, b, w);
-    s.buf_bytes = ((tile > rec ? tile : rec) + 16 + 15) & ~15u;
-    s.buf = take(s.buf_bytes, 1024);
-    s.lut = take(3 * 256 * 4, 16);
-    s.kind = take(G, 16);
-    s.req = take(G, 16);
-    s.mk = take(4 * G, 16);
-    s.mu = take(w * G, 16);
-    s.rank = take(4 * G, 16);
-    s.midoff = take(4 * G, 16);
-    s.total = ((o + 1023) & ~1023u) + 1024;  // + slack to realign the dynamic base
-    return s;
+// Does the per-value check |d - RN(v' + mu)| <= e need to run at reqBits =
+// 1 + E + R?  It can be skipped when a block-level bound proves every value
+// passes (the result is then the same as running it):
+//   For d in [mn, mx], v = RN(d - mu) has |v| <= max(|RN(mn - mu)|,
+//   |RN(mx - mu)|), so its effective exponent is at most P.  Truncating v to R
+//   mantissa bits drops less than 2^(p(v) - R) minus one unit of v, and the
+//   rounding of v adds at most half a unit, so |v' + mu - d| < 2^(P - R) = C.
+//   Then |v' + mu| < B + C with B = max(|mn|, |mx|), so both lie below
+//   2^(K + 2), K = max(p(B), P - R), where half a spacing is at most
+//   2^(K - M) = U; hence |d - d'| < C + U.  If C + U <= e, every value passes.
+// The comparison is done exactly in integers on e's significand.  K is kept
+// three binades below the largest exponent so that nothing overflows.
+template <typename T>
+__device__ __forceinline__ bool bound_check_needed(T mn, T mx, T mu, int R, typename Fmt<T>::U e_bits) {
+    using F = Fmt<T>;
+    using U = typename F::U;
+    const int P = max(eff_expo<T>(F::bits(F::sub(mx, mu))), eff_expo<T>(F::bits(F::sub(mn, mu))));
+    const U babs = max(F::bits(mn) & ~(U(1) << (F::W - 1)), F::bits(mx) & ~(U(1) << (F::W - 1)));
+    const int a = P - R;
+    const int K = max(eff_expo<T>(babs), a);
+    if (K > (1 << (F::E - 1)) - 1 - 3) return true;  // near overflow: check
+    const int ee = eff_expo<T>(e_bits);
+    const U efield = (e_bits >> F::M) & ((U(1) << F::E) - 1);
+    const U me = (e_bits & ((U(1) << F::M) - 1)) | (efield ? (U(1) << F::M) : U(0));  // e = me * 2^(ee - M)
+    if (me == 0) return true;
+    const int A = a - ee + F::M, V = K - F::M - ee + F::M;  // C = 2^A, U = 2^V in units of 2^(ee - M)
+    if (A > F::M + 1 || V > F::M + 1) return true;
+    const unsigned long long m = (unsigned long long)me;
+    bool fits;
+    if (A >= 0 && V >= 0) fits = (1ull << A) + (1ull << V) <= m;
+    else if (A >= 0) fits = (1ull << A) < m;
+    else if (V >= 0) fits = (1ull << V) < m;
+    else fits = true;  // both below one unit of e's significand, and me >= 1
+    return !fits;
 }
 
-template <typename T, int LPB, int VPL>
-__global__ void __launch_bounds__(kThreads, (VPL * sizeof(T) > 128) ? 1 : (sizeof(T) == 8 ? 3 : 4)) compress_kernel(const __grid_constant__ CUtensorMap tmap,
-                                                            CompressArgs a) {
+// ---------------------------------------------------------------------------
+// per-lane encoding (step 1); FULL: every value of the lane is valid
+
+template <typename T, int LPB, int VPL, bool FULL>
+__device__ __forceinline__ void encode_lane(typename Fmt<T>::U (&x)[VPL], uint32_t (&codes)[(2 * VPL + 31) / 32],
+                                            int &kind, int &req, int &req0, T &mu_out, uint32_t &mk_out,
+                                            const uint8_t *buf, uint32_t lane_row0, int nvalid, bool exists, T e,
+                                            uint64_t e_bits, Workspace *ws, uint32_t tile) {
     using F = Fmt<T>;
     using U = typename F::U;
     using S = typename F::S;
     constexpr int w = F::w;
     constexpr int W = F::W;
-    constexpr int BPW = 32 / LPB;          // blocks per warp
-    constexpr int RPL = VPL * w / 128;     // 128-byte rows per lane
     constexpr int NCODE = (2 * VPL + 31) / 32;
-    static_assert(RPL >= 1 && NCODE >= 1, "lane geometry");
-
-    extern __shared__ __align__(1024) uint8_t smem_raw[];
-    __shared__ __align__(8) uint64_t bar;
-    __shared__ uint32_t s_tile, s_nn, s_mid, s_nraw, s_nesc, s_rec, s_fail;
-    __shared__ uint64_t s_excl;
-
-    // the 128-byte swizzle of the tensor copy needs a 1024-byte aligned buffer
-    uint8_t *smem = smem_raw + ((1024u - (smem_addr(smem_raw) & 1023u)) & 1023u);
-    const Geometry &g = a.g;
-    const uint32_t b = g.b, G = g.G;
-    const CSmem2 L = compress_smem2(G, b, w);
-    uint8_t *buf = smem + L.buf;
-    uint32_t *lut = reinterpret_cast<uint32_t *>(smem + L.lut);
-    uint8_t *sm_kind = smem + L.kind;
-    uint8_t *sm_req = smem + L.req;
-    uint32_t *sm_mk = reinterpret_cast<uint32_t *>(smem + L.mk);
-    U *sm_mu = reinterpret_cast<U *>(smem + L.mu);
-    uint32_t *sm_rank = reinterpret_cast<uint32_t *>(smem + L.rank);
-    uint32_t *sm_midoff = reinterpret_cast<uint32_t *>(smem + L.midoff);
-
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-
-    // ---- 1. ticket, TMA load of the tile ------------------------------------
-    if (tid == 0) {
-        s_tile = atomicAdd(&a.ws->ticket, 1u);
-        if (SZX_CHECKS && s_tile >= a.g.ntiles) report_bad(a.ws, s_tile, 7);
-        s_fail = 0;
-        s_nesc = 0;
-        mbar_init(&bar, 1);
-        fence_mbar_init();
-    }
-    build_lut(lut);
-    __syncthreads();
-    const uint32_t tile = s_tile;
-    const uint64_t k0 = (uint64_t)tile * G;
-    const uint32_t Gt = (uint32_t)min_u64(G, g.nb - k0);
-    const uint64_t row0 = (uint64_t)tile * 256 * RPL;
-    const bool tma = a.use_tma && row0 < a.rows_full;
-    if (tid == 0 && tma) {
-        mbar_arrive_expect_tx(&bar, 256u * 128u * RPL);
-#pragma unroll
-        for (int i = 0; i < RPL; ++i) {
-            const uint32_t dst = smem_addr(buf + i * 32768);
-            const int y = (int)(row0 + 256 * i);
-            asm volatile(
-                "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
-                "[%4];" ::"r"(dst),
-                "l"(reinterpret_cast<uint64_t>(&tmap)), "r"(0), "r"(y), "r"(smem_addr(&bar))
-                : "memory");
-        }
-    }
-    if (tma && !mbar_wait_bounded(&bar, 0, a.copy_ns)) s_fail = 1;
-    // rows beyond the fully-covered ones (the input's ragged end, or every row
-    // when the tensor copy is not used): plain loads into the swizzled layout
-    {
-        const uint64_t tile_vals = min_u64((uint64_t)G * b, g.n - k0 * b);
-        const uint64_t first_plain = tma ? min_u64((a.rows_full - row0) * (128 / w), tile_vals) : 0;
-        const uint64_t in0 = k0 * b;
-        for (uint64_t i = first_plain + tid; i < tile_vals; i += kThreads) {
-            const uint32_t byte = (uint32_t)(i * w);
-            const uint32_t row = byte >> 7, chunk = (byte >> 4) & 7u;
-            const uint32_t phys = (row << 7) | ((chunk ^ (row & 7u)) << 4) | (byte & 15u);
-            *reinterpret_cast<U *>(buf + phys) = reinterpret_cast<const U *>(a.in)[in0 + i];
-        }
-    }
-    __syncthreads();
-
-    const T e = F::from((U)a.e_bits);
-
-    // ---- 2. block statistics and encoding (registers) -----------------------
+    const int lane = lane_id();
     const int sub = lane % LPB;
-    const uint32_t blk = (uint32_t)(warp * BPW + lane / LPB);
-    const bool exists = blk < Gt && !s_fail;
-    const uint64_t kg = k0 + blk;
-    const int len = exists ? (int)min_u64(b, g.n - kg * b) : 0;
-    int nvalid = len - sub * VPL;
-    nvalid = nvalid < 0 ? 0 : (nvalid > VPL ? VPL : nvalid);
-    const bool full = nvalid == VPL;
-    const uint32_t lane_row0 = (uint32_t)((warp * 32 + lane) * RPL);
-
-    auto load_value = [&](int m) -> U {
-        const uint32_t byte = (uint32_t)(m * w);
-        const uint32_t rowi = lane_row0 + (byte >> 7), cb = byte & 127u;
-        const uint32_t phys = (rowi << 7) | ((((cb >> 4) ^ (rowi & 7u))) << 4) | (cb & 15u);
-        return *reinterpret_cast<const U *>(buf + phys);
-    };
-
-    U x[VPL];
-#pragma unroll
-    for (int rr = 0; rr < RPL; ++rr) {
-        const uint32_t rowi = lane_row0 + rr;
-#pragma unroll
-        for (int c = 0; c < 8; ++c) {
-            const uint4 v = *reinterpret_cast<const uint4 *>(buf + (rowi << 7) + ((c ^ (rowi & 7u)) << 4));
-            const U *u = reinterpret_cast<const U *>(&v);
-#pragma unroll
-            for (int k = 0; k < 16 / w; ++k) x[rr * (128 / w) + c * (16 / w) + k] = u[k];
-        }
-    }
 
     // min / max (NaN and infinities propagate, so one test finds them)
     S kmn = std::numeric_limits<S>::max(), kmx = std::numeric_limits<S>::min();
     if constexpr (sizeof(T) == 4) {
         float lmn = F::from(x[0]), lmx = F::from(x[0]);
-        if (full) {
 #pragma unroll
-            for (int m = 1; m < VPL; ++m) {
+        for (int m = 1; m < VPL; ++m) {
+            if (FULL || m < nvalid) {
                 lmn = min_nan(lmn, F::from(x[m]));
                 lmx = max_nan(lmx, F::from(x[m]));
             }
-        } else {
-#pragma unroll
-            for (int m = 1; m < VPL; ++m)
-                if (m < nvalid) {
-                    lmn = min_nan(lmn, F::from(x[m]));
-                    lmx = max_nan(lmx, F::from(x[m]));
-                }
         }
-        if (nvalid > 0) {
+        if (FULL || nvalid > 0) {
             kmn = F::key(F::bits(lmn));
             kmx = F::key(F::bits(lmx));
         }
     } else {
 #pragma unroll
         for (int m = 0; m < VPL; ++m) {
-            if (m < nvalid) {
+            if (FULL || m < nvalid) {
                 const S kx = F::key(x[m]);
                 kmn = kx < kmn ? kx : kmn;
                 kmx = kx > kmx ? kx : kmx;
@@ -308,31 +239,39 @@ __global__ void __launch_bounds__(kThreads, (VPL * sizeof(T) > 128) ? 1 : (sizeo
     const T mn = F::from(F::unkey(kmn)), mx = F::from(F::unkey(kmx));
     const T r = F::half(F::sub(mx, mn));
     const T mu = F::add(mn, r);
+    mu_out = mu;
 
-    int kind = kConst;
+    kind = kConst;
     if (!exists) kind = 0xFF;
     else if (!all_finite || !F::finite(F::bits(r)) || !F::finite(F::bits(mu))) kind = kRaw;
     else if (!(within(mx, mu, e) && within(mn, mu, e))) kind = kNonConst;
 
     int R = F::expo(F::bits(r)) - F::expo(F::bits(e));
     R = R < 0 ? 0 : (R > F::M ? F::M : R);
-    const int req0 = 1 + F::E + R;
-    int req = req0;
+    req0 = 1 + F::E + R;
+    req = req0;
+    const bool check = kind == kNonConst && bound_check_needed<T>(mn, mx, mu, R, (U)e_bits);
 
-    // fast pass: truncate, and test every value against e with one rounding
+    // truncation; with `check`, a fast test of every value (one rounding)
     bool ok = true;
     {
         const int s = (8 - (req & 7)) & 7;
         const U mask = top_bytes_mask<U>((req + s) >> 3);
+        if (check) {
 #pragma unroll
-        for (int m = 0; m < VPL; ++m) {
-            if (full || m < nvalid) {
-                const T xv = F::from(x[m]);
-                const U t = (F::bits(F::sub(xv, mu)) >> s) & mask;
-                const T dp = F::add(F::from((U)(t << s)), mu);
-                ok = ok && fabs(F::sub(xv, dp)) < e;
-                x[m] = t;
+            for (int m = 0; m < VPL; ++m) {
+                if (FULL || m < nvalid) {
+                    const T xv = F::from(x[m]);
+                    const U t = (F::bits(F::sub(xv, mu)) >> s) & mask;
+                    const T dp = F::add(F::from((U)(t << s)), mu);
+                    ok = ok && fabs(F::sub(xv, dp)) < e;
+                    x[m] = t;
+                }
             }
+        } else {
+#pragma unroll
+            for (int m = 0; m < VPL; ++m)
+                if (FULL || m < nvalid) x[m] = (F::bits(F::sub(F::from(x[m]), mu)) >> s) & mask;
         }
     }
     const uint32_t segmask = (LPB == 32 ? kFull : ((1u << LPB) - 1u)) << (lane & ~(LPB - 1));
@@ -343,11 +282,11 @@ __global__ void __launch_bounds__(kThreads, (VPL * sizeof(T) > 128) ? 1 : (sizeo
     // exact slow path: ties with e and real failures (reqBits grows, or the
     // block is stored raw at full width)
     bool pending = kind == kNonConst && !ok;
-    if (pending && sub == 0) atomicAdd(&a.ws->diag[0], 1u);
+    if (pending && sub == 0) atomicAdd(&ws->diag[0], 1u);
     int rounds = 0;
     while (__any_sync(kFull, pending)) {
         if (SZX_CHECKS && ++rounds > 40) {
-            if (lane == 0) report_bad(a.ws, tile, 3);
+            if (lane == 0) report_bad(ws, tile, 3);
             if (pending) kind = kRaw;
             break;
         }
@@ -358,7 +297,10 @@ __global__ void __launch_bounds__(kThreads, (VPL * sizeof(T) > 128) ? 1 : (sizeo
 #pragma unroll
             for (int m = 0; m < VPL; ++m) {
                 if (m < nvalid) {
-                    const T xv = F::from(load_value(m));
+                    const uint32_t byte = (uint32_t)(m * w);
+                    const uint32_t rowi = lane_row0 + (byte >> 7), cb = byte & 127u;
+                    const uint32_t phys = (rowi << 7) | ((((cb >> 4) ^ (rowi & 7u))) << 4) | (cb & 15u);
+                    const T xv = F::from(*reinterpret_cast<const U *>(buf + phys));
                     const U t = (F::bits(F::sub(xv, mu)) >> s) & mask;
                     ok2 = ok2 && within(xv, F::add(F::from((U)(t << s)), mu), e);
                     x[m] = t;
@@ -380,7 +322,6 @@ __global__ void __launch_bounds__(kThreads, (VPL * sizeof(T) > 128) ? 1 : (sizeo
     const int s = (8 - (req & 7)) & 7;
     const int q = (req + s) >> 3;
     const int lmax = q < 3 ? q : 3;
-    uint32_t codes[NCODE];
 #pragma unroll
     for (int i = 0; i < NCODE; ++i) codes[i] = 0;
     {
@@ -390,8 +331,8 @@ __global__ void __launch_bounds__(kThreads, (VPL * sizeof(T) > 128) ? 1 : (sizeo
         for (int m = 0; m < VPL; ++m) {
             int l = F::clz(x[m] ^ prev) >> 3;
             l = l < lmax ? l : lmax;
-            if (!full && m >= nvalid) l = 0;
-            codes[m >> 4] |= (uint32_t)l << (2 * (m & 15));
+            if (!FULL && m >= nvalid) l = 0;
+            codes[m >> 4] += (uint32_t)l << (2 * (m & 15));
             prev = x[m];
         }
     }
@@ -401,28 +342,392 @@ __global__ void __launch_bounds__(kThreads, (VPL * sizeof(T) > 128) ? 1 : (sizeo
     uint32_t mk = kind == kNonConst ? (uint32_t)(nvalid * q) - suml : (kind == kRaw ? (uint32_t)nvalid * w : 0u);
 #pragma unroll
     for (int d = 1; d < LPB; d <<= 1) mk += __shfl_xor_sync(kFull, mk, d);
+    mk_out = mk;
+}
 
-    if (SZX_CHECKS && exists && sub == 0 && mk > (uint32_t)len * w) report_bad(a.ws, tile, 4);
-    if (exists && sub == 0) {
-        sm_kind[blk] = (uint8_t)kind;
-        sm_req[blk] = kind == kNonConst ? (uint8_t)req : (uint8_t)0xFF;
-        sm_mk[blk] = mk;
-        sm_mu[blk] = kind == kRaw ? U(0) : F::bits(mu);
-        if (kind == kNonConst && req > req0) atomicAdd(&s_nesc, 1u);
+// Shared-memory layout of the compress kernel: kStages tile buffers (each
+// later reused for its tile's record), per-stage block metadata, the table.
+constexpr int kStages = 3;
+constexpr int kConsumerWarps = 8;
+constexpr int kConsumers = kConsumerWarps * 32;
+constexpr int kProducerWarp = kConsumerWarps;
+constexpr int kStorerWarp = kConsumerWarps + 1;
+constexpr int kCThreads = kConsumers + 64;
+static_assert(kConsumers == kThreads, "a tile is laid out over 8 warps");
+
+struct CSmem {
+    uint32_t buf[kStages], buf_bytes;
+    uint32_t meta[kStages], m_kind, m_req, m_mk, m_mu, m_rank, m_midoff;
+    uint32_t lut, total;
+};
+__host__ __device__ inline CSmem compress_smem(uint32_t G, uint32_t b, uint32_t w) {
+    CSmem s;
+    uint32_t o = 0;
+    auto take = [&](uint32_t bytes, uint32_t align) {
+        o = (o + align - 1) & ~(align - 1);
+        const uint32_t at = o;
+        o += bytes;
+        return at;
+    };
+    const uint32_t tile = G * b * w;
+    const uint32_t rec = record_max_bytes(G, b, w);
+    s.buf_bytes = ((tile > rec ? tile : rec) + 16 + 15) & ~15u;
+    for (int i = 0; i < kStages; ++i) s.buf[i] = take(s.buf_bytes, 1024);
+    // one metadata block per stage
+    uint32_t m = 0;
+    auto mtake = [&](uint32_t bytes) {
+        m = (m + 15) & ~15u;
+        const uint32_t at = m;
+        m += bytes;
+        return at;
+    };
+    s.m_kind = mtake(G);
+    s.m_req = mtake(G);
+    s.m_mk = mtake(4 * G);
+    s.m_mu = mtake(w * G);
+    s.m_rank = mtake(4 * G);
+    s.m_midoff = mtake(4 * G);
+    for (int i = 0; i < kStages; ++i) s.meta[i] = take(m, 16);
+    s.lut = take(3 * 256 * 4, 16);
+    s.total = ((o + 1023) & ~1023u) + 1024;  // + slack to realign the dynamic base
+    return s;
+}
+
+__device__ __forceinline__ void consumer_sync() { asm volatile("bar.sync 1, %0;" ::"n"(kConsumers) : "memory"); }
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile(
+        "{\n\t.reg .b64 st;\n\t"
+        "mbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(smem_addr(bar))
+        : "memory");
+}
+
+// ---------------------------------------------------------------------------
+
+template <typename T, int LPB, int VPL>
+__global__ void __launch_bounds__(kCThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
+    compress_kernel(const __grid_constant__ CUtensorMap tmap, CompressArgs a) {
+    using F = Fmt<T>;
+    using U = typename F::U;
+    constexpr int w = F::w;
+    constexpr int W = F::W;
+    constexpr int BPW = 32 / LPB;       // blocks per warp
+    constexpr int RPL = VPL * w / 128;  // 128-byte rows per lane
+    constexpr int NCODE = (2 * VPL + 31) / 32;
+    static_assert(RPL >= 1 && NCODE >= 1, "lane geometry");
+
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    // full: tile copied in; ready: record written; empty: record stored
+    __shared__ __align__(8) uint64_t full[kStages], ready[kStages], empty[kStages];
+    __shared__ uint32_t st_tile[kStages], st_nn[kStages], st_mid[kStages], st_nraw[kStages], st_nesc[kStages],
+        st_rec[kStages], st_fail[kStages];
+    __shared__ uint32_t s_abort;
+
+    // the 128-byte swizzle of the tensor copy needs 1024-byte aligned buffers
+    uint8_t *smem = smem_raw + ((1024u - (smem_addr(smem_raw) & 1023u)) & 1023u);
+    const Geometry &g = a.g;
+    const uint32_t b = g.b, G = g.G;
+    const CSmem L = compress_smem(G, b, w);
+    uint32_t *lut = reinterpret_cast<uint32_t *>(smem + L.lut);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+
+    {
+        const uint4 *src = reinterpret_cast<const uint4 *>(kPlaneLut.v);
+        uint4 *dst = reinterpret_cast<uint4 *>(lut);
+        for (int i = tid; i < 768 / 4; i += kCThreads) dst[i] = src[i];
+    }
+    if (tid == 0) {
+        for (int i = 0; i < kStages; ++i) {
+            mbar_init(&full[i], 1);
+            mbar_init(&ready[i], kConsumers);
+            mbar_init(&empty[i], 1);
+        }
+        fence_mbar_init();
+        s_abort = 0;
+        for (int i = 0; i < kStages; ++i) {
+            st_tile[i] = 0xFFFFFFFFu;
+            st_nn[i] = st_mid[i] = st_nraw[i] = st_nesc[i] = st_rec[i] = st_fail[i] = 0;
+        }
     }
     __syncthreads();
 
-    // ---- 3. clear the buffer for the record; tile scan ---------------------
-    {
-        uint4 *p = reinterpret_cast<uint4 *>(buf);
-        const uint4 z = make_uint4(0, 0, 0, 0);
-        for (uint32_t i = tid; i < L.buf_bytes / 16; i += kThreads) p[i] = z;
+    if (warp == kProducerWarp) {
+        // ---- producer: tickets and tile copies into the stage ring ---------
+        if (lane != 0) return;
+        // per stage: is the last phase a copy (then it may still be in flight
+        // when the producer is done), and its phase index
+        bool copy_last[kStages] = {};
+        uint32_t copy_phase[kStages] = {};
+        for (uint32_t it = 0;; ++it) {
+            const int st = (int)(it % kStages);
+            const uint32_t k = it / kStages;
+            if (it >= kStages && !mbar_wait_bounded(&empty[st], (k - 1) & 1u, a.lookback_ns + a.copy_ns)) {
+                atomicOr(&a.ws->err, kErrTimeout);
+                break;
+            }
+            const uint32_t t = atomicAdd(&a.ws->ticket, 1u);
+            st_tile[st] = t;
+            st_fail[st] = 0;
+            st_nesc[st] = 0;
+            const uint64_t row0 = (uint64_t)t * 256 * RPL;
+            if (t < g.ntiles && a.use_tma && row0 < a.rows_full) {
+                mbar_arrive_expect_tx(&full[st], 256u * 128u * RPL);
+#pragma unroll
+                for (int i = 0; i < RPL; ++i) {
+                    const uint32_t dst = smem_addr(smem + L.buf[st] + i * 32768);
+                    const int y = (int)(row0 + 256 * i);
+                    asm volatile(
+                        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, "
+                        "{%2, %3}], [%4];" ::"r"(dst),
+                        "l"(reinterpret_cast<uint64_t>(&tmap)), "r"(0), "r"(y), "r"(smem_addr(&full[st]))
+                        : "memory");
+                }
+                copy_last[st] = true;
+                copy_phase[st] = k;
+            } else {
+                // a later phase on this stage implies its earlier copy was consumed
+                mbar_arrive(&full[st]);
+                copy_last[st] = false;
+            }
+            if (t >= g.ntiles) break;
+        }
+        // do not leave while a copy may still be writing into shared memory
+        for (int st = 0; st < kStages; ++st)
+            if (copy_last[st]) mbar_wait_bounded(&full[st], copy_phase[st] & 1u, a.copy_ns);
+        return;
     }
-    if (warp == 0) {
-        const uint32_t per = (Gt + 31) / 32;
-        const uint32_t lo = min(lane * per, Gt), hi = min(lo + per, Gt);
-        uint32_t c_nn = 0, c_mid = 0, c_raw = 0;
-        if (!s_fail) {
+
+    if (warp == kStorerWarp) {
+        // ---- storer: look-back, index entry, record store, state and mu ----
+        for (uint32_t it = 0;; ++it) {
+            const int st = (int)(it % kStages);
+            const uint32_t k = it / kStages;
+            if (!mbar_wait_bounded(&ready[st], k & 1u, a.lookback_ns + 4 * a.copy_ns)) {
+                if (lane == 0) atomicOr(&a.ws->err, kErrTimeout);
+                break;
+            }
+            const uint32_t tile = st_tile[st];
+            if (tile >= g.ntiles) break;
+            const uint8_t *meta = smem + L.meta[st];
+            const uint8_t *m_kind = meta + L.m_kind;
+            const U *m_mu = reinterpret_cast<const U *>(meta + L.m_mu);
+            const uint32_t rec_bytes = st_rec[st];
+            const uint64_t k0 = (uint64_t)tile * G;
+            const uint32_t Gt = (uint32_t)min_u64(G, g.nb - k0);
+            // warp-parallel decoupled look-back: 32 predecessors per probe,
+            // lane i looking at tile - 1 - i; stop at the nearest inclusive
+            // prefix, adding the aggregates in between
+            uint64_t excl = 0;
+            bool timed_out = false;
+            {
+                const uint64_t t0 = globaltimer_ns();
+                int64_t base = (int64_t)tile - 1;
+                while (base >= 0) {
+                    const int64_t j = base - lane;
+                    const uint64_t wv = j >= 0 ? ld_acquire_u64(&a.lookback[j]) : kFlagPrefix;
+                    const uint64_t flag = wv & ~kValueMask;
+                    const uint32_t pre = __ballot_sync(kFull, flag == kFlagPrefix);
+                    const uint32_t inv = __ballot_sync(kFull, flag == 0);
+                    const int first_p = pre ? __ffs(pre) - 1 : 32;
+                    const uint32_t need = first_p >= 31 ? kFull : ((2u << first_p) - 1u);
+                    if (inv & need) {
+                        // one lane's clock decides, so the warp stays converged
+                        if (__shfl_sync(kFull, (int)(globaltimer_ns() - t0 > a.lookback_ns), 0)) {
+                            timed_out = true;
+                            break;
+                        }
+                        __nanosleep(32);
+                        continue;
+                    }
+                    uint64_t v = lane <= first_p ? (wv & kValueMask) : 0ull;
+#pragma unroll
+                    for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(kFull, v, d);
+                    excl += v;
+                    if (first_p < 32) break;
+                    base -= 32;
+                }
+            }
+            if (lane == 0) {
+                if (st_fail[st]) {
+                    atomicOr(&a.ws->err, kErrTmaTimeout);
+                    atomicAdd(&a.ws->tma_timeouts, 1u);
+                    atomicCAS(&a.ws->first_tma_tile, 0u, tile + 1);
+                }
+                if (timed_out) {
+                    atomicOr(&a.ws->err, kErrTimeout);
+                    atomicAdd(&a.ws->lookback_timeouts, 1ull);
+                    atomicCAS(&a.ws->first_lb_tile, 0u, tile + 1);
+                }
+                st_release_u64(&a.lookback[tile], kFlagPrefix | (excl + rec_bytes));
+                uint64_t *idx = reinterpret_cast<uint64_t *>(a.out + g.off_index);
+                idx[tile] = excl;
+                if (tile == g.ntiles - 1) {
+                    idx[g.ntiles] = excl + rec_bytes;
+                    const uint64_t state_end = g.off_state + (g.nb + 7) / 8;
+                    for (uint64_t i = state_end; i < g.off_mu; ++i) a.out[i] = 0;
+                    for (uint64_t i = g.off_mu + g.nb * w; i < g.off_index; ++i) a.out[i] = 0;
+                    for (uint64_t i = g.off_index + 8 * (g.ntiles + 1); i < g.off_rec; ++i) a.out[i] = 0;
+                }
+                if (rec_bytes) {
+                    fence_proxy_async_smem();
+                    bulk_s2g(a.out + g.off_rec + excl, smem + L.buf[st], rec_bytes);
+                    bulk_commit();
+                }
+                atomicAdd(&a.ws->nn, (unsigned long long)st_nn[st]);
+                atomicAdd(&a.ws->nraw, (unsigned long long)st_nraw[st]);
+                atomicAdd(&a.ws->nesc, (unsigned long long)st_nesc[st]);
+            }
+            // state bits and mu values of the tile (fixed positions)
+            {
+                uint8_t *state = a.out + g.off_state + (size_t)k0 / 8;
+                for (uint32_t i = lane; i < (Gt + 7) / 8; i += 32) {
+                    uint32_t byte = 0;
+                    for (int j = 0; j < 8; ++j) {
+                        const uint32_t kk = i * 8 + j;
+                        if (kk < Gt && m_kind[kk] != kConst) byte |= 1u << j;
+                    }
+                    state[i] = (uint8_t)byte;
+                }
+                U *mu_dst = reinterpret_cast<U *>(a.out + g.off_mu) + k0;
+                for (uint32_t i = lane; i < Gt; i += 32) mu_dst[i] = m_mu[i];
+            }
+            __syncwarp();
+            if (lane == 0) {
+                // the buffer is free once the store has read it
+                if (rec_bytes) bulk_wait_read_all();
+                mbar_arrive(&empty[st]);
+                __threadfence();
+                const uint32_t done = atomicAdd(&a.ws->done, 1u);
+                if (done == g.ntiles - 1) {
+                    __threadfence();
+                    volatile Workspace *ws = a.ws;
+                    const uint64_t rec_total = reinterpret_cast<volatile uint64_t *>(a.out + g.off_index)[g.ntiles];
+                    const uint64_t total = g.off_rec + rec_total;
+                    uint32_t *h32 = reinterpret_cast<uint32_t *>(a.out);
+                    uint64_t *h64 = reinterpret_cast<uint64_t *>(a.out);
+                    h32[0] = kMagic;
+                    h32[1] = kVersion | (a.dtype << 8);
+                    h32[2] = b;
+                    h32[3] = G;
+                    h64[2] = g.n;
+                    h64[3] = a.e_bits;
+                    h64[4] = ws->nn;
+                    h64[5] = ws->nraw;
+                    h64[6] = ws->nesc;
+                    h64[7] = total;
+                    const uint64_t status = (ws->err & (kErrTimeout | kErrTmaTimeout)) ? 6ull
+                                            : (ws->err & kErrInternal)                 ? 5ull
+                                                                                       : 0ull;
+                    ws->result[0] = total;
+                    ws->result[1] = status;
+                    if (a.d_result) {
+                        a.d_result[0] = total;
+                        a.d_result[1] = status;
+                    }
+                }
+            }
+            __syncwarp();
+        }
+        return;
+    }
+
+    // ---- consumers (warps 0..7): encode tiles into records ------------------
+    const T e = F::from((U)a.e_bits);
+    for (uint32_t it = 0;; ++it) {
+        const int st = (int)(it % kStages);
+        const uint32_t k = it / kStages;
+        if (!mbar_wait_bounded(&full[st], k & 1u, a.copy_ns)) s_abort = 1;
+        consumer_sync();
+        const uint32_t tile = st_tile[st];
+        if (s_abort || tile >= g.ntiles) {
+            // hand the stage to the storer (it stops on the same tile), and stop
+            if (s_abort && tid == 0) st_tile[st] = 0xFFFFFFFFu;
+            consumer_sync();
+            mbar_arrive(&ready[st]);
+            if (s_abort && tid == 0) atomicOr(&a.ws->err, kErrTmaTimeout);
+            break;
+        }
+        uint8_t *buf = smem + L.buf[st];
+        uint8_t *meta = smem + L.meta[st];
+        uint8_t *sm_kind = meta + L.m_kind;
+        uint8_t *sm_req = meta + L.m_req;
+        uint32_t *sm_mk = reinterpret_cast<uint32_t *>(meta + L.m_mk);
+        U *sm_mu = reinterpret_cast<U *>(meta + L.m_mu);
+        uint32_t *sm_rank = reinterpret_cast<uint32_t *>(meta + L.m_rank);
+        uint32_t *sm_midoff = reinterpret_cast<uint32_t *>(meta + L.m_midoff);
+        const uint64_t k0 = (uint64_t)tile * G;
+        const uint32_t Gt = (uint32_t)min_u64(G, g.nb - k0);
+        const uint64_t row0 = (uint64_t)tile * 256 * RPL;
+        const bool tma = a.use_tma && row0 < a.rows_full;
+        // rows beyond the fully-covered ones (the input's ragged end, or every
+        // row when the tensor copy is not used): plain loads, swizzled layout
+        {
+            const uint64_t tile_vals = min_u64((uint64_t)G * b, g.n - k0 * b);
+            const uint64_t first_plain = tma ? min_u64((a.rows_full - row0) * (128 / w), tile_vals) : 0;
+            const uint64_t in0 = k0 * b;
+            for (uint64_t i = first_plain + tid; i < tile_vals; i += kConsumers) {
+                const uint32_t byte = (uint32_t)(i * w);
+                const uint32_t row = byte >> 7, chunk = (byte >> 4) & 7u;
+                const uint32_t phys = (row << 7) | ((chunk ^ (row & 7u)) << 4) | (byte & 15u);
+                *reinterpret_cast<U *>(buf + phys) = reinterpret_cast<const U *>(a.in)[in0 + i];
+            }
+            if (first_plain < tile_vals) consumer_sync();
+        }
+
+        // ---- 1. block statistics and encoding (registers) -------------------
+        const int sub = lane % LPB;
+        const uint32_t blk = (uint32_t)(warp * BPW + lane / LPB);
+        const bool exists = blk < Gt;
+        const uint64_t kg = k0 + blk;
+        const int len = exists ? (int)min_u64(b, g.n - kg * b) : 0;
+        int nvalid = len - sub * VPL;
+        nvalid = nvalid < 0 ? 0 : (nvalid > VPL ? VPL : nvalid);
+        const bool full_lane = nvalid == VPL;
+        const uint32_t lane_row0 = (uint32_t)((warp * 32 + lane) * RPL);
+
+        U x[VPL];
+#pragma unroll
+        for (int rr = 0; rr < RPL; ++rr) {
+            const uint32_t rowi = lane_row0 + rr;
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+                const uint4 v = *reinterpret_cast<const uint4 *>(buf + (rowi << 7) + ((c ^ (rowi & 7u)) << 4));
+                const U *u = reinterpret_cast<const U *>(&v);
+#pragma unroll
+                for (int kk = 0; kk < 16 / w; ++kk) x[rr * (128 / w) + c * (16 / w) + kk] = u[kk];
+            }
+        }
+        uint32_t codes[NCODE];
+        int kind, req, req0;
+        T mu;
+        uint32_t mk;
+        if (__all_sync(kFull, full_lane)) {
+            encode_lane<T, LPB, VPL, true>(x, codes, kind, req, req0, mu, mk, buf, lane_row0, nvalid, exists, e,
+                                           a.e_bits, a.ws, tile);
+        } else {
+            encode_lane<T, LPB, VPL, false>(x, codes, kind, req, req0, mu, mk, buf, lane_row0, nvalid, exists, e,
+                                            a.e_bits, a.ws, tile);
+        }
+        if (SZX_CHECKS && exists && sub == 0 && mk > (uint32_t)len * w) report_bad(a.ws, tile, 4);
+        if (exists && sub == 0) {
+            sm_kind[blk] = (uint8_t)kind;
+            sm_req[blk] = kind == kNonConst ? (uint8_t)req : (uint8_t)0xFF;
+            sm_mk[blk] = mk;
+            sm_mu[blk] = kind == kRaw ? U(0) : F::bits(mu);
+            if (kind == kNonConst && req > req0) atomicAdd(&st_nesc[st], 1u);
+        }
+        consumer_sync();
+
+        // ---- 2. clear the buffer for the record; tile scan -----------------
+        {
+            uint4 *p = reinterpret_cast<uint4 *>(buf);
+            const uint4 z = make_uint4(0, 0, 0, 0);
+            for (uint32_t i = tid; i < L.buf_bytes / 16; i += kConsumers) p[i] = z;
+        }
+        if (warp == 0) {
+            const uint32_t per = (Gt + 31) / 32;
+            const uint32_t lo = min(lane * per, Gt), hi = min(lo + per, Gt);
+            uint32_t c_nn = 0, c_mid = 0, c_raw = 0;
             for (uint32_t kk = lo; kk < hi; ++kk) {
                 if (sm_kind[kk] != kConst) {
                     c_nn += 1;
@@ -430,252 +735,165 @@ __global__ void __launch_bounds__(kThreads, (VPL * sizeof(T) > 128) ? 1 : (sizeo
                     c_raw += sm_kind[kk] == kRaw;
                 }
             }
-        }
-        uint32_t t_nn, t_mid, t_raw;
-        uint32_t e_nn = warp_exclusive_scan(c_nn, &t_nn);
-        uint32_t e_mid = warp_exclusive_scan(c_mid, &t_mid);
-        warp_exclusive_scan(c_raw, &t_raw);
-        for (uint32_t kk = lo; kk < hi; ++kk) {
-            sm_rank[kk] = e_nn;
-            sm_midoff[kk] = e_mid;
-            if (!s_fail && sm_kind[kk] != kConst) {
-                e_nn += 1;
-                e_mid += sm_mk[kk];
+            uint32_t t_nn, t_mid, t_raw;
+            uint32_t e_nn = warp_exclusive_scan(c_nn, &t_nn);
+            uint32_t e_mid = warp_exclusive_scan(c_mid, &t_mid);
+            warp_exclusive_scan(c_raw, &t_raw);
+            for (uint32_t kk = lo; kk < hi; ++kk) {
+                sm_rank[kk] = e_nn;
+                sm_midoff[kk] = e_mid;
+                if (sm_kind[kk] != kConst) {
+                    e_nn += 1;
+                    e_mid += sm_mk[kk];
+                }
+            }
+            if (lane == 0) {
+                uint32_t rec = (uint32_t)pad16((uint64_t)t_nn * (b / 4 + 1) + t_mid);
+                if (SZX_CHECKS && rec > record_max_bytes(G, b, w)) {
+                    report_bad(a.ws, tile, 2);
+                    rec = 0;
+                }
+                st_nn[st] = t_nn;
+                st_mid[st] = t_mid;
+                st_nraw[st] = t_raw;
+                st_rec[st] = rec;
+                st_release_u64(&a.lookback[tile], kFlagAgg | rec);
             }
         }
-        if (lane == 0) {
-            s_nn = t_nn;
-            s_mid = t_mid;
-            s_nraw = t_raw;
-            s_rec = s_fail ? 0u : (uint32_t)pad16((uint64_t)t_nn * (b / 4 + 1) + t_mid);
-            if (SZX_CHECKS && s_rec > record_max_bytes(G, b, w)) {
-                report_bad(a.ws, tile, 2);
-                s_rec = 0;
-            }
-            st_release_u64(&a.lookback[tile], kFlagAgg | s_rec);
-        }
-    }
-    __syncthreads();
 
-    // ---- 4. the record ------------------------------------------------------
-    // per-lane counts of values with code <= j (j = 0, 1, 2), packed in
-    // FB-bit fields, and their exclusive scan over the block's lanes.  Every
-    // lane runs this (the shuffles need the whole warp); lanes of constant or
-    // raw blocks contribute nothing.
-    using CntT = std::conditional_t<(LPB * VPL > 1023), unsigned long long, uint32_t>;
-    constexpr int FB = LPB * VPL > 1023 ? 16 : 10;
-    constexpr CntT FM = (CntT(1) << FB) - 1;
-    CntT cnt = 0;
-    if (exists && kind == kNonConst) {
+        // per-lane counts of values with code <= j (j = 0, 1, 2), packed in
+        // FB-bit fields, and their exclusive scan over the block's lanes.
+        // Every lane runs this (the shuffles need the whole warp); lanes of
+        // constant or raw blocks contribute nothing.
+        using CntT = std::conditional_t<(LPB * VPL > 1023), unsigned long long, uint32_t>;
+        constexpr int FB = LPB * VPL > 1023 ? 16 : 10;
+        constexpr CntT FM = (CntT(1) << FB) - 1;
+        CntT cnt = 0;
+        if (exists && kind == kNonConst) {
 #pragma unroll
-        for (int i = 0; i < NCODE; ++i) {
-            const int nv = nvalid - 16 * i;
-            const uint32_t vm = nv >= 16 ? 0x55555555u : (nv <= 0 ? 0u : (0x55555555u >> (2 * (16 - nv))));
-            const uint32_t lo = codes[i] & 0x55555555u, hi = (codes[i] >> 1) & 0x55555555u;
-            cnt += (CntT)__popc(~(lo | hi) & vm) | ((CntT)__popc(~hi & vm) << FB) |
-                   ((CntT)__popc(~(lo & hi) & vm) << (2 * FB));
-        }
-    }
-    CntT incl = cnt;
-#pragma unroll
-    for (int d = 1; d < LPB; d <<= 1) {
-        const CntT y = __shfl_up_sync(kFull, incl, d);
-        if (sub >= d) incl += y;
-    }
-    const CntT tot = __shfl_sync(kFull, incl, (lane & ~(LPB - 1)) + LPB - 1);
-    const CntT off = incl - cnt;
-
-    const uint32_t nn_t = s_nn;
-    uint32_t *words = reinterpret_cast<uint32_t *>(buf);
-    // every record write goes through put(): a self-checked build verifies
-    // that it lands inside the record
-    auto put = [&](uint32_t p, uint32_t run) {
-        if (SZX_CHECKS && (p + 8 > L.buf_bytes || p + 4 > s_rec + 16)) {
-            report_bad(a.ws, tile, 1);
-            return;
-        }
-        or_bytes(words, p, run);
-    };
-    if (exists && kind != kConst) {
-        const uint32_t rank = sm_rank[blk];
-        const uint32_t mbase = nn_t * (b / 4 + 1) + sm_midoff[blk];
-        if (sub == 0) {
-            // the reqBits byte's word may also hold mid bytes: OR it in too
-            const uint32_t p = nn_t * (b / 4) + rank;
-            atomicOr(words + (p >> 2), (kind == kNonConst ? (uint32_t)req : 0xFFu) << (8 * (p & 3u)));
-        }
-        if (kind == kRaw) {
-            // verbatim input bytes, value-major
-            const U *src = reinterpret_cast<const U *>(a.in) + kg * b + sub * VPL;
-            for (int m = 0; m < nvalid; ++m) {
-                const U v = src[m];
-                const uint32_t p = mbase + (uint32_t)(sub * VPL + m) * w;
-#pragma unroll
-                for (int h = 0; h < w / 4; ++h) put(p + 4 * h, (uint32_t)(v >> (32 * h)));
+            for (int i = 0; i < NCODE; ++i) {
+                const int nv = nvalid - 16 * i;
+                const uint32_t vm = nv >= 16 ? 0x55555555u : (nv <= 0 ? 0u : (0x55555555u >> (2 * (16 - nv))));
+                const uint32_t lo = codes[i] & 0x55555555u, hi = (codes[i] >> 1) & 0x55555555u;
+                cnt += (CntT)__popc(~(lo | hi) & vm) | ((CntT)__popc(~hi & vm) << FB) |
+                       ((CntT)__popc(~(lo & hi) & vm) << (2 * FB));
             }
-        } else {
-            // lead codes: this lane's values are bytes [sub*VPL/4, (sub+1)*VPL/4)
-            if (SZX_CHECKS && (rank + 1) * (b / 4) > nn_t * (b / 4)) report_bad(a.ws, tile, 6);
-            uint8_t *lead = buf + rank * (b / 4) + sub * (VPL / 4);
-            if constexpr (NCODE == 2) {
-                *reinterpret_cast<uint2 *>(lead) = make_uint2(codes[0], codes[1]);
+        }
+        CntT incl = cnt;
+#pragma unroll
+        for (int d = 1; d < LPB; d <<= 1) {
+            const CntT y = __shfl_up_sync(kFull, incl, d);
+            if (sub >= d) incl += y;
+        }
+        const CntT tot = __shfl_sync(kFull, incl, (lane & ~(LPB - 1)) + LPB - 1);
+        const CntT off = incl - cnt;
+        consumer_sync();
+
+        // ---- 3. the record --------------------------------------------------
+        const uint32_t nn_t = st_nn[st];
+        const uint32_t rec_bytes = st_rec[st];
+        uint32_t *words = reinterpret_cast<uint32_t *>(buf);
+        // every record write goes through put(): a self-checked build verifies
+        // that it lands inside the record
+        auto put = [&](uint32_t p, uint32_t run, uint32_t c) {
+            if (SZX_CHECKS && (p + 8 > L.buf_bytes || p + c > rec_bytes)) {
+                report_bad(a.ws, tile, 1);
+                return;
+            }
+            or_bytes(words, p, run, c);
+        };
+        if (exists && kind != kConst) {
+            const uint32_t rank = sm_rank[blk];
+            const uint32_t mbase = nn_t * (b / 4 + 1) + sm_midoff[blk];
+            if (sub == 0) {
+                // the reqBits byte's word may also hold mid bytes: OR it in too
+                const uint32_t p = nn_t * (b / 4) + rank;
+                atomicOr(words + (p >> 2), (kind == kNonConst ? (uint32_t)req : 0xFFu) << (8 * (p & 3u)));
+            }
+            if (kind == kRaw) {
+                // verbatim input bytes, value-major
+                const U *src = reinterpret_cast<const U *>(a.in) + kg * b + sub * VPL;
+                for (int m = 0; m < nvalid; ++m) {
+                    const U v = src[m];
+                    const uint32_t p = mbase + (uint32_t)(sub * VPL + m) * w;
+#pragma unroll
+                    for (int h = 0; h < w / 4; ++h) put(p + 4 * h, (uint32_t)(v >> (32 * h)), 4);
+                }
             } else {
-                *reinterpret_cast<uint32_t *>(lead) = codes[0];
-            }
-            const uint32_t n0 = (uint32_t)(tot & FM), n1 = (uint32_t)((tot >> FB) & FM),
-                           n2 = (uint32_t)((tot >> (2 * FB)) & FM);
-            uint32_t pos0 = mbase + (uint32_t)(off & FM);
-            uint32_t pos1 = mbase + n0 + (uint32_t)((off >> FB) & FM);
-            uint32_t pos2 = mbase + n0 + n1 + (uint32_t)((off >> (2 * FB)) & FM);
-            const uint32_t dense0 = mbase + n0 + n1 + n2 + (uint32_t)sub * VPL;
-#pragma unroll
-            for (int gq = 0; gq < VPL / 4; ++gq) {
-                // lookup codes: values past the end of a partial block never match
-                uint32_t code8 = (codes[gq >> 2] >> (8 * (gq & 3))) & 0xFFu;
-                uint32_t dense8 = 0;
-                if (!full) {
-                    const int nv = nvalid - 4 * gq;
-                    const uint32_t inval = nv >= 4 ? 0u : (nv <= 0 ? 0xFFu : (0xFFu << (2 * nv)) & 0xFFu);
-                    code8 |= inval;
-                    dense8 = inval;
-                }
-                uint32_t Wd[W / 8];
-                if constexpr (sizeof(T) == 4) {
-                    uint32_t Wq[4];
-                    transpose4((uint32_t)x[4 * gq], (uint32_t)x[4 * gq + 1], (uint32_t)x[4 * gq + 2],
-                               (uint32_t)x[4 * gq + 3], Wq);
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) Wd[j] = Wq[j];
+                // lead codes: this lane's values are bytes [sub*VPL/4, (sub+1)*VPL/4)
+                if (SZX_CHECKS && (rank + 1) * (b / 4) > nn_t * (b / 4)) report_bad(a.ws, tile, 6);
+                uint8_t *lead = buf + rank * (b / 4) + sub * (VPL / 4);
+                if constexpr (NCODE == 2) {
+                    *reinterpret_cast<uint2 *>(lead) = make_uint2(codes[0], codes[1]);
                 } else {
-                    uint32_t Wh[4], Wl[4];
-                    transpose4((uint32_t)(x[4 * gq] >> 32), (uint32_t)(x[4 * gq + 1] >> 32),
-                               (uint32_t)(x[4 * gq + 2] >> 32), (uint32_t)(x[4 * gq + 3] >> 32), Wh);
-                    transpose4((uint32_t)x[4 * gq], (uint32_t)x[4 * gq + 1], (uint32_t)x[4 * gq + 2],
-                               (uint32_t)x[4 * gq + 3], Wl);
+                    *reinterpret_cast<uint32_t *>(lead) = codes[0];
+                }
+                const int s = (8 - (req & 7)) & 7;
+                const int q = (req + s) >> 3;
+                const uint32_t n0 = (uint32_t)(tot & FM), n1 = (uint32_t)((tot >> FB) & FM),
+                               n2 = (uint32_t)((tot >> (2 * FB)) & FM);
+                uint32_t pos0 = mbase + (uint32_t)(off & FM);
+                uint32_t pos1 = mbase + n0 + (uint32_t)((off >> FB) & FM);
+                uint32_t pos2 = mbase + n0 + n1 + (uint32_t)((off >> (2 * FB)) & FM);
+                const uint32_t dense0 = mbase + n0 + n1 + n2 + (uint32_t)sub * VPL;
 #pragma unroll
-                    for (int j = 0; j < 4; ++j) {
-                        Wd[j] = Wh[j];
-                        Wd[4 + j] = Wl[j];
+                for (int gq = 0; gq < VPL / 4; ++gq) {
+                    // lookup codes: values past the end of a partial block never match
+                    uint32_t code8 = (codes[gq >> 2] >> (8 * (gq & 3))) & 0xFFu;
+                    uint32_t dense8 = 0;
+                    if (!full_lane) {
+                        const int nv = nvalid - 4 * gq;
+                        const uint32_t inval = nv >= 4 ? 0u : (nv <= 0 ? 0xFFu : (0xFFu << (2 * nv)) & 0xFFu);
+                        code8 |= inval;
+                        dense8 = inval;
+                    }
+                    uint32_t Wd[W / 8];
+                    if constexpr (sizeof(T) == 4) {
+                        uint32_t Wq[4];
+                        transpose4((uint32_t)x[4 * gq], (uint32_t)x[4 * gq + 1], (uint32_t)x[4 * gq + 2],
+                                   (uint32_t)x[4 * gq + 3], Wq);
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) Wd[j] = Wq[j];
+                    } else {
+                        uint32_t Wh[4], Wl[4];
+                        transpose4((uint32_t)(x[4 * gq] >> 32), (uint32_t)(x[4 * gq + 1] >> 32),
+                                   (uint32_t)(x[4 * gq + 2] >> 32), (uint32_t)(x[4 * gq + 3] >> 32), Wh);
+                        transpose4((uint32_t)x[4 * gq], (uint32_t)x[4 * gq + 1], (uint32_t)x[4 * gq + 2],
+                                   (uint32_t)x[4 * gq + 3], Wl);
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) {
+                            Wd[j] = Wh[j];
+                            Wd[4 + j] = Wl[j];
+                        }
+                    }
+                    {
+                        const uint32_t e0 = lut[code8];
+                        put(pos0, prmt(Wd[0], 0, e0), e0 >> 16);
+                        pos0 += e0 >> 16;
+                        const uint32_t e1 = lut[256 + code8];
+                        put(pos1, prmt(Wd[1], 0, e1), e1 >> 16);
+                        pos1 += e1 >> 16;
+                    }
+                    if (q >= 3) {
+                        const uint32_t e2 = lut[512 + code8];
+                        put(pos2, prmt(Wd[2], 0, e2), e2 >> 16);
+                        pos2 += e2 >> 16;
+                    }
+                    if (q >= 4) {
+                        const uint32_t sel = full_lane ? 0x43210u : lut[512 + dense8];
+#pragma unroll
+                        for (int j = 3; j < W / 8; ++j) {
+                            if (j < q)
+                                put(dense0 + (uint32_t)(j - 3) * len + 4 * gq, prmt(Wd[j], 0, sel), sel >> 16);
+                        }
                     }
                 }
-                {
-                    const uint32_t e0 = lut[code8];
-                    put(pos0, prmt(Wd[0], 0, e0));
-                    pos0 += e0 >> 16;
-                    const uint32_t e1 = lut[256 + code8];
-                    put(pos1, prmt(Wd[1], 0, e1));
-                    pos1 += e1 >> 16;
-                }
-                if (q >= 3) {
-                    const uint32_t e2 = lut[512 + code8];
-                    put(pos2, prmt(Wd[2], 0, e2));
-                    pos2 += e2 >> 16;
-                }
-                if (q >= 4) {
-                    const uint32_t sel = full ? 0x3210u : lut[512 + dense8];
-#pragma unroll
-                    for (int j = 3; j < W / 8; ++j) {
-                        if (j < q) put(dense0 + (uint32_t)(j - 3) * len + 4 * gq, prmt(Wd[j], 0, sel));
-                    }
-                }
             }
         }
-    }
-    __syncthreads();
-
-    // ---- 5. look-back, index entry, record store ---------------------------
-    if (tid == 0) {
-        if (s_fail) {
-            atomicOr(&a.ws->err, kErrTmaTimeout);
-            atomicAdd(&a.ws->tma_timeouts, 1u);
-            atomicCAS(&a.ws->first_tma_tile, 0u, tile + 1);
-        }
-        uint64_t excl = 0;
-        bool timed_out = false;
-        const uint64_t t0 = globaltimer_ns();
-        for (int64_t j = (int64_t)tile - 1; j >= 0;) {
-            const uint64_t wv = ld_acquire_u64(&a.lookback[j]);
-            const uint64_t flag = wv & ~kValueMask;
-            if (flag == 0) {
-                if (globaltimer_ns() - t0 > a.lookback_ns) {
-                    timed_out = true;
-                    break;
-                }
-                __nanosleep(64);
-                continue;
-            }
-            excl += wv & kValueMask;
-            if (flag == kFlagPrefix) break;
-            --j;
-        }
-        if (timed_out) {
-            atomicOr(&a.ws->err, kErrTimeout);
-            atomicAdd(&a.ws->lookback_timeouts, 1ull);
-            atomicCAS(&a.ws->first_lb_tile, 0u, tile + 1);
-        }
-        st_release_u64(&a.lookback[tile], kFlagPrefix | (excl + s_rec));
-        s_excl = excl;
-        uint64_t *idx = reinterpret_cast<uint64_t *>(a.out + g.off_index);
-        idx[tile] = excl;
-        if (tile == g.ntiles - 1) {
-            idx[g.ntiles] = excl + s_rec;
-            const uint64_t state_end = g.off_state + (g.nb + 7) / 8;
-            for (uint64_t i = state_end; i < g.off_mu; ++i) a.out[i] = 0;
-            for (uint64_t i = g.off_mu + g.nb * w; i < g.off_index; ++i) a.out[i] = 0;
-            for (uint64_t i = g.off_index + 8 * (g.ntiles + 1); i < g.off_rec; ++i) a.out[i] = 0;
-        }
-        if (s_rec) {
-            fence_proxy_async_smem();
-            bulk_s2g(a.out + g.off_rec + excl, buf, s_rec);
-            bulk_commit();
-        }
-    }
-    // state bits and mu values of the tile (fixed positions)
-    {
-        uint8_t *state = a.out + g.off_state + (size_t)k0 / 8;
-        for (uint32_t i = tid; i < (Gt + 7) / 8; i += kThreads) {
-            uint32_t byte = 0;
-            for (int j = 0; j < 8; ++j) {
-                const uint32_t kk = i * 8 + j;
-                if (kk < Gt && sm_kind[kk] != kConst) byte |= 1u << j;
-            }
-            state[i] = (uint8_t)byte;
-        }
-        U *mu_dst = reinterpret_cast<U *>(a.out + g.off_mu) + k0;
-        for (uint32_t i = tid; i < Gt; i += kThreads) mu_dst[i] = sm_mu[i];
-    }
-    if (tid == 0) {
-        atomicAdd(&a.ws->nn, (unsigned long long)s_nn);
-        atomicAdd(&a.ws->nraw, (unsigned long long)s_nraw);
-        atomicAdd(&a.ws->nesc, (unsigned long long)s_nesc);
-        __threadfence();
-        const uint32_t done = atomicAdd(&a.ws->done, 1u);
-        if (done == g.ntiles - 1) {
-            __threadfence();
-            volatile Workspace *ws = a.ws;
-            const uint64_t rec_total = reinterpret_cast<volatile uint64_t *>(a.out + g.off_index)[g.ntiles];
-            const uint64_t total = g.off_rec + rec_total;
-            uint32_t *h32 = reinterpret_cast<uint32_t *>(a.out);
-            uint64_t *h64 = reinterpret_cast<uint64_t *>(a.out);
-            h32[0] = kMagic;
-            h32[1] = kVersion | (a.dtype << 8);
-            h32[2] = b;
-            h32[3] = G;
-            h64[2] = g.n;
-            h64[3] = a.e_bits;
-            h64[4] = ws->nn;
-            h64[5] = ws->nraw;
-            h64[6] = ws->nesc;
-            h64[7] = total;
-            const uint64_t status = (ws->err & (kErrTimeout | kErrTmaTimeout)) ? 6ull : (ws->err & kErrInternal) ? 5ull : 0ull;
-            ws->result[0] = total;
-            ws->result[1] = status;
-            if (a.d_result) {
-                a.d_result[0] = total;
-                a.d_result[1] = status;
-            }
-        }
-        if (s_rec) bulk_wait_read_all();
+        // hand the record to the storer (its bulk store reads it through the
+        // async proxy)
+        fence_proxy_async_smem();
+        mbar_arrive(&ready[st]);
     }
 }
 
@@ -700,11 +918,18 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
 
 template <typename T, int LPB, int VPL>
 cudaError_t launch_t(const CUtensorMap &tm, const CompressArgs &a, cudaStream_t stream) {
-    const CSmem2 L = compress_smem2(a.g.G, a.g.b, Fmt<T>::w);
+    const CSmem L = compress_smem(a.g.G, a.g.b, Fmt<T>::w);
     auto kern = compress_kernel<T, LPB, VPL>;
     cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total);
     if (err != cudaSuccess) return err;
-    kern<<<(unsigned)a.g.ntiles, kThreads, L.total, stream>>>(tm, a);
+    int dev = 0, sms = 0, per_sm = 0;
+    if ((err = cudaGetDevice(&dev)) != cudaSuccess) return err;
+    if ((err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return err;
+    if ((err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kCThreads, L.total)) != cudaSuccess)
+        return err;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    const uint64_t grid = min_u64(a.g.ntiles, (uint64_t)sms * per_sm);
+    kern<<<(unsigned)grid, kCThreads, L.total, stream>>>(tm, a);
     return cudaGetLastError();
 }
 
