@@ -1,27 +1,34 @@
 // decompress.cu -- SZx decompression kernel for sm_103a.
 //
-// One CTA decodes one tile.  The tile index written by the compressor gives
-// the record's offset directly, so tiles decode independently: no device-wide
-// scan is left for decompression (the paper's GPU decoder, Sec. V-B, needs a
-// prefix scan of the mid-byte counts first).  Per tile:
+// One CTA (8 warps) decodes one tile of G blocks.  The tile index written by
+// the compressor gives each record's offset, so tiles decode independently:
+// no device-wide scan is left for decompression (the paper's GPU decoder,
+// Sec. V-B, runs a prefix scan of the mid-byte counts first).
+//
+// Work layout as in the compressor: every lane owns 128 contiguous output
+// bytes (32 f32 or 16 f64 values); a block of b values spans LPB = b / VPL
+// adjacent lanes.  Per tile:
 //   1. one thread bulk-copies the record into shared memory (TMA,
-//      cp.async.bulk + mbarrier); the state bits and mu values of the tile are
+//      cp.async.bulk + mbarrier); the tile's state bits and mu values are
 //      loaded alongside;
-//   2. warp 0 ranks the non-constant blocks; each warp reads the reqBits byte
-//      and lead codes of its blocks and counts their mid bytes; warp 0 scans
-//      the counts into mid-byte offsets and checks them against the record
-//      size (every read below is inside the record);
-//   3. each warp rebuilds its blocks: the own bytes of every value come from
-//      the mid-byte planes; a leading byte (one identical to the previous
-//      value's) is resolved per byte plane as a segmented "last writer" scan
-//      across the warp -- a ballot of the lanes that own a byte of that plane
-//      and a shuffle from the nearest such lane below -- which is the paper's
-//      index propagation (Sec. V-B) done in one step per plane; then
-//      v' = t << s and d' = RN(v' + mu).
+//   2. warp 0 ranks the non-constant blocks; every lane reads its reqBits
+//      byte and lead codes, checks them, and counts its mid bytes; warp 0
+//      scans the blocks' counts into mid-byte offsets and checks them against
+//      the record size, so that every later read is inside the record;
+//   3. every lane rebuilds its values: for each group of four values and each
+//      byte plane, the lane's run of own bytes is read with two aligned word
+//      loads and a funnel shift and spread to the owning values with a
+//      table-driven byte permute.  A leading byte (identical to the previous
+//      value's) is resolved per plane: inside a lane a byte permute copies the
+//      nearest earlier owner forward, and the carry into a lane is the last
+//      own byte of the nearest lower lane of the block that owns one (a ballot
+//      and a shuffle) -- the paper's index propagation (Sec. V-B) in one step
+//      per plane.  A byte transpose turns planes back into words; then
+//      v' = t << s and d' = RN(v' + mu), stored with 16-byte stores.
+#include <type_traits>
+
 #include "szx_device.cuh"
 #include "szx_launch.h"
-
-#include <type_traits>
 
 namespace szx {
 
@@ -34,79 +41,98 @@ struct DecompressArgs {
     uint64_t rec_total;
     uint32_t dtype;
     uint32_t check_header;  // re-check the stream header on the device
-    uint64_t copy_ns;       // wall-time limit of the record copy wait
     uint64_t total_bytes;
+    uint64_t copy_ns;  // wall-time limit of the record copy wait
 };
 
 __device__ __forceinline__ void flag_status(uint32_t *status, uint32_t code) {
     if (status) atomicMax(status, code);
 }
 
-template <typename U, int VPL>
-__device__ __forceinline__ void store_out(U *p, const U (&x)[VPL], int nvalid) {
-    constexpr int bytes = VPL * (int)sizeof(U);
-    if (nvalid == VPL) {
-        if constexpr (bytes % 16 == 0) {
-#pragma unroll
-            for (int i = 0; i < bytes / 16; ++i) {
-                uint4 v;
-                U *u = reinterpret_cast<U *>(&v);
-#pragma unroll
-                for (int j = 0; j < 16 / (int)sizeof(U); ++j) u[j] = x[i * (16 / sizeof(U)) + j];
-                reinterpret_cast<uint4 *>(p)[i] = v;
-            }
-        } else if constexpr (bytes == 8) {
-            uint2 v;
-            U *u = reinterpret_cast<U *>(&v);
-#pragma unroll
-            for (int j = 0; j < VPL; ++j) u[j] = x[j];
-            *reinterpret_cast<uint2 *>(p) = v;
-        } else {
-            p[0] = x[0];
-        }
-    } else {
-#pragma unroll
-        for (int m = 0; m < VPL; ++m)
-            if (m < nvalid) p[m] = x[m];
-    }
-}
+__device__ __forceinline__ uint32_t dprmt(uint32_t a, uint32_t b, uint32_t s) { return __byte_perm(a, b, s); }
 
-template <int VPL>
-using DCodeT = std::conditional_t<(VPL > 16), uint64_t, uint32_t>;
-
-template <int VPL>
-__device__ __forceinline__ DCodeT<VPL> lane_codes(const uint8_t *slot) {
-    const int lane = lane_id();
-    if constexpr (VPL >= 4) {
-        constexpr int nb = VPL / 4;
-        DCodeT<VPL> c = 0;
-#pragma unroll
-        for (int i = 0; i < nb; ++i) c |= (DCodeT<VPL>)slot[lane * nb + i] << (8 * i);
-        return c;
-    } else if constexpr (VPL == 2) {
-        return (slot[lane >> 1] >> (4 * (lane & 1))) & 0xFu;
-    } else {
-        return (slot[lane >> 2] >> (2 * (lane & 3))) & 0x3u;
-    }
-}
-
-template <int VPL>
-struct DPlanePack {
-    using T = std::conditional_t<(VPL > 16), uint64_t, uint32_t>;
-    static constexpr int PB = VPL > 16 ? 16 : 10;
-    static constexpr T one3 = (T(1) << (2 * PB)) | (T(1) << PB) | T(1);
-    __device__ __forceinline__ static T inc(int L) { return (one3 >> (PB * L)) << (PB * L); }
-    __device__ __forceinline__ static uint32_t field(T v, int j) {
-        return (uint32_t)(v >> (PB * j)) & ((1u << PB) - 1);
-    }
+// Tables (compile time), per plane j in 0..2 and the 2-bit codes of four
+// values (value k at bits 2k):
+//   expand: byte-permute selector moving the k-th byte of a run to the k-th
+//           value whose code is <= j (others get zero) | count << 16;
+//   carry:  byte-permute selector for the copy-forward of plane j: a value
+//           whose code is > j takes the byte of the nearest earlier value of
+//           the group with code <= j, or the carry byte (operand byte 4).
+struct DecodeLut {
+    uint32_t expand[768];
+    uint32_t carry[768];
 };
+constexpr DecodeLut make_decode_lut() {
+    DecodeLut t{};
+    for (uint32_t i = 0; i < 768; ++i) {
+        const uint32_t j = i >> 8, code = i & 255u;
+        uint32_t sel = 0x4444u, cnt = 0, csel = 0;
+        int src = -1;
+        for (uint32_t k = 0; k < 4; ++k) {
+            const bool own = ((code >> (2 * k)) & 3u) <= j;
+            if (own) {
+                sel = (sel & ~(0xFu << (4 * k))) | (cnt << (4 * k));
+                ++cnt;
+                src = (int)k;
+            }
+            csel |= (uint32_t)(src < 0 ? 4 : src) << (4 * k);
+        }
+        t.expand[i] = sel | (cnt << 16);
+        t.carry[i] = csel;
+    }
+    return t;
+}
+__device__ const DecodeLut kDecodeLut = make_decode_lut();
 
-template <typename T, int VPL>
-__global__ void __launch_bounds__(kThreads) decompress_kernel(DecompressArgs a) {
+__device__ __forceinline__ void transpose4d(uint32_t t0, uint32_t t1, uint32_t t2, uint32_t t3, uint32_t (&W)[4]) {
+    const uint32_t a = dprmt(t0, t1, 0x5140), b = dprmt(t0, t1, 0x7362);
+    const uint32_t c = dprmt(t2, t3, 0x5140), d = dprmt(t2, t3, 0x7362);
+    W[3] = dprmt(a, c, 0x5410);
+    W[2] = dprmt(a, c, 0x7632);
+    W[1] = dprmt(b, d, 0x5410);
+    W[0] = dprmt(b, d, 0x7632);
+}
+
+// The up to 4 bytes at byte offset p of a shared-memory byte buffer (with 8
+// bytes of readable slack after its end), little-endian.
+__device__ __forceinline__ uint32_t load_run(const uint8_t *buf, uint32_t p) {
+    const uint32_t *wp = reinterpret_cast<const uint32_t *>(buf) + (p >> 2);
+    return __funnelshift_r(wp[0], wp[1], (p & 3u) * 8u);
+}
+
+struct DSmem {
+    uint32_t rec, rec_bytes, lut, mu, state, rank, mk, midoff, total;
+};
+__host__ __device__ inline DSmem decompress_smem2(uint32_t G, uint32_t b, uint32_t w) {
+    DSmem s;
+    uint32_t o = 0;
+    auto take = [&](uint32_t bytes, uint32_t align) {
+        o = (o + align - 1) & ~(align - 1);
+        const uint32_t at = o;
+        o += bytes;
+        return at;
+    };
+    s.rec_bytes = record_max_bytes(G, b, w) + 16;
+    s.rec = take(s.rec_bytes, 128);
+    s.lut = take(sizeof(DecodeLut), 16);
+    s.mu = take(G * w, 16);
+    s.state = take((G + 7) / 8 + 16, 16);
+    s.rank = take(G * 4, 16);
+    s.mk = take(G * 4, 16);
+    s.midoff = take(G * 4, 16);
+    s.total = o;
+    return s;
+}
+
+template <typename T, int LPB, int VPL>
+__global__ void __launch_bounds__(kThreads, (VPL * sizeof(T) > 128) ? 1 : 3) decompress_kernel(DecompressArgs a) {
     using F = Fmt<T>;
     using U = typename F::U;
     constexpr int w = F::w;
     constexpr int W = F::W;
+    constexpr int BPW = 32 / LPB;
+    constexpr int NCODE = (2 * VPL + 31) / 32;
+    constexpr int NPW = W / 32;  // 32-bit words per value
 
     extern __shared__ __align__(128) uint8_t smem[];
     __shared__ __align__(8) uint64_t bar;
@@ -114,13 +140,13 @@ __global__ void __launch_bounds__(kThreads) decompress_kernel(DecompressArgs a) 
 
     const Geometry &g = a.g;
     const uint32_t b = g.b, G = g.G;
-    const DecompressSmem L = decompress_smem(G, b, w);
-    uint8_t *sm_rec = smem + L.rec;
+    const DSmem L = decompress_smem2(G, b, w);
+    uint8_t *rec = smem + L.rec;
+    const DecodeLut *lut = reinterpret_cast<const DecodeLut *>(smem + L.lut);
     U *sm_mu = reinterpret_cast<U *>(smem + L.mu);
     uint8_t *sm_state = smem + L.state;
-    uint8_t *sm_req = smem + L.req;
-    uint32_t *sm_mk = reinterpret_cast<uint32_t *>(smem + L.mk);
     uint32_t *sm_rank = reinterpret_cast<uint32_t *>(smem + L.rank);
+    uint32_t *sm_mk = reinterpret_cast<uint32_t *>(smem + L.mk);
     uint32_t *sm_midoff = reinterpret_cast<uint32_t *>(smem + L.midoff);
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -129,7 +155,7 @@ __global__ void __launch_bounds__(kThreads) decompress_kernel(DecompressArgs a) 
     const uint32_t Gt = (uint32_t)min_u64(G, g.nb - k0);
     const uint32_t rec_max = record_max_bytes(G, b, w);
 
-    // ---- 1. record, state bits and mu of the tile -------------------------
+    // ---- 1. record, state bits, mu values, tables ---------------------------
     if (tid == 0) {
         uint32_t bad = 0;
         if (a.check_header && tile == 0) {
@@ -150,10 +176,13 @@ __global__ void __launch_bounds__(kThreads) decompress_kernel(DecompressArgs a) 
         fence_mbar_init();
         if (size) {
             mbar_arrive_expect_tx(&bar, size);
-            bulk_g2s(sm_rec, a.in + g.off_rec + r0, size, &bar);
+            bulk_g2s(rec, a.in + g.off_rec + r0, size, &bar);
         }
     }
     {
+        const uint4 *src = reinterpret_cast<const uint4 *>(&kDecodeLut);
+        uint4 *dst = reinterpret_cast<uint4 *>(smem + L.lut);
+        for (uint32_t i = tid; i < sizeof(DecodeLut) / 16; i += kThreads) dst[i] = src[i];
         const uint8_t *st = a.in + g.off_state + k0 / 8;
         for (uint32_t i = tid; i < (Gt + 7) / 8; i += kThreads) sm_state[i] = st[i];
         const U *mu = reinterpret_cast<const U *>(a.in + g.off_mu) + k0;
@@ -162,9 +191,10 @@ __global__ void __launch_bounds__(kThreads) decompress_kernel(DecompressArgs a) 
     __syncthreads();
     const uint32_t size = s_size;
     if (size && !mbar_wait_bounded(&bar, 0, a.copy_ns)) s_bad = 2;
+    if (tid < 2) reinterpret_cast<uint32_t *>(rec + size)[tid] = 0;  // readable slack after the record
     __syncthreads();
 
-    // ---- 2. ranks, mid-byte counts, offsets -------------------------------
+    // ---- 2. ranks, codes, mid-byte counts, offsets ----------------------------
     if (warp == 0) {
         const uint32_t per = (Gt + 31) / 32;
         const uint32_t lo = min(lane * per, Gt), hi = min(lo + per, Gt);
@@ -183,46 +213,58 @@ __global__ void __launch_bounds__(kThreads) decompress_kernel(DecompressArgs a) 
     }
     __syncthreads();
     const uint32_t nn_t = s_nn;
-    if (!s_bad) {
-        for (uint32_t kk = warp; kk < Gt; kk += kWarps) {
-            if (!((sm_state[kk >> 3] >> (kk & 7)) & 1u)) {
-                if (lane == 0) sm_mk[kk] = 0;
-                continue;
-            }
-            const uint32_t rank = sm_rank[kk];
-            const int len = (int)min_u64(b, g.n - (k0 + kk) * b);
-            const int rq = sm_rec[nn_t * (b / 4) + rank];
-            uint32_t mk;
-            bool ok = true;
-            if (rq == 0xFF) {
-                mk = (uint32_t)len * w;
-            } else {
-                ok = rq >= 1 + F::E && rq <= W;
-                const int s = (8 - (rq & 7)) & 7;
-                const int q = (rq + s) >> 3;
-                const int lmax = q < 3 ? q : 3;
-                const DCodeT<VPL> codes = lane_codes<VPL>(sm_rec + rank * (b / 4));
-                uint32_t cnt = 0;
+    const int sub = lane % LPB;
+    const uint32_t blk = (uint32_t)(warp * BPW + lane / LPB);
+    const bool exists = blk < Gt && !s_bad;
+    const uint64_t kg = k0 + blk;
+    const int len = exists ? (int)min_u64(b, g.n - kg * b) : 0;
+    int nvalid = len - sub * VPL;
+    nvalid = nvalid < 0 ? 0 : (nvalid > VPL ? VPL : nvalid);
+    const bool full = nvalid == VPL;
+    const bool nonconst = exists && ((sm_state[blk >> 3] >> (blk & 7)) & 1u);
+    const uint32_t rank = nonconst ? sm_rank[blk] : 0u;
+    const int rq = nonconst ? (int)rec[nn_t * (b / 4) + rank] : 0;
+    const bool raw = nonconst && rq == 0xFF;
+    const bool coded = nonconst && !raw;
+    bool ok = !coded || (rq >= 1 + F::E && rq <= W);
+    const int s = (8 - (rq & 7)) & 7;
+    const int q = coded && ok ? (rq + s) >> 3 : 2;
+    const int lmax = q < 3 ? q : 3;
+    uint32_t codes[NCODE];
 #pragma unroll
-                for (int m = 0; m < VPL; ++m) {
-                    const int l = (int)(codes >> (2 * m)) & 3;
-                    const bool valid = lane * VPL + m < len;
-                    if (valid) {
-                        ok = ok && l <= lmax;
-                        cnt += (uint32_t)(q - l);
-                    } else {
-                        ok = ok && l == 0;
-                    }
-                }
-                ok = __all_sync(kFull, ok);
-                mk = __reduce_add_sync(kFull, ok ? cnt : 0u);
-            }
-            if (lane == 0) {
-                sm_req[kk] = (uint8_t)rq;
-                sm_mk[kk] = mk;
-                if (!ok) s_bad |= 1;
-            }
+    for (int i = 0; i < NCODE; ++i) codes[i] = 0;
+    if (coded) {
+        const uint8_t *lead = rec + rank * (b / 4) + sub * (VPL / 4);
+        if constexpr (NCODE == 2) {
+            const uint2 v = *reinterpret_cast<const uint2 *>(lead);
+            codes[0] = v.x;
+            codes[1] = v.y;
+        } else {
+            codes[0] = *reinterpret_cast<const uint32_t *>(lead);
         }
+        // codes past the end are 0; no code exceeds min(3, q)
+#pragma unroll
+        for (int i = 0; i < NCODE; ++i) {
+            const int nv = nvalid - 16 * i;
+            const uint32_t vm = nv >= 16 ? 0xFFFFFFFFu : (nv <= 0 ? 0u : (0xFFFFFFFFu >> (2 * (16 - nv))));
+            if (codes[i] & ~vm) ok = false;
+            if (lmax == 2 && (codes[i] & (codes[i] >> 1) & 0x55555555u)) ok = false;
+        }
+    }
+    uint32_t suml = 0;
+#pragma unroll
+    for (int i = 0; i < NCODE; ++i) suml += __popc(codes[i] & 0x55555555u) + 2 * __popc(codes[i] & 0xAAAAAAAAu);
+    uint32_t mk = coded ? (uint32_t)(nvalid * q) - suml : (raw ? (uint32_t)nvalid * w : 0u);
+    const uint32_t segmask = (LPB == 32 ? kFull : ((1u << LPB) - 1u)) << (lane & ~(LPB - 1));
+    {
+        const uint32_t bal = __ballot_sync(kFull, ok);
+        ok = (bal & segmask) == segmask;
+    }
+#pragma unroll
+    for (int d = 1; d < LPB; d <<= 1) mk += __shfl_xor_sync(kFull, mk, d);
+    if (exists && sub == 0) {
+        sm_mk[blk] = nonconst ? mk : 0u;
+        if (!ok) s_bad |= 1;
     }
     __syncthreads();
     if (warp == 0 && !s_bad) {
@@ -247,7 +289,7 @@ __global__ void __launch_bounds__(kThreads) decompress_kernel(DecompressArgs a) 
         // the record's pad bytes must be zero
         const uint32_t used = nn_t * (b / 4 + 1) + s_mid;
         for (uint32_t i = used + tid; i < size; i += kThreads)
-            if (sm_rec[i]) s_bad |= 1;
+            if (rec[i]) s_bad |= 1;
     }
     __syncthreads();
     if (s_bad) {
@@ -256,130 +298,165 @@ __global__ void __launch_bounds__(kThreads) decompress_kernel(DecompressArgs a) 
         return;
     }
 
-    // ---- 3. decode ---------------------------------------------------------
-    const uint32_t mid_base = nn_t * (b / 4 + 1);
-    U *out = reinterpret_cast<U *>(a.out);
-    for (uint32_t kk = warp; kk < Gt; kk += kWarps) {
-        const uint64_t first = (k0 + kk) * b;
-        const int len = (int)min_u64(b, g.n - first);
-        const int nvalid = max(0, min(VPL, len - lane * VPL));
-        U *dst = out + first + lane * VPL;
-        U x[VPL];
-        const U mu_bits = sm_mu[kk];
-        if (!((sm_state[kk >> 3] >> (kk & 7)) & 1u)) {
+    // ---- 3. decode ----------------------------------------------------------
+    const uint32_t mbase = exists ? nn_t * (b / 4 + 1) + sm_midoff[blk] : 0u;
+    const U mu_bits = exists ? sm_mu[blk] : U(0);
+    U x[VPL];
+
+    // per-lane counts of values with code <= j (j = 0, 1, 2), packed, and
+    // their exclusive scan over the block's lanes (every lane runs this)
+    using CntT = std::conditional_t<(LPB * VPL > 1023), unsigned long long, uint32_t>;
+    constexpr int FB = LPB * VPL > 1023 ? 16 : 10;
+    constexpr CntT FM = (CntT(1) << FB) - 1;
+    CntT cnt = 0;
+    if (coded) {
 #pragma unroll
-            for (int m = 0; m < VPL; ++m) x[m] = mu_bits;
-            store_out<U, VPL>(dst, x, nvalid);
-            continue;
+        for (int i = 0; i < NCODE; ++i) {
+            const int nv = nvalid - 16 * i;
+            const uint32_t vm = nv >= 16 ? 0x55555555u : (nv <= 0 ? 0u : (0x55555555u >> (2 * (16 - nv))));
+            const uint32_t lo = codes[i] & 0x55555555u, hi = (codes[i] >> 1) & 0x55555555u;
+            cnt += (CntT)__popc(~(lo | hi) & vm) | ((CntT)__popc(~hi & vm) << FB) |
+                   ((CntT)__popc(~(lo & hi) & vm) << (2 * FB));
         }
-        const uint32_t rank = sm_rank[kk];
-        const uint8_t *mid = sm_rec + mid_base + sm_midoff[kk];
-        const int rq = sm_req[kk];
-        if (rq == 0xFF) {
+    }
+    CntT incl = cnt;
 #pragma unroll
-            for (int m = 0; m < VPL; ++m) {
-                U u = 0;
-                if (m < nvalid) {
-                    const uint8_t *p = mid + (size_t)(lane * VPL + m) * w;
+    for (int d = 1; d < LPB; d <<= 1) {
+        const CntT y = __shfl_up_sync(kFull, incl, d);
+        if (sub >= d) incl += y;
+    }
+    const CntT tot = __shfl_sync(kFull, incl, (lane & ~(LPB - 1)) + LPB - 1);
+    const CntT off = incl - cnt;
+    const uint32_t n0 = (uint32_t)(tot & FM), n1 = (uint32_t)((tot >> FB) & FM),
+                   n2 = (uint32_t)((tot >> (2 * FB)) & FM);
+    const uint32_t cj[3] = {(uint32_t)(cnt & FM), (uint32_t)((cnt >> FB) & FM), (uint32_t)((cnt >> (2 * FB)) & FM)};
+    uint32_t pos0 = mbase + (uint32_t)(off & FM);
+    uint32_t pos1 = mbase + n0 + (uint32_t)((off >> FB) & FM);
+    uint32_t pos2 = mbase + n0 + n1 + (uint32_t)((off >> (2 * FB)) & FM);
+    const uint32_t dense0 = mbase + n0 + n1 + n2 + (uint32_t)sub * VPL;
+
+    // carries into the lane for the planes that can inherit (j < lmax): the
+    // last own byte of the nearest lower lane of the block that owns one
+    uint32_t carry[3];
+    {
+        const uint32_t below = segmask & ((1u << lane) - 1u);
+        const uint32_t pj[3] = {pos0, pos1, pos2};
 #pragma unroll
-                    for (int i = 0; i < w; ++i) u |= (U)p[i] << (8 * i);
-                }
-                x[m] = u;
-            }
-            store_out<U, VPL>(dst, x, nvalid);
-            continue;
+        for (int j = 0; j < 3; ++j) {
+            const bool has = coded && j < lmax && cj[j] > 0;
+            const uint32_t last = has ? rec[pj[j] + cj[j] - 1] : 0u;
+            const uint32_t m = __ballot_sync(kFull, has) & below;
+            const uint32_t v = __shfl_sync(kFull, last, m ? 31 - __clz(m) : 0);
+            carry[j] = m ? v : 0u;
         }
-        const int s = (8 - (rq & 7)) & 7;
-        const int q = (rq + s) >> 3;
-        const int lmax = q < 3 ? q : 3;
-        const DCodeT<VPL> codes = lane_codes<VPL>(sm_rec + rank * (b / 4));
-        int Lm[VPL];
-        bool valid[VPL];
-        typename DPlanePack<VPL>::T cnt = 0;
-#pragma unroll
-        for (int m = 0; m < VPL; ++m) {
-            valid[m] = m < nvalid;
-            Lm[m] = (int)(codes >> (2 * m)) & 3;
-            if (valid[m]) cnt += DPlanePack<VPL>::inc(Lm[m]);
-        }
-        typename DPlanePack<VPL>::T tot;
-        const typename DPlanePack<VPL>::T off = warp_exclusive_scan(cnt, &tot);
-        const uint32_t n0 = DPlanePack<VPL>::field(tot, 0), n1 = DPlanePack<VPL>::field(tot, 1),
-                       n2 = DPlanePack<VPL>::field(tot, 2);
-        const uint32_t P[3] = {0u, n0, n0 + n1};
-        // own bytes from the planes
-        U own[VPL];
-#pragma unroll
-        for (int m = 0; m < VPL; ++m) own[m] = 0;
-        const int sparse = q < 3 ? q : 3;
-        for (int j = 0; j < sparse; ++j) {
-            uint32_t pos = P[j] + DPlanePack<VPL>::field(off, j);
-#pragma unroll
-            for (int m = 0; m < VPL; ++m) {
-                if (valid[m] && Lm[m] <= j) own[m] |= (U)mid[pos++] << (W - 8 - 8 * j);
-            }
-        }
-        for (int j = 3; j < q; ++j) {
-            const uint8_t *plane = mid + n0 + n1 + n2 + (uint32_t)(j - 3) * len + lane * VPL;
-#pragma unroll
-            for (int m = 0; m < VPL; ++m)
-                if (valid[m]) own[m] |= (U)plane[m] << (W - 8 - 8 * j);
-        }
-        // leading bytes: per plane j < lmax, the nearest earlier owner
-        U incoming = 0;
-        for (int j = 0; j < lmax; ++j) {
-            bool has = false;
-            uint32_t last = 0;
-#pragma unroll
-            for (int m = 0; m < VPL; ++m) {
-                if (valid[m] && Lm[m] <= j) {
-                    has = true;
-                    last = (uint32_t)(own[m] >> (W - 8 - 8 * j)) & 0xFFu;
-                }
-            }
-            const uint32_t below = __ballot_sync(kFull, has) & ((1u << lane) - 1u);
-            const int src = below ? 31 - __clz(below) : 0;
-            uint32_t byte = __shfl_sync(kFull, last, src);
-            if (!below) byte = 0;
-            incoming |= (U)byte << (W - 8 - 8 * j);
-        }
-        U prev = incoming;
+    }
+
+    if (coded) {
         const T mu = F::from(mu_bits);
 #pragma unroll
-        for (int m = 0; m < VPL; ++m) {
-            const int l = Lm[m];
-            const U hi = l ? ~(U)0 << (W - 8 * l) : (U)0;
-            const U t = own[m] | (prev & hi);
-            prev = t;
-            x[m] = F::bits(F::add(F::from((U)(t << s)), mu));
+        for (int gq = 0; gq < VPL / 4; ++gq) {
+            uint32_t code8 = (codes[gq >> 2] >> (8 * (gq & 3))) & 0xFFu;
+            uint32_t dense8 = 0;
+            if (!full) {
+                const int nv = nvalid - 4 * gq;
+                const uint32_t inval = nv >= 4 ? 0u : (nv <= 0 ? 0xFFu : (0xFFu << (2 * nv)) & 0xFFu);
+                code8 |= inval;
+                dense8 = inval;
+            }
+            // plane words: byte k = byte j of value 4gq + k
+            uint32_t P[W / 8];
+#pragma unroll
+            for (int j = 0; j < W / 8; ++j) P[j] = 0;
+            {
+                const uint32_t e0 = lut->expand[code8];
+                P[0] = dprmt(load_run(rec, pos0), 0, e0);
+                pos0 += e0 >> 16;
+                const uint32_t e1 = lut->expand[256 + code8];
+                P[1] = dprmt(load_run(rec, pos1), 0, e1);
+                pos1 += e1 >> 16;
+                if (q >= 3) {
+                    const uint32_t e2 = lut->expand[512 + code8];
+                    P[2] = dprmt(load_run(rec, pos2), 0, e2);
+                    pos2 += e2 >> 16;
+                }
+                if (q >= 4) {
+                    const uint32_t sel = full ? 0x3210u : lut->expand[512 + dense8];
+#pragma unroll
+                    for (int j = 3; j < W / 8; ++j)
+                        if (j < q) P[j] = dprmt(load_run(rec, dense0 + (uint32_t)(j - 3) * len + 4 * gq), 0, sel);
+                }
+            }
+            // leading bytes: copy the nearest earlier owner forward
+            P[0] = dprmt(P[0], carry[0], lut->carry[code8]);
+            carry[0] = P[0] >> 24;
+            P[1] = dprmt(P[1], carry[1], lut->carry[256 + code8]);
+            carry[1] = P[1] >> 24;
+            if (lmax >= 3) {
+                P[2] = dprmt(P[2], carry[2], lut->carry[512 + code8]);
+                carry[2] = P[2] >> 24;
+            }
+            // planes back to words: t = (P0.k, P1.k, P2.k, P3.k), most significant first
+            U t[4];
+            if constexpr (NPW == 1) {
+                uint32_t Wq[4];
+                transpose4d(P[3], P[2], P[1], P[0], Wq);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) t[k] = Wq[3 - k];
+            } else {
+                uint32_t Wh[4], Wl[4];
+                transpose4d(P[3], P[2], P[1], P[0], Wh);
+                transpose4d(P[7], P[6], P[5], P[4], Wl);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) t[k] = ((U)Wh[3 - k] << 32) | (U)Wl[3 - k];
+            }
+#pragma unroll
+            for (int k = 0; k < 4; ++k) x[4 * gq + k] = F::bits(F::add(F::from((U)(t[k] << s)), mu));
         }
-        store_out<U, VPL>(dst, x, nvalid);
+    } else if (raw) {
+        const uint8_t *p = rec + mbase + (uint32_t)sub * VPL * w;
+#pragma unroll
+        for (int m = 0; m < VPL; ++m) {
+            U u = 0;
+            if (m < nvalid) {
+#pragma unroll
+                for (int i = 0; i < w; ++i) u |= (U)p[m * w + i] << (8 * i);
+            }
+            x[m] = u;
+        }
+    } else {
+#pragma unroll
+        for (int m = 0; m < VPL; ++m) x[m] = mu_bits;
+    }
+
+    if (exists && nvalid > 0) {
+        U *dst = reinterpret_cast<U *>(a.out) + kg * b + sub * VPL;
+        if (full) {
+#pragma unroll
+            for (int i = 0; i < VPL * w / 16; ++i) {
+                uint4 v;
+                U *u = reinterpret_cast<U *>(&v);
+#pragma unroll
+                for (int k = 0; k < 16 / w; ++k) u[k] = x[i * (16 / w) + k];
+                reinterpret_cast<uint4 *>(dst)[i] = v;
+            }
+        } else {
+#pragma unroll
+            for (int m = 0; m < VPL; ++m)
+                if (m < nvalid) dst[m] = x[m];
+        }
     }
 }
 
 // ---------------------------------------------------------------------------
 
-template <typename T, int VPL>
+template <typename T, int LPB, int VPL>
 static cudaError_t launch_t(const DecompressArgs &a, cudaStream_t stream) {
-    const DecompressSmem L = decompress_smem(a.g.G, a.g.b, Fmt<T>::w);
-    auto kern = decompress_kernel<T, VPL>;
+    const DSmem L = decompress_smem2(a.g.G, a.g.b, Fmt<T>::w);
+    auto kern = decompress_kernel<T, LPB, VPL>;
     cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total);
     if (err != cudaSuccess) return err;
     kern<<<(unsigned)a.g.ntiles, kThreads, L.total, stream>>>(a);
     return cudaGetLastError();
-}
-
-template <typename T>
-static cudaError_t launch_vpl(const DecompressArgs &a, cudaStream_t stream) {
-    switch (a.g.b) {
-        case 32: return launch_t<T, 1>(a, stream);
-        case 64: return launch_t<T, 2>(a, stream);
-        case 128: return launch_t<T, 4>(a, stream);
-        case 256: return launch_t<T, 8>(a, stream);
-        case 512: return launch_t<T, 16>(a, stream);
-        case 1024: return launch_t<T, 32>(a, stream);
-        default: return cudaErrorInvalidValue;
-    }
 }
 
 cudaError_t launch_decompress(const void *in, uint64_t in_bytes, uint64_t total_bytes, uint64_t n, int dtype,
@@ -396,7 +473,26 @@ cudaError_t launch_decompress(const void *in, uint64_t in_bytes, uint64_t total_
     a.check_header = check_header ? 1u : 0u;
     a.total_bytes = total_bytes;
     a.copy_ns = 1000ull * wait_limit_from_env("SZX_COPY_US", 1000000u);
-    return dtype == 0 ? launch_vpl<float>(a, stream) : launch_vpl<double>(a, stream);
+    if (dtype == 0) {
+        switch (block) {
+            case 32: return launch_t<float, 1, 32>(a, stream);
+            case 64: return launch_t<float, 2, 32>(a, stream);
+            case 128: return launch_t<float, 4, 32>(a, stream);
+            case 256: return launch_t<float, 8, 32>(a, stream);
+            case 512: return launch_t<float, 16, 32>(a, stream);
+            case 1024: return launch_t<float, 32, 32>(a, stream);
+        }
+    } else {
+        switch (block) {
+            case 32: return launch_t<double, 2, 16>(a, stream);
+            case 64: return launch_t<double, 4, 16>(a, stream);
+            case 128: return launch_t<double, 8, 16>(a, stream);
+            case 256: return launch_t<double, 16, 16>(a, stream);
+            case 512: return launch_t<double, 32, 16>(a, stream);
+            case 1024: return launch_t<double, 32, 32>(a, stream);
+        }
+    }
+    return cudaErrorInvalidValue;
 }
 
 }  // namespace szx

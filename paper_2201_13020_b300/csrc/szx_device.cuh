@@ -305,27 +305,4 @@ __host__ __device__ __forceinline__ uint64_t workspace_bytes(uint64_t ntiles) {
     return kWsHeader + 8 * ntiles;
 }
 
-// Shared-memory carve-up of the decompress kernel.
-struct DecompressSmem {
-    uint32_t rec, mu, state, req, mk, rank, midoff, total;
-};
-__host__ __device__ inline DecompressSmem decompress_smem(uint32_t G, uint32_t b, uint32_t w) {
-    DecompressSmem s;
-    uint32_t o = 0;
-    auto take = [&](uint32_t bytes) {
-        uint32_t at = o;
-        o = (o + bytes + 127) & ~127u;
-        return at;
-    };
-    s.rec = take(record_max_bytes(G, b, w));
-    s.mu = take(G * w);
-    s.state = take((G + 7) / 8 + 16);
-    s.req = take(G);
-    s.mk = take(G * 4);
-    s.rank = take(G * 4);
-    s.midoff = take(G * 4);
-    s.total = o;
-    return s;
-}
-
 }  // namespace szx
