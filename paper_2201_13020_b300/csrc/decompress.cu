@@ -1,20 +1,21 @@
 // decompress.cu -- SZx decompression kernel for sm_103a.
 //
-// One CTA (8 warps) decodes one tile of G blocks.  The tile index written by
-// the compressor gives each record's offset, so tiles decode independently:
-// no device-wide scan is left for decompression (the paper's GPU decoder,
-// Sec. V-B, runs a prefix scan of the mid-byte counts first).
+// Persistent CTAs decode tiles of G blocks.  The tile index written by the
+// compressor gives each record's offset, so tiles decode independently: no
+// device-wide scan is left for decompression (the paper's GPU decoder, Sec.
+// V-B, runs a prefix scan of the mid-byte counts first).  Per CTA, a producer
+// warp bulk-copies records (TMA, cp.async.bulk + mbarrier) into a ring of
+// three stages while eight decoding warps work on earlier ones.
 //
 // Work layout as in the compressor: every lane owns 128 contiguous output
 // bytes (32 f32 or 16 f64 values); a block of b values spans LPB = b / VPL
 // adjacent lanes.  Per tile:
-//   1. one thread bulk-copies the record into shared memory (TMA,
-//      cp.async.bulk + mbarrier); the tile's state bits and mu values are
-//      loaded alongside;
-//   2. warp 0 ranks the non-constant blocks; every lane reads its reqBits
-//      byte and lead codes, checks them, and counts its mid bytes; warp 0
-//      scans the blocks' counts into mid-byte offsets and checks them against
-//      the record size, so that every later read is inside the record;
+//   1. every lane ranks its block among the tile's non-constant blocks (a
+//      popcount of the tile's state bits), reads its reqBits byte and lead
+//      codes, checks them, and counts its mid bytes;
+//   2. after one barrier every warp scans the blocks' counts into mid-byte
+//      offsets and checks the total against the record size, so that every
+//      later read is inside the record;
 //   3. every lane rebuilds its values: for each group of four values and each
 //      byte plane, the lane's run of own bytes is read with two aligned word
 //      loads and a funnel shift and spread to the owning values with a
@@ -100,10 +101,14 @@ __device__ __forceinline__ uint32_t load_run(const uint8_t *buf, uint32_t p) {
     return __funnelshift_r(wp[0], wp[1], (p & 3u) * 8u);
 }
 
+constexpr int kDStages = 3;
+constexpr int kDConsumers = kThreads;     // 8 decoding warps
+constexpr int kDThreads = kDConsumers + 32;  // + a producer warp
+
 struct DSmem {
-    uint32_t rec, rec_bytes, lut, mu, state, rank, mk, midoff, total;
+    uint32_t rec[kDStages], rec_bytes, mk[kDStages], lut, total;
 };
-__host__ __device__ inline DSmem decompress_smem2(uint32_t G, uint32_t b, uint32_t w) {
+__host__ __device__ inline DSmem decompress_smem(uint32_t G, uint32_t b, uint32_t w) {
     DSmem s;
     uint32_t o = 0;
     auto take = [&](uint32_t bytes, uint32_t align) {
@@ -113,19 +118,27 @@ __host__ __device__ inline DSmem decompress_smem2(uint32_t G, uint32_t b, uint32
         return at;
     };
     s.rec_bytes = record_max_bytes(G, b, w) + 16;
-    s.rec = take(s.rec_bytes, 128);
+    for (int i = 0; i < kDStages; ++i) s.rec[i] = take(s.rec_bytes, 128);
+    for (int i = 0; i < kDStages; ++i) s.mk[i] = take(G * 4, 16);
     s.lut = take(sizeof(DecodeLut), 16);
-    s.mu = take(G * w, 16);
-    s.state = take((G + 7) / 8 + 16, 16);
-    s.rank = take(G * 4, 16);
-    s.mk = take(G * 4, 16);
-    s.midoff = take(G * 4, 16);
     s.total = o;
     return s;
 }
 
+__device__ __forceinline__ void decoder_sync() { asm volatile("bar.sync 1, %0;" ::"n"(kDConsumers) : "memory"); }
+
+__device__ __forceinline__ void dmbar_arrive(uint64_t *bar) {
+    asm volatile(
+        "{\n\t.reg .b64 st;\n\t"
+        "mbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(smem_addr(bar))
+        : "memory");
+}
+
+// Persistent decoder: a producer warp bulk-copies the records of the CTA's
+// tiles (tile = blockIdx.x + k * gridDim.x) into a ring of stages; eight
+// decoding warps turn each record into the tile's values.
 template <typename T, int LPB, int VPL>
-__global__ void __launch_bounds__(kThreads, (VPL * sizeof(T) > 128) ? 1 : 3) decompress_kernel(DecompressArgs a) {
+__global__ void __launch_bounds__(kDThreads, (VPL * sizeof(T) > 128) ? 1 : 2) decompress_kernel(DecompressArgs a) {
     using F = Fmt<T>;
     using U = typename F::U;
     constexpr int w = F::w;
@@ -135,315 +148,349 @@ __global__ void __launch_bounds__(kThreads, (VPL * sizeof(T) > 128) ? 1 : 3) dec
     constexpr int NPW = W / 32;  // 32-bit words per value
 
     extern __shared__ __align__(128) uint8_t smem[];
-    __shared__ __align__(8) uint64_t bar;
-    __shared__ uint32_t s_size, s_bad, s_nn, s_mid;
+    __shared__ __align__(8) uint64_t full[kDStages], empty[kDStages];
+    __shared__ uint32_t st_tile[kDStages], st_size[kDStages], st_bad[kDStages];
+    __shared__ uint32_t s_abort;
 
     const Geometry &g = a.g;
     const uint32_t b = g.b, G = g.G;
-    const DSmem L = decompress_smem2(G, b, w);
-    uint8_t *rec = smem + L.rec;
+    const DSmem L = decompress_smem(G, b, w);
     const DecodeLut *lut = reinterpret_cast<const DecodeLut *>(smem + L.lut);
-    U *sm_mu = reinterpret_cast<U *>(smem + L.mu);
-    uint8_t *sm_state = smem + L.state;
-    uint32_t *sm_rank = reinterpret_cast<uint32_t *>(smem + L.rank);
-    uint32_t *sm_mk = reinterpret_cast<uint32_t *>(smem + L.mk);
-    uint32_t *sm_midoff = reinterpret_cast<uint32_t *>(smem + L.midoff);
-
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const uint32_t tile = blockIdx.x;
-    const uint64_t k0 = (uint64_t)tile * G;
-    const uint32_t Gt = (uint32_t)min_u64(G, g.nb - k0);
-    const uint32_t rec_max = record_max_bytes(G, b, w);
 
-    // ---- 1. record, state bits, mu values, tables ---------------------------
-    if (tid == 0) {
-        uint32_t bad = 0;
-        if (a.check_header && tile == 0) {
-            const uint32_t *h32 = reinterpret_cast<const uint32_t *>(a.in);
-            const uint64_t *h64 = reinterpret_cast<const uint64_t *>(a.in);
-            if (h32[0] != kMagic || (h32[1] & 0xFFFFu) != (kVersion | (a.dtype << 8)) || h32[2] != b ||
-                h32[3] != G || h64[2] != g.n || h64[7] != a.total_bytes)
-                bad = 1;
-        }
-        const uint64_t *idx = reinterpret_cast<const uint64_t *>(a.in + g.off_index);
-        const uint64_t r0 = idx[tile], r1 = idx[tile + 1];
-        if (r0 > r1 || r1 > a.rec_total || (r0 & 15) || (r1 & 15) || r1 - r0 > rec_max) bad = 1;
-        if (tile == g.ntiles - 1 && r1 != a.rec_total) bad = 1;
-        const uint32_t size = bad ? 0u : (uint32_t)(r1 - r0);
-        s_size = size;
-        s_bad = bad;
-        mbar_init(&bar, 1);
-        fence_mbar_init();
-        if (size) {
-            mbar_arrive_expect_tx(&bar, size);
-            bulk_g2s(rec, a.in + g.off_rec + r0, size, &bar);
-        }
-    }
     {
         const uint4 *src = reinterpret_cast<const uint4 *>(&kDecodeLut);
         uint4 *dst = reinterpret_cast<uint4 *>(smem + L.lut);
-        for (uint32_t i = tid; i < sizeof(DecodeLut) / 16; i += kThreads) dst[i] = src[i];
-        const uint8_t *st = a.in + g.off_state + k0 / 8;
-        for (uint32_t i = tid; i < (Gt + 7) / 8; i += kThreads) sm_state[i] = st[i];
-        const U *mu = reinterpret_cast<const U *>(a.in + g.off_mu) + k0;
-        for (uint32_t i = tid; i < Gt; i += kThreads) sm_mu[i] = mu[i];
+        for (uint32_t i = tid; i < sizeof(DecodeLut) / 16; i += kDThreads) dst[i] = src[i];
     }
-    __syncthreads();
-    const uint32_t size = s_size;
-    if (size && !mbar_wait_bounded(&bar, 0, a.copy_ns)) s_bad = 2;
-    if (tid < 2) reinterpret_cast<uint32_t *>(rec + size)[tid] = 0;  // readable slack after the record
+    if (tid == 0) {
+        for (int i = 0; i < kDStages; ++i) {
+            mbar_init(&full[i], 1);
+            mbar_init(&empty[i], kDConsumers);
+            st_tile[i] = 0xFFFFFFFFu;
+            st_size[i] = st_bad[i] = 0;
+        }
+        fence_mbar_init();
+        s_abort = 0;
+    }
     __syncthreads();
 
-    // ---- 2. ranks, codes, mid-byte counts, offsets ----------------------------
-    if (warp == 0) {
-        const uint32_t per = (Gt + 31) / 32;
-        const uint32_t lo = min(lane * per, Gt), hi = min(lo + per, Gt);
-        uint32_t c = 0;
-        for (uint32_t kk = lo; kk < hi; ++kk) c += (sm_state[kk >> 3] >> (kk & 7)) & 1u;
-        uint32_t tot;
-        uint32_t e = warp_exclusive_scan(c, &tot);
-        for (uint32_t kk = lo; kk < hi; ++kk) {
-            sm_rank[kk] = e;
-            e += (sm_state[kk >> 3] >> (kk & 7)) & 1u;
+    if (warp == kThreads / 32) {
+        // ---- producer: record copies into the stage ring --------------------
+        if (lane != 0) return;
+        const uint32_t rec_max = record_max_bytes(G, b, w);
+        bool copy_last[kDStages] = {};
+        uint32_t copy_phase[kDStages] = {};
+        for (uint32_t it = 0;; ++it) {
+            const int st = (int)(it % kDStages);
+            const uint32_t k = it / kDStages;
+            if (it >= kDStages && !mbar_wait_bounded(&empty[st], (k - 1) & 1u, 4 * a.copy_ns)) {
+                flag_status(a.status, 6u);
+                break;
+            }
+            const uint64_t tile64 = (uint64_t)blockIdx.x + (uint64_t)it * gridDim.x;
+            const uint32_t tile = tile64 < g.ntiles ? (uint32_t)tile64 : 0xFFFFFFFFu;
+            uint32_t bad = 0, size = 0;
+            uint64_t r0 = 0;
+            if (tile != 0xFFFFFFFFu) {
+                if (a.check_header && tile == 0) {
+                    const uint32_t *h32 = reinterpret_cast<const uint32_t *>(a.in);
+                    const uint64_t *h64 = reinterpret_cast<const uint64_t *>(a.in);
+                    if (h32[0] != kMagic || (h32[1] & 0xFFFFu) != (kVersion | (a.dtype << 8)) || h32[2] != b ||
+                        h32[3] != G || h64[2] != g.n || h64[7] != a.total_bytes)
+                        bad = 1;
+                }
+                const uint64_t *idx = reinterpret_cast<const uint64_t *>(a.in + g.off_index);
+                r0 = idx[tile];
+                const uint64_t r1 = idx[tile + 1];
+                if (r0 > r1 || r1 > a.rec_total || (r0 & 15) || (r1 & 15) || r1 - r0 > rec_max) bad = 1;
+                if (tile == g.ntiles - 1 && r1 != a.rec_total) bad = 1;
+                size = bad ? 0u : (uint32_t)(r1 - r0);
+            }
+            st_tile[st] = tile;
+            st_size[st] = size;
+            st_bad[st] = bad;
+            if (size) {
+                mbar_arrive_expect_tx(&full[st], size);
+                bulk_g2s(smem + L.rec[st], a.in + g.off_rec + r0, size, &full[st]);
+                copy_last[st] = true;
+                copy_phase[st] = k;
+            } else {
+                dmbar_arrive(&full[st]);
+                copy_last[st] = false;
+            }
+            if (tile == 0xFFFFFFFFu) break;
         }
-        if (lane == 0) {
-            s_nn = tot;
-            if ((uint64_t)tot * (b / 4 + 1) > size) s_bad |= 1;
-        }
-    }
-    __syncthreads();
-    const uint32_t nn_t = s_nn;
-    const int sub = lane % LPB;
-    const uint32_t blk = (uint32_t)(warp * BPW + lane / LPB);
-    const bool exists = blk < Gt && !s_bad;
-    const uint64_t kg = k0 + blk;
-    const int len = exists ? (int)min_u64(b, g.n - kg * b) : 0;
-    int nvalid = len - sub * VPL;
-    nvalid = nvalid < 0 ? 0 : (nvalid > VPL ? VPL : nvalid);
-    const bool full = nvalid == VPL;
-    const bool nonconst = exists && ((sm_state[blk >> 3] >> (blk & 7)) & 1u);
-    const uint32_t rank = nonconst ? sm_rank[blk] : 0u;
-    const int rq = nonconst ? (int)rec[nn_t * (b / 4) + rank] : 0;
-    const bool raw = nonconst && rq == 0xFF;
-    const bool coded = nonconst && !raw;
-    bool ok = !coded || (rq >= 1 + F::E && rq <= W);
-    const int s = (8 - (rq & 7)) & 7;
-    const int q = coded && ok ? (rq + s) >> 3 : 2;
-    const int lmax = q < 3 ? q : 3;
-    uint32_t codes[NCODE];
-#pragma unroll
-    for (int i = 0; i < NCODE; ++i) codes[i] = 0;
-    if (coded) {
-        const uint8_t *lead = rec + rank * (b / 4) + sub * (VPL / 4);
-        if constexpr (NCODE == 2) {
-            const uint2 v = *reinterpret_cast<const uint2 *>(lead);
-            codes[0] = v.x;
-            codes[1] = v.y;
-        } else {
-            codes[0] = *reinterpret_cast<const uint32_t *>(lead);
-        }
-        // codes past the end are 0; no code exceeds min(3, q)
-#pragma unroll
-        for (int i = 0; i < NCODE; ++i) {
-            const int nv = nvalid - 16 * i;
-            const uint32_t vm = nv >= 16 ? 0xFFFFFFFFu : (nv <= 0 ? 0u : (0xFFFFFFFFu >> (2 * (16 - nv))));
-            if (codes[i] & ~vm) ok = false;
-            if (lmax == 2 && (codes[i] & (codes[i] >> 1) & 0x55555555u)) ok = false;
-        }
-    }
-    uint32_t suml = 0;
-#pragma unroll
-    for (int i = 0; i < NCODE; ++i) suml += __popc(codes[i] & 0x55555555u) + 2 * __popc(codes[i] & 0xAAAAAAAAu);
-    uint32_t mk = coded ? (uint32_t)(nvalid * q) - suml : (raw ? (uint32_t)nvalid * w : 0u);
-    const uint32_t segmask = (LPB == 32 ? kFull : ((1u << LPB) - 1u)) << (lane & ~(LPB - 1));
-    {
-        const uint32_t bal = __ballot_sync(kFull, ok);
-        ok = (bal & segmask) == segmask;
-    }
-#pragma unroll
-    for (int d = 1; d < LPB; d <<= 1) mk += __shfl_xor_sync(kFull, mk, d);
-    if (exists && sub == 0) {
-        sm_mk[blk] = nonconst ? mk : 0u;
-        if (!ok) s_bad |= 1;
-    }
-    __syncthreads();
-    if (warp == 0 && !s_bad) {
-        const uint32_t per = (Gt + 31) / 32;
-        const uint32_t lo = min(lane * per, Gt), hi = min(lo + per, Gt);
-        uint32_t c = 0;
-        for (uint32_t kk = lo; kk < hi; ++kk) c += sm_mk[kk];
-        uint32_t tot;
-        uint32_t e = warp_exclusive_scan(c, &tot);
-        for (uint32_t kk = lo; kk < hi; ++kk) {
-            sm_midoff[kk] = e;
-            e += sm_mk[kk];
-        }
-        if (lane == 0) {
-            s_mid = tot;
-            const uint64_t used = (uint64_t)nn_t * (b / 4 + 1) + tot;
-            if (pad16(used) != size) s_bad |= 1;
-        }
-    }
-    __syncthreads();
-    if (!s_bad) {
-        // the record's pad bytes must be zero
-        const uint32_t used = nn_t * (b / 4 + 1) + s_mid;
-        for (uint32_t i = used + tid; i < size; i += kThreads)
-            if (rec[i]) s_bad |= 1;
-    }
-    __syncthreads();
-    if (s_bad) {
-        if (tid == 0) flag_status(a.status, s_bad & 2 ? 6u : 3u);
-        if (tid == 0 && size && (s_bad & 2)) mbar_wait_bounded(&bar, 0, a.copy_ns);
+        // do not leave while a copy may still be writing into shared memory
+        for (int st = 0; st < kDStages; ++st)
+            if (copy_last[st]) mbar_wait_bounded(&full[st], copy_phase[st] & 1u, a.copy_ns);
         return;
     }
 
-    // ---- 3. decode ----------------------------------------------------------
-    const uint32_t mbase = exists ? nn_t * (b / 4 + 1) + sm_midoff[blk] : 0u;
-    const U mu_bits = exists ? sm_mu[blk] : U(0);
-    U x[VPL];
+    // ---- decoders (warps 0..7) ---------------------------------------------
+    for (uint32_t it = 0;; ++it) {
+        const int st = (int)(it % kDStages);
+        const uint32_t k = it / kDStages;
+        if (!mbar_wait_bounded(&full[st], k & 1u, a.copy_ns)) s_abort = 1;
+        const uint32_t tile = st_tile[st];
+        const uint32_t size = st_size[st];
+        uint8_t *rec = smem + L.rec[st];
+        uint32_t *sm_mk = reinterpret_cast<uint32_t *>(smem + L.mk[st]);
+        const uint64_t k0 = (uint64_t)tile * G;
+        const uint32_t Gt = tile < g.ntiles ? (uint32_t)min_u64(G, g.nb - k0) : 0u;
 
-    // per-lane counts of values with code <= j (j = 0, 1, 2), packed, and
-    // their exclusive scan over the block's lanes (every lane runs this)
-    using CntT = std::conditional_t<(LPB * VPL > 1023), unsigned long long, uint32_t>;
-    constexpr int FB = LPB * VPL > 1023 ? 16 : 10;
-    constexpr CntT FM = (CntT(1) << FB) - 1;
-    CntT cnt = 0;
-    if (coded) {
+        // ---- ranks, codes, mid-byte counts --------------------------------
+        const int sub = lane % LPB;
+        const uint32_t blk = (uint32_t)(warp * BPW + lane / LPB);
+        const bool exists = blk < Gt && !st_bad[st];
+        const uint64_t kg = k0 + blk;
+        const int len = exists ? (int)min_u64(b, g.n - kg * b) : 0;
+        int nvalid = len - sub * VPL;
+        nvalid = nvalid < 0 ? 0 : (nvalid > VPL ? VPL : nvalid);
+        const bool full_lane = nvalid == VPL;
+        // rank of the block among the tile's non-constant blocks: a popcount
+        // of the tile's state bits below it (the tile's bits start at a byte)
+        uint32_t rank = 0;
+        bool nonconst = false;
+        uint32_t nn_t = 0;
+        if (tile < g.ntiles) {
+            const uint8_t *stb = a.in + g.off_state + k0 / 8;
+            for (uint32_t i = 0; i < (Gt + 7) / 8; i += 4) {
+                uint32_t wv = 0;
 #pragma unroll
-        for (int i = 0; i < NCODE; ++i) {
-            const int nv = nvalid - 16 * i;
-            const uint32_t vm = nv >= 16 ? 0x55555555u : (nv <= 0 ? 0u : (0x55555555u >> (2 * (16 - nv))));
-            const uint32_t lo = codes[i] & 0x55555555u, hi = (codes[i] >> 1) & 0x55555555u;
-            cnt += (CntT)__popc(~(lo | hi) & vm) | ((CntT)__popc(~hi & vm) << FB) |
-                   ((CntT)__popc(~(lo & hi) & vm) << (2 * FB));
-        }
-    }
-    CntT incl = cnt;
-#pragma unroll
-    for (int d = 1; d < LPB; d <<= 1) {
-        const CntT y = __shfl_up_sync(kFull, incl, d);
-        if (sub >= d) incl += y;
-    }
-    const CntT tot = __shfl_sync(kFull, incl, (lane & ~(LPB - 1)) + LPB - 1);
-    const CntT off = incl - cnt;
-    const uint32_t n0 = (uint32_t)(tot & FM), n1 = (uint32_t)((tot >> FB) & FM),
-                   n2 = (uint32_t)((tot >> (2 * FB)) & FM);
-    const uint32_t cj[3] = {(uint32_t)(cnt & FM), (uint32_t)((cnt >> FB) & FM), (uint32_t)((cnt >> (2 * FB)) & FM)};
-    uint32_t pos0 = mbase + (uint32_t)(off & FM);
-    uint32_t pos1 = mbase + n0 + (uint32_t)((off >> FB) & FM);
-    uint32_t pos2 = mbase + n0 + n1 + (uint32_t)((off >> (2 * FB)) & FM);
-    const uint32_t dense0 = mbase + n0 + n1 + n2 + (uint32_t)sub * VPL;
-
-    // carries into the lane for the planes that can inherit (j < lmax): the
-    // last own byte of the nearest lower lane of the block that owns one
-    uint32_t carry[3];
-    {
-        const uint32_t below = segmask & ((1u << lane) - 1u);
-        const uint32_t pj[3] = {pos0, pos1, pos2};
-#pragma unroll
-        for (int j = 0; j < 3; ++j) {
-            const bool has = coded && j < lmax && cj[j] > 0;
-            const uint32_t last = has ? rec[pj[j] + cj[j] - 1] : 0u;
-            const uint32_t m = __ballot_sync(kFull, has) & below;
-            const uint32_t v = __shfl_sync(kFull, last, m ? 31 - __clz(m) : 0);
-            carry[j] = m ? v : 0u;
-        }
-    }
-
-    if (coded) {
-        const T mu = F::from(mu_bits);
-#pragma unroll
-        for (int gq = 0; gq < VPL / 4; ++gq) {
-            uint32_t code8 = (codes[gq >> 2] >> (8 * (gq & 3))) & 0xFFu;
-            uint32_t dense8 = 0;
-            if (!full) {
-                const int nv = nvalid - 4 * gq;
-                const uint32_t inval = nv >= 4 ? 0u : (nv <= 0 ? 0xFFu : (0xFFu << (2 * nv)) & 0xFFu);
-                code8 |= inval;
-                dense8 = inval;
-            }
-            // plane words: byte k = byte j of value 4gq + k
-            uint32_t P[W / 8];
-#pragma unroll
-            for (int j = 0; j < W / 8; ++j) P[j] = 0;
-            {
-                const uint32_t e0 = lut->expand[code8];
-                P[0] = dprmt(load_run(rec, pos0), 0, e0);
-                pos0 += e0 >> 16;
-                const uint32_t e1 = lut->expand[256 + code8];
-                P[1] = dprmt(load_run(rec, pos1), 0, e1);
-                pos1 += e1 >> 16;
-                if (q >= 3) {
-                    const uint32_t e2 = lut->expand[512 + code8];
-                    P[2] = dprmt(load_run(rec, pos2), 0, e2);
-                    pos2 += e2 >> 16;
-                }
-                if (q >= 4) {
-                    const uint32_t sel = full ? 0x3210u : lut->expand[512 + dense8];
-#pragma unroll
-                    for (int j = 3; j < W / 8; ++j)
-                        if (j < q) P[j] = dprmt(load_run(rec, dense0 + (uint32_t)(j - 3) * len + 4 * gq), 0, sel);
+                for (int j = 0; j < 4; ++j)
+                    if (i + j < (Gt + 7) / 8) wv |= (uint32_t)stb[i + j] << (8 * j);
+                const uint32_t base = i * 8;
+                if (Gt - base < 32) wv &= (1u << (Gt - base)) - 1u;
+                nn_t += __popc(wv);
+                if (exists && blk >= base) {
+                    if (blk < base + 32) {
+                        rank += __popc(wv & ((1u << (blk - base)) - 1u));
+                        nonconst = (wv >> (blk - base)) & 1u;
+                    } else {
+                        rank += __popc(wv);
+                    }
                 }
             }
-            // leading bytes: copy the nearest earlier owner forward
-            P[0] = dprmt(P[0], carry[0], lut->carry[code8]);
-            carry[0] = P[0] >> 24;
-            P[1] = dprmt(P[1], carry[1], lut->carry[256 + code8]);
-            carry[1] = P[1] >> 24;
-            if (lmax >= 3) {
-                P[2] = dprmt(P[2], carry[2], lut->carry[512 + code8]);
-                carry[2] = P[2] >> 24;
-            }
-            // planes back to words: t = (P0.k, P1.k, P2.k, P3.k), most significant first
-            U t[4];
-            if constexpr (NPW == 1) {
-                uint32_t Wq[4];
-                transpose4d(P[3], P[2], P[1], P[0], Wq);
+        }
+        bool ok = (uint64_t)nn_t * (b / 4 + 1) <= size;
+        nonconst = nonconst && ok;
+        const int rq = nonconst ? (int)rec[nn_t * (b / 4) + rank] : 0;
+        const bool raw = nonconst && rq == 0xFF;
+        const bool coded = nonconst && !raw;
+        if (coded && !(rq >= 1 + F::E && rq <= W)) ok = false;
+        const int s = (8 - (rq & 7)) & 7;
+        const int q = coded && ok ? (rq + s) >> 3 : 2;
+        const int lmax = q < 3 ? q : 3;
+        uint32_t codes[NCODE];
 #pragma unroll
-                for (int k = 0; k < 4; ++k) t[k] = Wq[3 - k];
+        for (int i = 0; i < NCODE; ++i) codes[i] = 0;
+        if (coded && ok) {
+            const uint8_t *lead = rec + rank * (b / 4) + sub * (VPL / 4);
+            if constexpr (NCODE == 2) {
+                const uint2 v = *reinterpret_cast<const uint2 *>(lead);
+                codes[0] = v.x;
+                codes[1] = v.y;
             } else {
-                uint32_t Wh[4], Wl[4];
-                transpose4d(P[3], P[2], P[1], P[0], Wh);
-                transpose4d(P[7], P[6], P[5], P[4], Wl);
-#pragma unroll
-                for (int k = 0; k < 4; ++k) t[k] = ((U)Wh[3 - k] << 32) | (U)Wl[3 - k];
+                codes[0] = *reinterpret_cast<const uint32_t *>(lead);
             }
+            // codes past the end are 0; no code exceeds min(3, q)
 #pragma unroll
-            for (int k = 0; k < 4; ++k) x[4 * gq + k] = F::bits(F::add(F::from((U)(t[k] << s)), mu));
-        }
-    } else if (raw) {
-        const uint8_t *p = rec + mbase + (uint32_t)sub * VPL * w;
-#pragma unroll
-        for (int m = 0; m < VPL; ++m) {
-            U u = 0;
-            if (m < nvalid) {
-#pragma unroll
-                for (int i = 0; i < w; ++i) u |= (U)p[m * w + i] << (8 * i);
+            for (int i = 0; i < NCODE; ++i) {
+                const int nv = nvalid - 16 * i;
+                const uint32_t vm = nv >= 16 ? 0xFFFFFFFFu : (nv <= 0 ? 0u : (0xFFFFFFFFu >> (2 * (16 - nv))));
+                if (codes[i] & ~vm) ok = false;
+                if (lmax == 2 && (codes[i] & (codes[i] >> 1) & 0x55555555u)) ok = false;
             }
-            x[m] = u;
         }
-    } else {
+        uint32_t suml = 0;
 #pragma unroll
-        for (int m = 0; m < VPL; ++m) x[m] = mu_bits;
-    }
+        for (int i = 0; i < NCODE; ++i) suml += __popc(codes[i] & 0x55555555u) + 2 * __popc(codes[i] & 0xAAAAAAAAu);
+        uint32_t mk = coded ? (uint32_t)(nvalid * q) - suml : (raw ? (uint32_t)nvalid * w : 0u);
+        const uint32_t segmask = (LPB == 32 ? kFull : ((1u << LPB) - 1u)) << (lane & ~(LPB - 1));
+        {
+            const uint32_t bal = __ballot_sync(kFull, ok);
+            ok = (bal & segmask) == segmask;
+        }
+#pragma unroll
+        for (int d = 1; d < LPB; d <<= 1) mk += __shfl_xor_sync(kFull, mk, d);
+        if (blk < G && sub == 0) sm_mk[blk] = (exists && nonconst) ? mk : 0u;
+        if (!ok && exists) st_bad[st] = 1;
+        decoder_sync();
+        if (s_abort || tile >= g.ntiles) break;
 
-    if (exists && nvalid > 0) {
-        U *dst = reinterpret_cast<U *>(a.out) + kg * b + sub * VPL;
-        if (full) {
-#pragma unroll
-            for (int i = 0; i < VPL * w / 16; ++i) {
-                uint4 v;
-                U *u = reinterpret_cast<U *>(&v);
-#pragma unroll
-                for (int k = 0; k < 16 / w; ++k) u[k] = x[i * (16 / w) + k];
-                reinterpret_cast<uint4 *>(dst)[i] = v;
-            }
-        } else {
-#pragma unroll
-            for (int m = 0; m < VPL; ++m)
-                if (m < nvalid) dst[m] = x[m];
+        // ---- mid-byte offsets: every warp scans the tile's counts ----------
+        uint32_t midoff, total;
+        {
+            const uint32_t per = (Gt + 31) / 32;
+            const uint32_t lo = min(lane * per, Gt), hi = min(lo + per, Gt);
+            uint32_t c = 0;
+            for (uint32_t kk = lo; kk < hi; ++kk) c += sm_mk[kk];
+            uint32_t e = warp_exclusive_scan(c, &total);
+            const uint32_t chunk = blk / (per ? per : 1u);
+            uint32_t before = __shfl_sync(kFull, e, chunk < 32 ? (int)chunk : 0);
+            for (uint32_t kk = chunk * per; kk < blk && kk < Gt; ++kk) before += sm_mk[kk];
+            midoff = before;
         }
+        const uint32_t used = nn_t * (b / 4 + 1) + total;
+        const bool bad = st_bad[st] || pad16(used) != size;
+        if (bad) {
+            if (tid == 0) flag_status(a.status, 3u);
+        } else {
+            // ---- decode --------------------------------------------------
+            const uint32_t mbase = nn_t * (b / 4 + 1) + midoff;
+            const U mu_bits = exists ? reinterpret_cast<const U *>(a.in + g.off_mu)[kg] : U(0);
+            U x[VPL];
+
+            using CntT = std::conditional_t<(LPB * VPL > 1023), unsigned long long, uint32_t>;
+            constexpr int FB = LPB * VPL > 1023 ? 16 : 10;
+            constexpr CntT FM = (CntT(1) << FB) - 1;
+            CntT cnt = 0;
+            if (coded) {
+#pragma unroll
+                for (int i = 0; i < NCODE; ++i) {
+                    const int nv = nvalid - 16 * i;
+                    const uint32_t vm = nv >= 16 ? 0x55555555u : (nv <= 0 ? 0u : (0x55555555u >> (2 * (16 - nv))));
+                    const uint32_t lo = codes[i] & 0x55555555u, hi = (codes[i] >> 1) & 0x55555555u;
+                    cnt += (CntT)__popc(~(lo | hi) & vm) | ((CntT)__popc(~hi & vm) << FB) |
+                           ((CntT)__popc(~(lo & hi) & vm) << (2 * FB));
+                }
+            }
+            CntT incl = cnt;
+#pragma unroll
+            for (int d = 1; d < LPB; d <<= 1) {
+                const CntT y = __shfl_up_sync(kFull, incl, d);
+                if (sub >= d) incl += y;
+            }
+            const CntT tot = __shfl_sync(kFull, incl, (lane & ~(LPB - 1)) + LPB - 1);
+            const CntT off = incl - cnt;
+            const uint32_t n0 = (uint32_t)(tot & FM), n1 = (uint32_t)((tot >> FB) & FM),
+                           n2 = (uint32_t)((tot >> (2 * FB)) & FM);
+            const uint32_t cj[3] = {(uint32_t)(cnt & FM), (uint32_t)((cnt >> FB) & FM),
+                                    (uint32_t)((cnt >> (2 * FB)) & FM)};
+            uint32_t pos0 = mbase + (uint32_t)(off & FM);
+            uint32_t pos1 = mbase + n0 + (uint32_t)((off >> FB) & FM);
+            uint32_t pos2 = mbase + n0 + n1 + (uint32_t)((off >> (2 * FB)) & FM);
+            const uint32_t dense0 = mbase + n0 + n1 + n2 + (uint32_t)sub * VPL;
+
+            // carries into the lane for the planes that can inherit (j < lmax):
+            // the last own byte of the nearest lower lane of the block that owns one
+            uint32_t carry[3];
+            {
+                const uint32_t below = segmask & ((1u << lane) - 1u);
+                const uint32_t pj[3] = {pos0, pos1, pos2};
+#pragma unroll
+                for (int j = 0; j < 3; ++j) {
+                    const bool has = coded && j < lmax && cj[j] > 0;
+                    const uint32_t last = has ? rec[pj[j] + cj[j] - 1] : 0u;
+                    const uint32_t m = __ballot_sync(kFull, has) & below;
+                    const uint32_t v = __shfl_sync(kFull, last, m ? 31 - __clz(m) : 0);
+                    carry[j] = m ? v : 0u;
+                }
+            }
+
+            if (coded) {
+                const T mu = F::from(mu_bits);
+#pragma unroll
+                for (int gq = 0; gq < VPL / 4; ++gq) {
+                    uint32_t code8 = (codes[gq >> 2] >> (8 * (gq & 3))) & 0xFFu;
+                    uint32_t dense8 = 0;
+                    if (!full_lane) {
+                        const int nv = nvalid - 4 * gq;
+                        const uint32_t inval = nv >= 4 ? 0u : (nv <= 0 ? 0xFFu : (0xFFu << (2 * nv)) & 0xFFu);
+                        code8 |= inval;
+                        dense8 = inval;
+                    }
+                    // plane words: byte k = byte j of value 4gq + k
+                    uint32_t P[W / 8];
+#pragma unroll
+                    for (int j = 0; j < W / 8; ++j) P[j] = 0;
+                    {
+                        const uint32_t e0 = lut->expand[code8];
+                        P[0] = dprmt(load_run(rec, pos0), 0, e0);
+                        pos0 += e0 >> 16;
+                        const uint32_t e1 = lut->expand[256 + code8];
+                        P[1] = dprmt(load_run(rec, pos1), 0, e1);
+                        pos1 += e1 >> 16;
+                        if (q >= 3) {
+                            const uint32_t e2 = lut->expand[512 + code8];
+                            P[2] = dprmt(load_run(rec, pos2), 0, e2);
+                            pos2 += e2 >> 16;
+                        }
+                        if (q >= 4) {
+                            const uint32_t sel = full_lane ? 0x3210u : lut->expand[512 + dense8];
+#pragma unroll
+                            for (int j = 3; j < W / 8; ++j)
+                                if (j < q)
+                                    P[j] = dprmt(load_run(rec, dense0 + (uint32_t)(j - 3) * len + 4 * gq), 0, sel);
+                        }
+                    }
+                    // leading bytes: copy the nearest earlier owner forward
+                    P[0] = dprmt(P[0], carry[0], lut->carry[code8]);
+                    carry[0] = P[0] >> 24;
+                    P[1] = dprmt(P[1], carry[1], lut->carry[256 + code8]);
+                    carry[1] = P[1] >> 24;
+                    if (lmax >= 3) {
+                        P[2] = dprmt(P[2], carry[2], lut->carry[512 + code8]);
+                        carry[2] = P[2] >> 24;
+                    }
+                    // planes back to words: t = (P0.k, P1.k, P2.k, P3.k), most significant first
+                    U t[4];
+                    if constexpr (NPW == 1) {
+                        uint32_t Wq[4];
+                        transpose4d(P[3], P[2], P[1], P[0], Wq);
+#pragma unroll
+                        for (int kk = 0; kk < 4; ++kk) t[kk] = Wq[3 - kk];
+                    } else {
+                        uint32_t Wh[4], Wl[4];
+                        transpose4d(P[3], P[2], P[1], P[0], Wh);
+                        transpose4d(P[7], P[6], P[5], P[4], Wl);
+#pragma unroll
+                        for (int kk = 0; kk < 4; ++kk) t[kk] = ((U)Wh[3 - kk] << 32) | (U)Wl[3 - kk];
+                    }
+#pragma unroll
+                    for (int kk = 0; kk < 4; ++kk) x[4 * gq + kk] = F::bits(F::add(F::from((U)(t[kk] << s)), mu));
+                }
+            } else if (raw) {
+                const uint8_t *p = rec + mbase + (uint32_t)sub * VPL * w;
+#pragma unroll
+                for (int m = 0; m < VPL; ++m) {
+                    U u = 0;
+                    if (m < nvalid) {
+#pragma unroll
+                        for (int i = 0; i < w; ++i) u |= (U)p[m * w + i] << (8 * i);
+                    }
+                    x[m] = u;
+                }
+            } else {
+#pragma unroll
+                for (int m = 0; m < VPL; ++m) x[m] = mu_bits;
+            }
+
+            if (exists && nvalid > 0) {
+                U *dst = reinterpret_cast<U *>(a.out) + kg * b + sub * VPL;
+                if (full_lane) {
+#pragma unroll
+                    for (int i = 0; i < VPL * w / 16; ++i) {
+                        uint4 v;
+                        U *u = reinterpret_cast<U *>(&v);
+#pragma unroll
+                        for (int kk = 0; kk < 16 / w; ++kk) u[kk] = x[i * (16 / w) + kk];
+                        reinterpret_cast<uint4 *>(dst)[i] = v;
+                    }
+                } else {
+#pragma unroll
+                    for (int m = 0; m < VPL; ++m)
+                        if (m < nvalid) dst[m] = x[m];
+                }
+            }
+            // strictness: the record's pad bytes must be zero
+            if (warp == 0)
+                for (uint32_t i = used + lane; i < size; i += 32)
+                    if (rec[i]) flag_status(a.status, 3u);
+        }
+        // this thread is done with the stage's record
+        dmbar_arrive(&empty[st]);
     }
 }
 
@@ -451,11 +498,18 @@ __global__ void __launch_bounds__(kThreads, (VPL * sizeof(T) > 128) ? 1 : 3) dec
 
 template <typename T, int LPB, int VPL>
 static cudaError_t launch_t(const DecompressArgs &a, cudaStream_t stream) {
-    const DSmem L = decompress_smem2(a.g.G, a.g.b, Fmt<T>::w);
+    const DSmem L = decompress_smem(a.g.G, a.g.b, Fmt<T>::w);
     auto kern = decompress_kernel<T, LPB, VPL>;
     cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total);
     if (err != cudaSuccess) return err;
-    kern<<<(unsigned)a.g.ntiles, kThreads, L.total, stream>>>(a);
+    int dev = 0, sms = 0, per_sm = 0;
+    if ((err = cudaGetDevice(&dev)) != cudaSuccess) return err;
+    if ((err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return err;
+    if ((err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kDThreads, L.total)) != cudaSuccess)
+        return err;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    const uint64_t grid = min_u64(a.g.ntiles, (uint64_t)sms * per_sm);
+    kern<<<(unsigned)grid, kDThreads, L.total, stream>>>(a);
     return cudaGetLastError();
 }
 
