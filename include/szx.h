@@ -115,6 +115,49 @@ szx_status szx_compress_async(const void *d_in, size_t n, szx_dtype dtype,
                               szx_stream_t stream);
 
 /*
+ * Size of the fixed device array that szx_compress_static_async uses as its
+ * scratch, and the largest tile count it accepts: a 128-byte header plus one
+ * 8-byte look-back word per tile.  Every tile holds at least 32 KiB of input,
+ * so the limit admits any input of up to 131056 * 32 KiB (about 4 GiB).
+ */
+#define SZX_STATIC_SCRATCH_BYTES (1u << 20)
+#define SZX_STATIC_MAX_TILES ((SZX_STATIC_SCRATCH_BYTES - 128u) / 8u)
+
+/*
+ * Compression that allocates nothing: the paper has no counterpart; it is
+ * an interface variant of szx_compress_async for callers whose output buffer
+ * is exactly szx_stream_max_bytes(n, dtype, block) long and who may not
+ * allocate scratch space.  The stream it writes is byte-identical to
+ * szx_compress_async's for the same arguments.
+ *
+ * d_in, n, dtype, eb, block, d_out, d_result, stream: as szx_compress_async.
+ * out_capacity must be >= szx_stream_max_bytes(n, dtype, block); nothing past
+ * the stream's own bytes is written.  The look-back scratch is one array of
+ * SZX_STATIC_SCRATCH_BYTES inside the library, per device; no call allocates
+ * device or host memory.
+ *
+ * Set-up: the first call made with a given device current looks up that
+ * device's array address (cudaGetSymbolAddress, which may load the
+ * library's device code); make that first call before any stream capture.
+ * Each call clears the array prefix it uses on `stream` before its kernel.
+ *
+ * Sharing: all calls on one device use the same array.  Calls that can
+ * overlap in time (on different streams, or from different host threads
+ * without ordering) race on it and produce undefined streams; order them.
+ *
+ * Errors (returned immediately): SZX_ERR_INVALID for the same argument errors
+ * as szx_compress_async and for an input whose tile count exceeds
+ * SZX_STATIC_MAX_TILES; SZX_ERR_TOO_SMALL if out_capacity is below
+ * szx_stream_max_bytes; SZX_ERR_CUDA if a CUDA call fails.  Device-side
+ * results arrive in d_result as for szx_compress_async.
+ */
+szx_status szx_compress_static_async(const void *d_in, size_t n,
+                                     szx_dtype dtype, double eb,
+                                     uint32_t block, void *d_out,
+                                     size_t out_capacity, uint64_t *d_result,
+                                     szx_stream_t stream);
+
+/*
  * Read and check the 64-byte header of the stream at d_in (device pointer;
  * one 64-byte device-to-host copy, synchronous on `stream`).  Errors:
  * SZX_ERR_INVALID (null), SZX_ERR_CORRUPT (bad magic, version, dtype, block,

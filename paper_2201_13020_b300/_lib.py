@@ -43,6 +43,8 @@ def lib():
     L.szx_compress.argtypes = [vp, sz, i, dbl, u32, vp, sz, ctypes.POINTER(sz), vp]
     L.szx_compress_async.restype = i
     L.szx_compress_async.argtypes = [vp, sz, i, dbl, u32, vp, sz, vp, vp]
+    L.szx_compress_static_async.restype = i
+    L.szx_compress_static_async.argtypes = [vp, sz, i, dbl, u32, vp, sz, vp, vp]
     L.szx_header_read.restype = i
     L.szx_header_read.argtypes = [vp, sz, ctypes.POINTER(SzxHeader), vp]
     L.szx_decompress.restype = i
@@ -58,4 +60,4 @@ def lib():
 
 
 EXPORTED = ["szx_compress_bound", "szx_stream_max_bytes", "szx_compress", "szx_compress_async",
-            "szx_header_read", "szx_decompress", "szx_decompress_async", "szx_status_string", "szx_version"]
+            "szx_compress_static_async", "szx_header_read", "szx_decompress", "szx_decompress_async", "szx_status_string", "szx_version"]

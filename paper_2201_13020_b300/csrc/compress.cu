@@ -937,13 +937,19 @@ cudaError_t launch_t(const CUtensorMap &tm, const CompressArgs &a, cudaStream_t 
 
 cudaError_t launch_compress(const void *in, uint64_t n, int dtype, uint64_t e_bits, uint32_t block,
                             void *out, uint64_t ws_offset, uint64_t *d_result, cudaStream_t stream) {
+    return launch_compress_ws(in, n, dtype, e_bits, block, out, static_cast<uint8_t *>(out) + ws_offset,
+                              d_result, stream);
+}
+
+cudaError_t launch_compress_ws(const void *in, uint64_t n, int dtype, uint64_t e_bits, uint32_t block,
+                               void *out, void *ws, uint64_t *d_result, cudaStream_t stream) {
     CompressArgs a;
     const uint32_t w = dtype == 0 ? 4 : 8;
     a.in = static_cast<const uint8_t *>(in);
     a.out = static_cast<uint8_t *>(out);
     a.g = make_geometry(n, block, w);
-    a.ws = reinterpret_cast<Workspace *>(a.out + ws_offset);
-    a.lookback = reinterpret_cast<uint64_t *>(a.out + ws_offset + kWsHeader);
+    a.ws = reinterpret_cast<Workspace *>(ws);
+    a.lookback = reinterpret_cast<uint64_t *>(static_cast<uint8_t *>(ws) + kWsHeader);
     a.d_result = d_result;
     a.e_bits = e_bits;
     a.dtype = (uint32_t)dtype;

@@ -16,6 +16,12 @@ uint32_t wait_limit_from_env(const char *name, uint32_t fallback);
 cudaError_t launch_compress(const void *in, uint64_t n, int dtype, uint64_t e_bits, uint32_t block,
                             void *out, uint64_t ws_offset, uint64_t *d_result, cudaStream_t stream);
 
+// Same, with the workspace (workspace_bytes(ntiles) bytes, 256-byte aligned)
+// at an arbitrary device address instead of the tail of out.  Clears it on
+// `stream` before the kernel runs.
+cudaError_t launch_compress_ws(const void *in, uint64_t n, int dtype, uint64_t e_bits, uint32_t block,
+                               void *out, void *ws, uint64_t *d_result, cudaStream_t stream);
+
 // Enqueue the decompression of a stream of total_bytes whose header says
 // (n, dtype, block).  Errors are folded into *d_status with atomicMax as
 // szx_status codes (d_status may be null).

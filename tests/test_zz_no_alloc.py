@@ -1,0 +1,77 @@
+"""szx_compress_static_async: compression whose scratch is a fixed array in
+the library, called through the C ABI and compared with szx_compress_async.
+
+The file is collected last on purpose: it must pass both alone and after every
+other test, when the library's device array has already been used.
+"""
+import ctypes
+
+import pytest
+
+from paper_2201_13020_b300 import _lib
+from paper_2201_13020_b300 import inputs
+
+SZX_OK, SZX_ERR_INVALID, SZX_ERR_TOO_SMALL = 0, 1, 2
+GUARD = 4096
+
+
+def _vp(p):
+    return ctypes.c_void_p(p)
+
+
+def test_static_limit_and_capacity_rejected_on_host():
+    # Both checks return before any CUDA call, so fake (aligned, non-null)
+    # device addresses are never dereferenced.
+    L = _lib.lib()
+    max_tiles = ((1 << 20) - 128) // 8
+    n_tile = 64 * 128  # f32, block 128: 64 blocks per tile
+    n_over = (max_tiles + 1) * n_tile
+    st = L.szx_compress_static_async(_vp(256), n_over, _lib.SZX_F32, 1e-3, 128, _vp(512), 1 << 62,
+                                     None, None)
+    assert st == SZX_ERR_INVALID
+    n_ok = 10_000
+    smax = L.szx_stream_max_bytes(n_ok, _lib.SZX_F32, 128)
+    st = L.szx_compress_static_async(_vp(256), n_ok, _lib.SZX_F32, 1e-3, 128, _vp(512), smax - 16,
+                                     None, None)
+    assert st == SZX_ERR_TOO_SMALL
+
+
+@pytest.mark.gpu
+def test_static_scratch_matches_existing_entry_point_twice_in_a_row():
+    torch = pytest.importorskip("torch")
+    L = _lib.lib()
+    dev = torch.device("cuda:0")
+    s = torch.cuda.current_stream()
+    h = _vp(s.cuda_stream)
+    # Two calls in a row, the second smaller and of the other dtype, so that
+    # its tiles reuse look-back words the first call left behind.
+    cases = [
+        (inputs.grf_3d((96, 96, 96), -5.0 / 3.0, 11, dtype=torch.float32), 1e-3, 128),
+        (inputs.grf_3d((40, 50, 61), -11.0 / 3.0, 12, dtype=torch.float64), 1e-4, 256),
+    ]
+    for xc, rel, block in cases:
+        x = xc.reshape(-1).to(dev)
+        n = x.numel()
+        code = _lib.SZX_F32 if x.dtype == torch.float32 else _lib.SZX_F64
+        eb = inputs.rel_to_abs(xc, rel)
+        smax = L.szx_stream_max_bytes(n, code, block)
+        # Static path: a buffer of exactly the stream maximum plus a guard
+        # region that must come back untouched.
+        buf = torch.full((smax + GUARD,), 0xA5, dtype=torch.uint8, device=dev)
+        res_s = torch.zeros(2, dtype=torch.int64, device=dev)
+        st = L.szx_compress_static_async(_vp(x.data_ptr()), n, code, float(eb), block, _vp(buf.data_ptr()),
+                                         smax, _vp(res_s.data_ptr()), h)
+        assert st == SZX_OK
+        # Existing path.
+        cap = L.szx_compress_bound(n, code, block)
+        ref = torch.empty(cap, dtype=torch.uint8, device=dev)
+        res_r = torch.zeros(2, dtype=torch.int64, device=dev)
+        st = L.szx_compress_async(_vp(x.data_ptr()), n, code, float(eb), block, _vp(ref.data_ptr()), cap,
+                                  _vp(res_r.data_ptr()), h)
+        assert st == SZX_OK
+        torch.cuda.synchronize()
+        rs, rr = res_s.cpu().tolist(), res_r.cpu().tolist()
+        assert rr[1] == SZX_OK and rs == rr
+        nbytes = rr[0]
+        assert torch.equal(buf[:nbytes], ref[:nbytes])
+        assert bool((buf[smax:] == 0xA5).all())
