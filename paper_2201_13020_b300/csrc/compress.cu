@@ -902,20 +902,6 @@ __global__ void __launch_bounds__(kCThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
 
 namespace {
 
-PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
-    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-    static std::once_flag once;
-    std::call_once(once, [] {
-        void *p = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
-                cudaSuccess &&
-            q == cudaDriverEntryPointSuccess)
-            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
-    });
-    return fn;
-}
-
 template <typename T, int LPB, int VPL>
 cudaError_t launch_t(const CUtensorMap &tm, const CompressArgs &a, cudaStream_t stream) {
     const CSmem L = compress_smem(a.g.G, a.g.b, Fmt<T>::w);
@@ -957,21 +943,7 @@ cudaError_t launch_compress_ws(const void *in, uint64_t n, int dtype, uint64_t e
     a.copy_ns = 1000ull * wait_limit_from_env("SZX_COPY_US", 1000000u);
     a.rows_full = n * w / 128;
     CUtensorMap tm;
-    std::memset(&tm, 0, sizeof(tm));
-    a.use_tma = 0;
-    if (a.rows_full > 0 && a.rows_full < (1ull << 31)) {
-        auto enc = tensor_map_encoder();
-        if (enc) {
-            cuuint64_t dims[2] = {32, a.rows_full};
-            cuuint64_t strides[1] = {128};
-            cuuint32_t box[2] = {32, 256};
-            cuuint32_t estr[2] = {1, 1};
-            CUresult r = enc(&tm, CU_TENSOR_MAP_DATA_TYPE_UINT32, 2, const_cast<void *>(in), dims, strides, box,
-                             estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-                             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-            a.use_tma = r == CUDA_SUCCESS ? 1u : 0u;
-        }
-    }
+    a.use_tma = encode_row_map(&tm, in, a.rows_full) ? 1u : 0u;
     cudaError_t err = cudaMemsetAsync(a.ws, 0, workspace_bytes(a.g.ntiles), stream);
     if (err != cudaSuccess) return err;
     if (dtype == 0) {
@@ -994,6 +966,39 @@ cudaError_t launch_compress_ws(const void *in, uint64_t n, int dtype, uint64_t e
         }
     }
     return cudaErrorInvalidValue;
+}
+
+// ---------------------------------------------------------------------------
+
+namespace {
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    });
+    return fn;
+}
+}  // namespace
+
+bool encode_row_map(CUtensorMap *tm, const void *base, uint64_t rows) {
+    std::memset(tm, 0, sizeof(*tm));
+    if (rows == 0 || rows >= (1ull << 31)) return false;
+    auto enc = tensor_map_encoder();
+    if (!enc) return false;
+    cuuint64_t dims[2] = {32, rows};
+    cuuint64_t strides[1] = {128};
+    cuuint32_t box[2] = {32, 256};
+    cuuint32_t estr[2] = {1, 1};
+    const CUresult r = enc(tm, CU_TENSOR_MAP_DATA_TYPE_UINT32, 2, const_cast<void *>(base), dims, strides, box, estr,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
 }
 
 }  // namespace szx

@@ -3,9 +3,18 @@
 // Persistent CTAs decode tiles of G blocks.  The tile index written by the
 // compressor gives each record's offset, so tiles decode independently: no
 // device-wide scan is left for decompression (the paper's GPU decoder, Sec.
-// V-B, runs a prefix scan of the mid-byte counts first).  Per CTA, a producer
-// warp bulk-copies records (TMA, cp.async.bulk + mbarrier) into a ring of
-// three stages while eight decoding warps work on earlier ones.
+// V-B, runs a prefix scan of the mid-byte counts first).  Per CTA, three warp
+// roles share a ring of three stage buffers through mbarriers:
+//   producer (one thread): per tile, bulk-copies (cp.async.bulk) the record,
+//     the tile's mu values and a 16-byte-aligned window of its state bits into
+//     a stage; the tile index entries are loaded one tile ahead, so no global
+//     latency sits between two copies;
+//   eight decoding warps: decode the stage's record into registers, then
+//     write the values back into the same stage buffer as the output tile, in
+//     the 128-byte-swizzled row layout of the TMA tensor store;
+//   storer (one thread): stores the tile with a 2-D TMA tensor store (rows of
+//     128 bytes), then frees the stage for the producer.
+// The decoders therefore touch global memory only for the ragged last row.
 //
 // Work layout as in the compressor: every lane owns 128 contiguous output
 // bytes (32 f32 or 16 f64 values); a block of b values spans LPB = b / VPL
@@ -25,7 +34,9 @@
 //      own byte of the nearest lower lane of the block that owns one (a ballot
 //      and a shuffle) -- the paper's index propagation (Sec. V-B) in one step
 //      per plane.  A byte transpose turns planes back into words; then
-//      v' = t << s and d' = RN(v' + mu), stored with 16-byte stores.
+//      v' = t << s and d' = RN(v' + mu);
+//   4. after a second barrier (the record is no longer read) the values go to
+//      the stage buffer and the storer takes over.
 #include <type_traits>
 
 #include "szx_device.cuh"
@@ -43,7 +54,9 @@ struct DecompressArgs {
     uint32_t dtype;
     uint32_t check_header;  // re-check the stream header on the device
     uint64_t total_bytes;
-    uint64_t copy_ns;  // wall-time limit of the record copy wait
+    uint64_t copy_ns;    // wall-time limit of the record copy wait
+    uint64_t rows_full;  // 128-byte output rows fully inside the output
+    uint32_t use_tma;    // store full rows with the tensor store (else plain stores)
 };
 
 __device__ __forceinline__ void flag_status(uint32_t *status, uint32_t code) {
@@ -102,26 +115,34 @@ __device__ __forceinline__ uint32_t load_run(const uint8_t *buf, uint32_t p) {
 }
 
 constexpr int kDStages = 3;
-constexpr int kDConsumers = kThreads;     // 8 decoding warps
-constexpr int kDThreads = kDConsumers + 32;  // + a producer warp
+constexpr int kDConsumers = kThreads;                 // 8 decoding warps
+constexpr int kDProducerWarp = kDConsumers / 32;      // warp 8
+constexpr int kDStorerWarp = kDProducerWarp + 1;      // warp 9
+constexpr int kDThreads = kDConsumers + 64;
+constexpr uint32_t kBitsWindow = 64;  // 16-byte-aligned window holding a tile's state bits
 
+// Per stage (1024-byte aligned, for the swizzled tensor store): the buffer
+// that receives the record and then holds the decoded tile, the tile's mu
+// values, its state-bit window and its blocks' mid-byte counts.
 struct DSmem {
-    uint32_t rec[kDStages], rec_bytes, mk[kDStages], lut, total;
+    uint32_t buf[kDStages], mu[kDStages], bits[kDStages], mk[kDStages];
+    uint32_t lut, total;
 };
 __host__ __device__ inline DSmem decompress_smem(uint32_t G, uint32_t b, uint32_t w) {
     DSmem s;
-    uint32_t o = 0;
-    auto take = [&](uint32_t bytes, uint32_t align) {
-        o = (o + align - 1) & ~(align - 1);
-        const uint32_t at = o;
-        o += bytes;
-        return at;
-    };
-    s.rec_bytes = record_max_bytes(G, b, w) + 16;
-    for (int i = 0; i < kDStages; ++i) s.rec[i] = take(s.rec_bytes, 128);
-    for (int i = 0; i < kDStages; ++i) s.mk[i] = take(G * 4, 16);
-    s.lut = take(sizeof(DecodeLut), 16);
-    s.total = o;
+    const uint32_t tile = G * b * w;
+    const uint32_t rec = record_max_bytes(G, b, w) + 16;  // + slack for the 8-byte run reads
+    const uint32_t body = ((tile > rec ? tile : rec) + 15) & ~15u;
+    const uint32_t mub = (G * w + 15) & ~15u;
+    const uint32_t stage = (body + mub + kBitsWindow + 4 * G + 1023) & ~1023u;
+    for (int i = 0; i < kDStages; ++i) {
+        s.buf[i] = i * stage;
+        s.mu[i] = s.buf[i] + body;
+        s.bits[i] = s.mu[i] + mub;
+        s.mk[i] = s.bits[i] + kBitsWindow;
+    }
+    s.lut = kDStages * stage;
+    s.total = s.lut + (uint32_t)sizeof(DecodeLut) + 1024;  // + slack to realign the dynamic base
     return s;
 }
 
@@ -134,29 +155,37 @@ __device__ __forceinline__ void dmbar_arrive(uint64_t *bar) {
         : "memory");
 }
 
-// Persistent decoder: a producer warp bulk-copies the records of the CTA's
-// tiles (tile = blockIdx.x + k * gridDim.x) into a ring of stages; eight
-// decoding warps turn each record into the tile's values.
+// Persistent decoder: tile = blockIdx.x + k * gridDim.x.
 template <typename T, int LPB, int VPL>
-__global__ void __launch_bounds__(kDThreads, (VPL * sizeof(T) > 128) ? 1 : 2) decompress_kernel(DecompressArgs a) {
+__global__ void __launch_bounds__(kDThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
+    decompress_kernel(const __grid_constant__ CUtensorMap tmap, DecompressArgs a) {
     using F = Fmt<T>;
     using U = typename F::U;
     constexpr int w = F::w;
     constexpr int W = F::W;
     constexpr int BPW = 32 / LPB;
     constexpr int NCODE = (2 * VPL + 31) / 32;
-    constexpr int NPW = W / 32;  // 32-bit words per value
+    constexpr int NPW = W / 32;         // 32-bit words per value
+    constexpr int RPL = VPL * w / 128;  // 128-byte rows per lane
+    static_assert(RPL >= 1, "lane geometry");
 
-    extern __shared__ __align__(128) uint8_t smem[];
-    __shared__ __align__(8) uint64_t full[kDStages], empty[kDStages];
-    __shared__ uint32_t st_tile[kDStages], st_size[kDStages], st_bad[kDStages];
+    extern __shared__ __align__(16) uint8_t smem_raw[];  // realigned to 1024 below
+    // full: record, mu and state bits copied in; done: tile decoded into the
+    // stage; empty: tile stored, stage free
+    __shared__ __align__(8) uint64_t full[kDStages], done[kDStages], empty[kDStages];
+    // st_bad: set by the producer (index or header fault); st_dbad: set by a
+    // decoder (bad codes), read only after the first barrier
+    __shared__ uint32_t st_tile[kDStages], st_size[kDStages], st_bad[kDStages], st_dbad[kDStages],
+        st_boff[kDStages], st_store[kDStages];
     __shared__ uint32_t s_abort;
 
+    uint8_t *smem = smem_raw + ((1024u - (smem_addr(smem_raw) & 1023u)) & 1023u);
     const Geometry &g = a.g;
     const uint32_t b = g.b, G = g.G;
     const DSmem L = decompress_smem(G, b, w);
     const DecodeLut *lut = reinterpret_cast<const DecodeLut *>(smem + L.lut);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    constexpr uint32_t kNone = 0xFFFFFFFFu;
 
     {
         const uint4 *src = reinterpret_cast<const uint4 *>(&kDecodeLut);
@@ -166,33 +195,47 @@ __global__ void __launch_bounds__(kDThreads, (VPL * sizeof(T) > 128) ? 1 : 2) de
     if (tid == 0) {
         for (int i = 0; i < kDStages; ++i) {
             mbar_init(&full[i], 1);
-            mbar_init(&empty[i], kDConsumers);
-            st_tile[i] = 0xFFFFFFFFu;
-            st_size[i] = st_bad[i] = 0;
+            mbar_init(&done[i], kDConsumers / 32);
+            mbar_init(&empty[i], 1);
+            st_tile[i] = kNone;
+            st_size[i] = st_bad[i] = st_dbad[i] = st_boff[i] = st_store[i] = 0;
         }
         fence_mbar_init();
         s_abort = 0;
     }
     __syncthreads();
 
-    if (warp == kThreads / 32) {
-        // ---- producer: record copies into the stage ring --------------------
+    if (warp == kDProducerWarp) {
+        // ---- producer: record, mu and state-bit copies into the ring --------
         if (lane != 0) return;
         const uint32_t rec_max = record_max_bytes(G, b, w);
+        const uint64_t *idx = reinterpret_cast<const uint64_t *>(a.in + g.off_index);
         bool copy_last[kDStages] = {};
         uint32_t copy_phase[kDStages] = {};
+        uint64_t n0 = 0, n1 = 0;  // index entries of the next tile
+        if (blockIdx.x < g.ntiles) {
+            n0 = idx[blockIdx.x];
+            n1 = idx[blockIdx.x + 1];
+        }
         for (uint32_t it = 0;; ++it) {
             const int st = (int)(it % kDStages);
             const uint32_t k = it / kDStages;
-            if (it >= kDStages && !mbar_wait_bounded(&empty[st], (k - 1) & 1u, 4 * a.copy_ns)) {
+            const uint64_t tile64 = (uint64_t)blockIdx.x + (uint64_t)it * gridDim.x;
+            const uint32_t tile = tile64 < g.ntiles ? (uint32_t)tile64 : kNone;
+            const uint64_t r0 = n0, r1 = n1;
+            // load the following tile's entries now; they arrive while this
+            // iteration waits for its stage
+            const uint64_t next = tile64 + gridDim.x;
+            if (next < g.ntiles) {
+                n0 = idx[next];
+                n1 = idx[next + 1];
+            }
+            if (it >= kDStages && !mbar_wait_bounded(&empty[st], (k - 1) & 1u, 8 * a.copy_ns)) {
                 flag_status(a.status, 6u);
                 break;
             }
-            const uint64_t tile64 = (uint64_t)blockIdx.x + (uint64_t)it * gridDim.x;
-            const uint32_t tile = tile64 < g.ntiles ? (uint32_t)tile64 : 0xFFFFFFFFu;
             uint32_t bad = 0, size = 0;
-            uint64_t r0 = 0;
-            if (tile != 0xFFFFFFFFu) {
+            if (tile != kNone) {
                 if (a.check_header && tile == 0) {
                     const uint32_t *h32 = reinterpret_cast<const uint32_t *>(a.in);
                     const uint64_t *h64 = reinterpret_cast<const uint64_t *>(a.in);
@@ -200,9 +243,6 @@ __global__ void __launch_bounds__(kDThreads, (VPL * sizeof(T) > 128) ? 1 : 2) de
                         h32[3] != G || h64[2] != g.n || h64[7] != a.total_bytes)
                         bad = 1;
                 }
-                const uint64_t *idx = reinterpret_cast<const uint64_t *>(a.in + g.off_index);
-                r0 = idx[tile];
-                const uint64_t r1 = idx[tile + 1];
                 if (r0 > r1 || r1 > a.rec_total || (r0 & 15) || (r1 & 15) || r1 - r0 > rec_max) bad = 1;
                 if (tile == g.ntiles - 1 && r1 != a.rec_total) bad = 1;
                 size = bad ? 0u : (uint32_t)(r1 - r0);
@@ -210,20 +250,67 @@ __global__ void __launch_bounds__(kDThreads, (VPL * sizeof(T) > 128) ? 1 : 2) de
             st_tile[st] = tile;
             st_size[st] = size;
             st_bad[st] = bad;
-            if (size) {
-                mbar_arrive_expect_tx(&full[st], size);
-                bulk_g2s(smem + L.rec[st], a.in + g.off_rec + r0, size, &full[st]);
+            st_dbad[st] = 0;
+            if (tile != kNone && !bad) {
+                const uint64_t k0 = (uint64_t)tile * G;
+                const uint32_t Gt = (uint32_t)min_u64(G, g.nb - k0);
+                // mu values: G * w is a multiple of 32, and the section is
+                // padded to 16 bytes, so the rounded copy stays inside it
+                const uint32_t mu_bytes = (uint32_t)pad16((uint64_t)Gt * w);
+                // state bits: the 16-byte-aligned window around the tile's bytes
+                const uint64_t sb0 = g.off_state + k0 / 8;
+                const uint64_t sbA = sb0 & ~uint64_t(15);
+                const uint64_t sbE = pad16(g.off_state + (k0 + Gt + 7) / 8);
+                st_boff[st] = (uint32_t)(sb0 - sbA);
+                mbar_arrive_expect_tx(&full[st], size + mu_bytes + (uint32_t)(sbE - sbA));
+                if (size) bulk_g2s(smem + L.buf[st], a.in + g.off_rec + r0, size, &full[st]);
+                bulk_g2s(smem + L.mu[st], a.in + g.off_mu + k0 * w, mu_bytes, &full[st]);
+                bulk_g2s(smem + L.bits[st], a.in + sbA, (uint32_t)(sbE - sbA), &full[st]);
                 copy_last[st] = true;
                 copy_phase[st] = k;
             } else {
                 dmbar_arrive(&full[st]);
                 copy_last[st] = false;
             }
-            if (tile == 0xFFFFFFFFu) break;
+            if (tile == kNone) break;
         }
         // do not leave while a copy may still be writing into shared memory
         for (int st = 0; st < kDStages; ++st)
             if (copy_last[st]) mbar_wait_bounded(&full[st], copy_phase[st] & 1u, a.copy_ns);
+        return;
+    }
+
+    if (warp == kDStorerWarp) {
+        // ---- storer: tensor stores of decoded tiles ------------------------
+        if (lane != 0) return;
+        for (uint32_t it = 0;; ++it) {
+            const int st = (int)(it % kDStages);
+            const uint32_t k = it / kDStages;
+            if (!mbar_wait_bounded(&done[st], k & 1u, 8 * a.copy_ns)) {
+                flag_status(a.status, 6u);
+                break;
+            }
+            const uint32_t tile = st_tile[st];
+            if (tile >= g.ntiles) break;
+            const uint64_t row0 = (uint64_t)tile * 256 * RPL;
+            if (st_store[st] && a.use_tma && row0 < a.rows_full) {
+#pragma unroll
+                for (int i = 0; i < RPL; ++i) {
+                    const uint64_t y = row0 + 256 * (uint64_t)i;
+                    if (y < a.rows_full) {
+                        asm volatile(
+                            "cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(
+                                reinterpret_cast<uint64_t>(&tmap)),
+                            "r"(0), "r"((int)y), "r"(smem_addr(smem + L.buf[st] + i * 32768))
+                            : "memory");
+                    }
+                }
+                bulk_commit();
+                bulk_wait_read_all();  // the stage may be refilled once the store has read it
+            }
+            dmbar_arrive(&empty[st]);
+        }
+        bulk_wait_all();
         return;
     }
 
@@ -234,7 +321,7 @@ __global__ void __launch_bounds__(kDThreads, (VPL * sizeof(T) > 128) ? 1 : 2) de
         if (!mbar_wait_bounded(&full[st], k & 1u, a.copy_ns)) s_abort = 1;
         const uint32_t tile = st_tile[st];
         const uint32_t size = st_size[st];
-        uint8_t *rec = smem + L.rec[st];
+        uint8_t *rec = smem + L.buf[st];
         uint32_t *sm_mk = reinterpret_cast<uint32_t *>(smem + L.mk[st]);
         const uint64_t k0 = (uint64_t)tile * G;
         const uint32_t Gt = tile < g.ntiles ? (uint32_t)min_u64(G, g.nb - k0) : 0u;
@@ -253,8 +340,8 @@ __global__ void __launch_bounds__(kDThreads, (VPL * sizeof(T) > 128) ? 1 : 2) de
         uint32_t rank = 0;
         bool nonconst = false;
         uint32_t nn_t = 0;
-        if (tile < g.ntiles) {
-            const uint8_t *stb = a.in + g.off_state + k0 / 8;
+        if (tile < g.ntiles && !st_bad[st]) {
+            const uint8_t *stb = smem + L.bits[st] + st_boff[st];
             for (uint32_t i = 0; i < (Gt + 7) / 8; i += 4) {
                 uint32_t wv = 0;
 #pragma unroll
@@ -315,9 +402,15 @@ __global__ void __launch_bounds__(kDThreads, (VPL * sizeof(T) > 128) ? 1 : 2) de
 #pragma unroll
         for (int d = 1; d < LPB; d <<= 1) mk += __shfl_xor_sync(kFull, mk, d);
         if (blk < G && sub == 0) sm_mk[blk] = (exists && nonconst) ? mk : 0u;
-        if (!ok && exists) st_bad[st] = 1;
+        if (!ok && exists) st_dbad[st] = 1;
         decoder_sync();
-        if (s_abort || tile >= g.ntiles) break;
+        if (s_abort || tile >= g.ntiles) {
+            // hand the stage to the storer (it stops on the same tile), and stop
+            if (tid == 0) st_tile[st] = kNone;
+            decoder_sync();
+            if (lane == 0) dmbar_arrive(&done[st]);
+            break;
+        }
 
         // ---- mid-byte offsets: every warp scans the tile's counts ----------
         uint32_t midoff, total;
@@ -333,14 +426,15 @@ __global__ void __launch_bounds__(kDThreads, (VPL * sizeof(T) > 128) ? 1 : 2) de
             midoff = before;
         }
         const uint32_t used = nn_t * (b / 4 + 1) + total;
-        const bool bad = st_bad[st] || pad16(used) != size;
+        // uniform over the CTA: st_bad and the counts were fixed before the barrier
+        const bool bad = st_bad[st] || st_dbad[st] || pad16(used) != size;
+        U x[VPL];
         if (bad) {
             if (tid == 0) flag_status(a.status, 3u);
         } else {
             // ---- decode --------------------------------------------------
             const uint32_t mbase = nn_t * (b / 4 + 1) + midoff;
-            const U mu_bits = exists ? reinterpret_cast<const U *>(a.in + g.off_mu)[kg] : U(0);
-            U x[VPL];
+            const U mu_bits = exists ? reinterpret_cast<const U *>(smem + L.mu[st])[blk] : U(0);
 
             using CntT = std::conditional_t<(LPB * VPL > 1023), unsigned long long, uint32_t>;
             constexpr int FB = LPB * VPL > 1023 ? 16 : 10;
@@ -467,37 +561,66 @@ __global__ void __launch_bounds__(kDThreads, (VPL * sizeof(T) > 128) ? 1 : 2) de
                 for (int m = 0; m < VPL; ++m) x[m] = mu_bits;
             }
 
-            if (exists && nvalid > 0) {
-                U *dst = reinterpret_cast<U *>(a.out) + kg * b + sub * VPL;
-                if (full_lane) {
-#pragma unroll
-                    for (int i = 0; i < VPL * w / 16; ++i) {
-                        uint4 v;
-                        U *u = reinterpret_cast<U *>(&v);
-#pragma unroll
-                        for (int kk = 0; kk < 16 / w; ++kk) u[kk] = x[i * (16 / w) + kk];
-                        reinterpret_cast<uint4 *>(dst)[i] = v;
-                    }
-                } else {
-#pragma unroll
-                    for (int m = 0; m < VPL; ++m)
-                        if (m < nvalid) dst[m] = x[m];
-                }
-            }
             // strictness: the record's pad bytes must be zero
             if (warp == 0)
                 for (uint32_t i = used + lane; i < size; i += 32)
                     if (rec[i]) flag_status(a.status, 3u);
         }
-        // this thread is done with the stage's record
-        dmbar_arrive(&empty[st]);
+        decoder_sync();  // the record is no longer read: the stage takes the output
+
+        if (!bad) {
+            if (exists && nvalid > 0) {
+                const uint32_t lane_row0 = (uint32_t)((warp * 32 + lane) * RPL);
+                const uint64_t grow0 = (uint64_t)tile * 256 * RPL + lane_row0;
+#pragma unroll
+                for (int rr = 0; rr < RPL; ++rr) {
+                    constexpr int VPR = 128 / w;  // values per row
+                    const int nv = nvalid - rr * VPR;
+                    if (nv <= 0) continue;
+                    if (a.use_tma && grow0 + rr < a.rows_full) {
+                        // full row: 128-byte-swizzled into the stage for the tensor store
+                        const uint32_t rowi = lane_row0 + rr;
+                        uint8_t *row = smem + L.buf[st] + (rowi << 7);
+#pragma unroll
+                        for (int c = 0; c < 8; ++c) {
+                            uint4 v;
+                            U *u = reinterpret_cast<U *>(&v);
+#pragma unroll
+                            for (int kk = 0; kk < 16 / w; ++kk) u[kk] = x[rr * VPR + c * (16 / w) + kk];
+                            *reinterpret_cast<uint4 *>(row + ((c ^ (rowi & 7u)) << 4)) = v;
+                        }
+                    } else {
+                        U *dst = reinterpret_cast<U *>(a.out) + kg * b + sub * VPL + rr * VPR;
+                        if (nv >= VPR) {
+#pragma unroll
+                            for (int c = 0; c < 8; ++c) {
+                                uint4 v;
+                                U *u = reinterpret_cast<U *>(&v);
+#pragma unroll
+                                for (int kk = 0; kk < 16 / w; ++kk) u[kk] = x[rr * VPR + c * (16 / w) + kk];
+                                reinterpret_cast<uint4 *>(dst)[c] = v;
+                            }
+                        } else {
+#pragma unroll
+                            for (int m = 0; m < VPR; ++m)
+                                if (m < nv) dst[m] = x[rr * VPR + m];
+                        }
+                    }
+                }
+            }
+        }
+        if (tid == 0) st_store[st] = bad ? 0u : 1u;
+        // the storer takes the stage once every warp has written its rows
+        fence_proxy_async_smem();
+        __syncwarp();
+        if (lane == 0) dmbar_arrive(&done[st]);
     }
 }
 
 // ---------------------------------------------------------------------------
 
 template <typename T, int LPB, int VPL>
-static cudaError_t launch_t(const DecompressArgs &a, cudaStream_t stream) {
+static cudaError_t launch_t(const CUtensorMap &tm, const DecompressArgs &a, cudaStream_t stream) {
     const DSmem L = decompress_smem(a.g.G, a.g.b, Fmt<T>::w);
     auto kern = decompress_kernel<T, LPB, VPL>;
     cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total);
@@ -509,7 +632,7 @@ static cudaError_t launch_t(const DecompressArgs &a, cudaStream_t stream) {
         return err;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     const uint64_t grid = min_u64(a.g.ntiles, (uint64_t)sms * per_sm);
-    kern<<<(unsigned)grid, kDThreads, L.total, stream>>>(a);
+    kern<<<(unsigned)grid, kDThreads, L.total, stream>>>(tm, a);
     return cudaGetLastError();
 }
 
@@ -527,23 +650,26 @@ cudaError_t launch_decompress(const void *in, uint64_t in_bytes, uint64_t total_
     a.check_header = check_header ? 1u : 0u;
     a.total_bytes = total_bytes;
     a.copy_ns = 1000ull * wait_limit_from_env("SZX_COPY_US", 1000000u);
+    a.rows_full = n * (dtype == 0 ? 4 : 8) / 128;
+    CUtensorMap tm;
+    a.use_tma = encode_row_map(&tm, out, a.rows_full) ? 1u : 0u;
     if (dtype == 0) {
         switch (block) {
-            case 32: return launch_t<float, 1, 32>(a, stream);
-            case 64: return launch_t<float, 2, 32>(a, stream);
-            case 128: return launch_t<float, 4, 32>(a, stream);
-            case 256: return launch_t<float, 8, 32>(a, stream);
-            case 512: return launch_t<float, 16, 32>(a, stream);
-            case 1024: return launch_t<float, 32, 32>(a, stream);
+            case 32: return launch_t<float, 1, 32>(tm, a, stream);
+            case 64: return launch_t<float, 2, 32>(tm, a, stream);
+            case 128: return launch_t<float, 4, 32>(tm, a, stream);
+            case 256: return launch_t<float, 8, 32>(tm, a, stream);
+            case 512: return launch_t<float, 16, 32>(tm, a, stream);
+            case 1024: return launch_t<float, 32, 32>(tm, a, stream);
         }
     } else {
         switch (block) {
-            case 32: return launch_t<double, 2, 16>(a, stream);
-            case 64: return launch_t<double, 4, 16>(a, stream);
-            case 128: return launch_t<double, 8, 16>(a, stream);
-            case 256: return launch_t<double, 16, 16>(a, stream);
-            case 512: return launch_t<double, 32, 16>(a, stream);
-            case 1024: return launch_t<double, 32, 32>(a, stream);
+            case 32: return launch_t<double, 2, 16>(tm, a, stream);
+            case 64: return launch_t<double, 4, 16>(tm, a, stream);
+            case 128: return launch_t<double, 8, 16>(tm, a, stream);
+            case 256: return launch_t<double, 16, 16>(tm, a, stream);
+            case 512: return launch_t<double, 32, 16>(tm, a, stream);
+            case 1024: return launch_t<double, 32, 32>(tm, a, stream);
         }
     }
     return cudaErrorInvalidValue;

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cstdint>
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 namespace szx {
@@ -9,6 +10,11 @@ namespace szx {
 // Limit (microseconds) of a bounded device-side wait: the environment variable
 // `name` (a positive integer) if set, else `fallback`.  Read on every launch.
 uint32_t wait_limit_from_env(const char *name, uint32_t fallback);
+
+// Encode a 2-D TMA tensor map over `rows` rows of 128 bytes at base (32-bit
+// elements, 32 x 256 box = 32 KiB, 128-byte swizzle).  False if rows is 0 or
+// >= 2^31, or the driver entry point is unavailable or rejects the map.
+bool encode_row_map(CUtensorMap *tm, const void *base, uint64_t rows);
 
 // Enqueue the compression of n values (dtype 0 = f32, 1 = f64) with bound bits
 // e_bits into the stream at out; the workspace starts ws_offset bytes into
