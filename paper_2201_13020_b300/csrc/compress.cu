@@ -356,23 +356,17 @@ constexpr int kCThreads = kConsumers + 64;
 static_assert(kConsumers == kThreads, "a tile is laid out over 8 warps");
 
 struct CSmem {
-    uint32_t buf[kStages], buf_bytes;
-    uint32_t meta[kStages], m_kind, m_req, m_mk, m_mu, m_rank, m_midoff;
+    uint32_t buf_stride, buf_bytes;  // tile buffer st at st * buf_stride (1024-aligned)
+    uint32_t meta0, meta_stride;     // metadata block st at meta0 + st * meta_stride
+    uint32_t m_kind, m_req, m_mk, m_mu, m_rank, m_midoff;  // offsets inside a metadata block
     uint32_t lut, total;
 };
 __host__ __device__ inline CSmem compress_smem(uint32_t G, uint32_t b, uint32_t w) {
     CSmem s;
-    uint32_t o = 0;
-    auto take = [&](uint32_t bytes, uint32_t align) {
-        o = (o + align - 1) & ~(align - 1);
-        const uint32_t at = o;
-        o += bytes;
-        return at;
-    };
     const uint32_t tile = G * b * w;
     const uint32_t rec = record_max_bytes(G, b, w);
     s.buf_bytes = ((tile > rec ? tile : rec) + 16 + 15) & ~15u;
-    for (int i = 0; i < kStages; ++i) s.buf[i] = take(s.buf_bytes, 1024);
+    s.buf_stride = (s.buf_bytes + 1023) & ~1023u;
     // one metadata block per stage
     uint32_t m = 0;
     auto mtake = [&](uint32_t bytes) {
@@ -387,8 +381,10 @@ __host__ __device__ inline CSmem compress_smem(uint32_t G, uint32_t b, uint32_t 
     s.m_mu = mtake(w * G);
     s.m_rank = mtake(4 * G);
     s.m_midoff = mtake(4 * G);
-    for (int i = 0; i < kStages; ++i) s.meta[i] = take(m, 16);
-    s.lut = take(3 * 256 * 4, 16);
+    s.meta_stride = (m + 15) & ~15u;
+    s.meta0 = (kStages - 1) * s.buf_stride + s.buf_bytes;  // after the last buffer (16-aligned)
+    s.lut = s.meta0 + kStages * s.meta_stride;
+    const uint32_t o = s.lut + 3 * 256 * 4;
     s.total = ((o + 1023) & ~1023u) + 1024;  // + slack to realign the dynamic base
     return s;
 }
@@ -416,7 +412,7 @@ __global__ void __launch_bounds__(kCThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
     constexpr int NCODE = (2 * VPL + 31) / 32;
     static_assert(RPL >= 1 && NCODE >= 1, "lane geometry");
 
-    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    extern __shared__ __align__(16) uint8_t smem_raw[];  // realigned to 1024 below
     // full: tile copied in; ready: record written; empty: record stored
     __shared__ __align__(8) uint64_t full[kStages], ready[kStages], empty[kStages];
     __shared__ uint32_t st_tile[kStages], st_nn[kStages], st_mid[kStages], st_nraw[kStages], st_nesc[kStages],
@@ -456,8 +452,7 @@ __global__ void __launch_bounds__(kCThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
         if (lane != 0) return;
         // per stage: is the last phase a copy (then it may still be in flight
         // when the producer is done), and its phase index
-        bool copy_last[kStages] = {};
-        uint32_t copy_phase[kStages] = {};
+        uint32_t copy_last = 0, copy_par = 0;  // bit st
         for (uint32_t it = 0;; ++it) {
             const int st = (int)(it % kStages);
             const uint32_t k = it / kStages;
@@ -474,7 +469,7 @@ __global__ void __launch_bounds__(kCThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
                 mbar_arrive_expect_tx(&full[st], 256u * 128u * RPL);
 #pragma unroll
                 for (int i = 0; i < RPL; ++i) {
-                    const uint32_t dst = smem_addr(smem + L.buf[st] + i * 32768);
+                    const uint32_t dst = smem_addr(smem + st * L.buf_stride + i * 32768);
                     const int y = (int)(row0 + 256 * i);
                     asm volatile(
                         "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, "
@@ -482,18 +477,18 @@ __global__ void __launch_bounds__(kCThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
                         "l"(reinterpret_cast<uint64_t>(&tmap)), "r"(0), "r"(y), "r"(smem_addr(&full[st]))
                         : "memory");
                 }
-                copy_last[st] = true;
-                copy_phase[st] = k;
+                copy_last |= 1u << st;
+                copy_par = (copy_par & ~(1u << st)) | ((k & 1u) << st);
             } else {
                 // a later phase on this stage implies its earlier copy was consumed
                 mbar_arrive(&full[st]);
-                copy_last[st] = false;
+                copy_last &= ~(1u << st);
             }
             if (t >= g.ntiles) break;
         }
         // do not leave while a copy may still be writing into shared memory
         for (int st = 0; st < kStages; ++st)
-            if (copy_last[st]) mbar_wait_bounded(&full[st], copy_phase[st] & 1u, a.copy_ns);
+            if ((copy_last >> st) & 1u) mbar_wait_bounded(&full[st], (copy_par >> st) & 1u, a.copy_ns);
         return;
     }
 
@@ -508,7 +503,7 @@ __global__ void __launch_bounds__(kCThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
             }
             const uint32_t tile = st_tile[st];
             if (tile >= g.ntiles) break;
-            const uint8_t *meta = smem + L.meta[st];
+            const uint8_t *meta = smem + (L.meta0 + st * L.meta_stride);
             const uint8_t *m_kind = meta + L.m_kind;
             const U *m_mu = reinterpret_cast<const U *>(meta + L.m_mu);
             const uint32_t rec_bytes = st_rec[st];
@@ -570,7 +565,7 @@ __global__ void __launch_bounds__(kCThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
                 }
                 if (rec_bytes) {
                     fence_proxy_async_smem();
-                    bulk_s2g(a.out + g.off_rec + excl, smem + L.buf[st], rec_bytes);
+                    bulk_s2g(a.out + g.off_rec + excl, smem + st * L.buf_stride, rec_bytes);
                     bulk_commit();
                 }
                 atomicAdd(&a.ws->nn, (unsigned long long)st_nn[st]);
@@ -647,8 +642,8 @@ __global__ void __launch_bounds__(kCThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
             if (s_abort && tid == 0) atomicOr(&a.ws->err, kErrTmaTimeout);
             break;
         }
-        uint8_t *buf = smem + L.buf[st];
-        uint8_t *meta = smem + L.meta[st];
+        uint8_t *buf = smem + st * L.buf_stride;
+        uint8_t *meta = smem + (L.meta0 + st * L.meta_stride);
         uint8_t *sm_kind = meta + L.m_kind;
         uint8_t *sm_req = meta + L.m_req;
         uint32_t *sm_mk = reinterpret_cast<uint32_t *>(meta + L.m_mk);

@@ -125,7 +125,8 @@ constexpr uint32_t kBitsWindow = 64;  // 16-byte-aligned window holding a tile's
 // that receives the record and then holds the decoded tile, the tile's mu
 // values, its state-bit window and its blocks' mid-byte counts.
 struct DSmem {
-    uint32_t buf[kDStages], mu[kDStages], bits[kDStages], mk[kDStages];
+    uint32_t stage;          // stage stride; stage st starts at st * stage
+    uint32_t mu, bits, mk;   // offsets inside a stage (the buffer is at 0)
     uint32_t lut, total;
 };
 __host__ __device__ inline DSmem decompress_smem(uint32_t G, uint32_t b, uint32_t w) {
@@ -134,14 +135,11 @@ __host__ __device__ inline DSmem decompress_smem(uint32_t G, uint32_t b, uint32_
     const uint32_t rec = record_max_bytes(G, b, w) + 16;  // + slack for the 8-byte run reads
     const uint32_t body = ((tile > rec ? tile : rec) + 15) & ~15u;
     const uint32_t mub = (G * w + 15) & ~15u;
-    const uint32_t stage = (body + mub + kBitsWindow + 4 * G + 1023) & ~1023u;
-    for (int i = 0; i < kDStages; ++i) {
-        s.buf[i] = i * stage;
-        s.mu[i] = s.buf[i] + body;
-        s.bits[i] = s.mu[i] + mub;
-        s.mk[i] = s.bits[i] + kBitsWindow;
-    }
-    s.lut = kDStages * stage;
+    s.stage = (body + mub + kBitsWindow + 4 * G + 1023) & ~1023u;
+    s.mu = body;
+    s.bits = s.mu + mub;
+    s.mk = s.bits + kBitsWindow;
+    s.lut = kDStages * s.stage;
     s.total = s.lut + (uint32_t)sizeof(DecodeLut) + 1024;  // + slack to realign the dynamic base
     return s;
 }
@@ -210,8 +208,9 @@ __global__ void __launch_bounds__(kDThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
         if (lane != 0) return;
         const uint32_t rec_max = record_max_bytes(G, b, w);
         const uint64_t *idx = reinterpret_cast<const uint64_t *>(a.in + g.off_index);
-        bool copy_last[kDStages] = {};
-        uint32_t copy_phase[kDStages] = {};
+        // per stage (bit st): is its last phase a copy (then it may still be in
+        // flight when the producer is done), and that phase's parity
+        uint32_t copy_last = 0, copy_par = 0;
         uint64_t n0 = 0, n1 = 0;  // index entries of the next tile
         if (blockIdx.x < g.ntiles) {
             n0 = idx[blockIdx.x];
@@ -263,20 +262,20 @@ __global__ void __launch_bounds__(kDThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
                 const uint64_t sbE = pad16(g.off_state + (k0 + Gt + 7) / 8);
                 st_boff[st] = (uint32_t)(sb0 - sbA);
                 mbar_arrive_expect_tx(&full[st], size + mu_bytes + (uint32_t)(sbE - sbA));
-                if (size) bulk_g2s(smem + L.buf[st], a.in + g.off_rec + r0, size, &full[st]);
-                bulk_g2s(smem + L.mu[st], a.in + g.off_mu + k0 * w, mu_bytes, &full[st]);
-                bulk_g2s(smem + L.bits[st], a.in + sbA, (uint32_t)(sbE - sbA), &full[st]);
-                copy_last[st] = true;
-                copy_phase[st] = k;
+                if (size) bulk_g2s(smem + st * L.stage, a.in + g.off_rec + r0, size, &full[st]);
+                bulk_g2s(smem + st * L.stage + L.mu, a.in + g.off_mu + k0 * w, mu_bytes, &full[st]);
+                bulk_g2s(smem + st * L.stage + L.bits, a.in + sbA, (uint32_t)(sbE - sbA), &full[st]);
+                copy_last |= 1u << st;
+                copy_par = (copy_par & ~(1u << st)) | ((k & 1u) << st);
             } else {
                 dmbar_arrive(&full[st]);
-                copy_last[st] = false;
+                copy_last &= ~(1u << st);
             }
             if (tile == kNone) break;
         }
         // do not leave while a copy may still be writing into shared memory
         for (int st = 0; st < kDStages; ++st)
-            if (copy_last[st]) mbar_wait_bounded(&full[st], copy_phase[st] & 1u, a.copy_ns);
+            if ((copy_last >> st) & 1u) mbar_wait_bounded(&full[st], (copy_par >> st) & 1u, a.copy_ns);
         return;
     }
 
@@ -301,7 +300,7 @@ __global__ void __launch_bounds__(kDThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
                         asm volatile(
                             "cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(
                                 reinterpret_cast<uint64_t>(&tmap)),
-                            "r"(0), "r"((int)y), "r"(smem_addr(smem + L.buf[st] + i * 32768))
+                            "r"(0), "r"((int)y), "r"(smem_addr(smem + st * L.stage + i * 32768))
                             : "memory");
                     }
                 }
@@ -321,8 +320,8 @@ __global__ void __launch_bounds__(kDThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
         if (!mbar_wait_bounded(&full[st], k & 1u, a.copy_ns)) s_abort = 1;
         const uint32_t tile = st_tile[st];
         const uint32_t size = st_size[st];
-        uint8_t *rec = smem + L.buf[st];
-        uint32_t *sm_mk = reinterpret_cast<uint32_t *>(smem + L.mk[st]);
+        uint8_t *rec = smem + st * L.stage;
+        uint32_t *sm_mk = reinterpret_cast<uint32_t *>(smem + st * L.stage + L.mk);
         const uint64_t k0 = (uint64_t)tile * G;
         const uint32_t Gt = tile < g.ntiles ? (uint32_t)min_u64(G, g.nb - k0) : 0u;
 
@@ -341,7 +340,7 @@ __global__ void __launch_bounds__(kDThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
         bool nonconst = false;
         uint32_t nn_t = 0;
         if (tile < g.ntiles && !st_bad[st]) {
-            const uint8_t *stb = smem + L.bits[st] + st_boff[st];
+            const uint8_t *stb = smem + st * L.stage + L.bits + st_boff[st];
             for (uint32_t i = 0; i < (Gt + 7) / 8; i += 4) {
                 uint32_t wv = 0;
 #pragma unroll
@@ -434,7 +433,7 @@ __global__ void __launch_bounds__(kDThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
         } else {
             // ---- decode --------------------------------------------------
             const uint32_t mbase = nn_t * (b / 4 + 1) + midoff;
-            const U mu_bits = exists ? reinterpret_cast<const U *>(smem + L.mu[st])[blk] : U(0);
+            const U mu_bits = exists ? reinterpret_cast<const U *>(smem + st * L.stage + L.mu)[blk] : U(0);
 
             using CntT = std::conditional_t<(LPB * VPL > 1023), unsigned long long, uint32_t>;
             constexpr int FB = LPB * VPL > 1023 ? 16 : 10;
@@ -580,7 +579,7 @@ __global__ void __launch_bounds__(kDThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
                     if (a.use_tma && grow0 + rr < a.rows_full) {
                         // full row: 128-byte-swizzled into the stage for the tensor store
                         const uint32_t rowi = lane_row0 + rr;
-                        uint8_t *row = smem + L.buf[st] + (rowi << 7);
+                        uint8_t *row = smem + st * L.stage + (rowi << 7);
 #pragma unroll
                         for (int c = 0; c < 8; ++c) {
                             uint4 v;
