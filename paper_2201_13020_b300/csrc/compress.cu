@@ -938,7 +938,7 @@ cudaError_t launch_compress_ws(const void *in, uint64_t n, int dtype, uint64_t e
     a.copy_ns = 1000ull * wait_limit_from_env("SZX_COPY_US", 1000000u);
     a.rows_full = n * w / 128;
     CUtensorMap tm;
-    a.use_tma = encode_row_map(&tm, in, a.rows_full) ? 1u : 0u;
+    a.use_tma = encode_row_map(&tm, in, a.rows_full, 256) ? 1u : 0u;
     cudaError_t err = cudaMemsetAsync(a.ws, 0, workspace_bytes(a.g.ntiles), stream);
     if (err != cudaSuccess) return err;
     if (dtype == 0) {
@@ -981,14 +981,14 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
 }
 }  // namespace
 
-bool encode_row_map(CUtensorMap *tm, const void *base, uint64_t rows) {
+bool encode_row_map(CUtensorMap *tm, const void *base, uint64_t rows, uint32_t box_rows) {
     std::memset(tm, 0, sizeof(*tm));
     if (rows == 0 || rows >= (1ull << 31)) return false;
     auto enc = tensor_map_encoder();
     if (!enc) return false;
     cuuint64_t dims[2] = {32, rows};
     cuuint64_t strides[1] = {128};
-    cuuint32_t box[2] = {32, 256};
+    cuuint32_t box[2] = {32, box_rows};
     cuuint32_t estr[2] = {1, 1};
     const CUresult r = enc(tm, CU_TENSOR_MAP_DATA_TYPE_UINT32, 2, const_cast<void *>(base), dims, strides, box, estr,
                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,

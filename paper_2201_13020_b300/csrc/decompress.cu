@@ -65,34 +65,34 @@ __device__ __forceinline__ void flag_status(uint32_t *status, uint32_t code) {
 
 __device__ __forceinline__ uint32_t dprmt(uint32_t a, uint32_t b, uint32_t s) { return __byte_perm(a, b, s); }
 
-// Tables (compile time), per plane j in 0..2 and the 2-bit codes of four
-// values (value k at bits 2k):
-//   expand: byte-permute selector moving the k-th byte of a run to the k-th
-//           value whose code is <= j (others get zero) | count << 16;
-//   carry:  byte-permute selector for the copy-forward of plane j: a value
-//           whose code is > j takes the byte of the nearest earlier value of
-//           the group with code <= j, or the carry byte (operand byte 4).
+// Table (compile time), per plane j in 0..2 and the 2-bit codes of four values
+// (value k at bits 2k): a byte-permute selector that, applied to (run of own
+// bytes, carry byte), gives value k the next byte of the run if it owns one
+// (code <= j), else the byte of the nearest earlier owner of the group, else
+// the carry byte (operand byte 4) -- expansion and the copy-forward of
+// identical leading bytes in one permute -- plus the number of owners << 16.
 struct DecodeLut {
-    uint32_t expand[768];
-    uint32_t carry[768];
+    uint32_t sel[768];
 };
 constexpr DecodeLut make_decode_lut() {
     DecodeLut t{};
     for (uint32_t i = 0; i < 768; ++i) {
         const uint32_t j = i >> 8, code = i & 255u;
-        uint32_t sel = 0x4444u, cnt = 0, csel = 0;
-        int src = -1;
+        uint32_t sel = 0, cnt = 0;
+        int last = -1;
         for (uint32_t k = 0; k < 4; ++k) {
             const bool own = ((code >> (2 * k)) & 3u) <= j;
+            uint32_t nib = 0;
             if (own) {
-                sel = (sel & ~(0xFu << (4 * k))) | (cnt << (4 * k));
+                nib = cnt;
+                last = (int)cnt;
                 ++cnt;
-                src = (int)k;
+            } else {
+                nib = last < 0 ? 4u : (uint32_t)last;
             }
-            csel |= (uint32_t)(src < 0 ? 4 : src) << (4 * k);
+            sel |= nib << (4 * k);
         }
-        t.expand[i] = sel | (cnt << 16);
-        t.carry[i] = csel;
+        t.sel[i] = sel | (cnt << 16);
     }
     return t;
 }
@@ -114,32 +114,35 @@ __device__ __forceinline__ uint32_t load_run(const uint8_t *buf, uint32_t p) {
     return __funnelshift_r(wp[0], wp[1], (p & 3u) * 8u);
 }
 
-constexpr int kDStages = 3;
-constexpr int kDConsumers = kThreads;                 // 8 decoding warps
-constexpr int kDProducerWarp = kDConsumers / 32;      // warp 8
-constexpr int kDStorerWarp = kDProducerWarp + 1;      // warp 9
-constexpr int kDThreads = kDConsumers + 64;
+constexpr int kDStages = 2;
+constexpr int kDConsumers = kThreads;             // 8 decoding warps
+constexpr int kDWarps = kDConsumers / 32;
+constexpr int kDProducerWarp = kDWarps;           // warp 8
+constexpr int kDThreads = kDConsumers + 32;
 constexpr uint32_t kBitsWindow = 64;  // 16-byte-aligned window holding a tile's state bits
 
-// Per stage (1024-byte aligned, for the swizzled tensor store): the buffer
-// that receives the record and then holds the decoded tile, the tile's mu
-// values, its state-bit window and its blocks' mid-byte counts.
+// Shared memory: kDStages stages (each: the record buffer, the tile's mu
+// values, its state-bit window and its blocks' mid-byte counts), one output
+// buffer per decoding warp (its 32 * RPL rows of 128 bytes, 1024-byte aligned
+// for the swizzled tensor store), and the decode table.
 struct DSmem {
-    uint32_t stage;          // stage stride; stage st starts at st * stage
-    uint32_t mu, bits, mk;   // offsets inside a stage (the buffer is at 0)
+    uint32_t stage;         // stage st starts at st * stage
+    uint32_t mu, bits, mk;  // offsets inside a stage (the record buffer is at 0)
+    uint32_t wbuf, wbuf_bytes;  // warp w's output buffer at wbuf + w * wbuf_bytes
     uint32_t lut, total;
 };
 __host__ __device__ inline DSmem decompress_smem(uint32_t G, uint32_t b, uint32_t w) {
     DSmem s;
-    const uint32_t tile = G * b * w;
     const uint32_t rec = record_max_bytes(G, b, w) + 16;  // + slack for the 8-byte run reads
-    const uint32_t body = ((tile > rec ? tile : rec) + 15) & ~15u;
+    const uint32_t body = (rec + 15) & ~15u;
     const uint32_t mub = (G * w + 15) & ~15u;
     s.stage = (body + mub + kBitsWindow + 4 * G + 1023) & ~1023u;
     s.mu = body;
     s.bits = s.mu + mub;
     s.mk = s.bits + kBitsWindow;
-    s.lut = kDStages * s.stage;
+    s.wbuf = kDStages * s.stage;
+    s.wbuf_bytes = (G * b * w) / kDWarps;  // 4 KiB per 128-byte row per lane
+    s.lut = s.wbuf + kDWarps * s.wbuf_bytes;
     s.total = s.lut + (uint32_t)sizeof(DecodeLut) + 1024;  // + slack to realign the dynamic base
     return s;
 }
@@ -153,7 +156,7 @@ __device__ __forceinline__ void dmbar_arrive(uint64_t *bar) {
         : "memory");
 }
 
-// Persistent decoder: tile = blockIdx.x + k * gridDim.x.
+// Persistent decoder: tile = blockIdx.x + it * gridDim.x for it = 0, 1, ...
 template <typename T, int LPB, int VPL>
 __global__ void __launch_bounds__(kDThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
     decompress_kernel(const __grid_constant__ CUtensorMap tmap, DecompressArgs a) {
@@ -165,25 +168,24 @@ __global__ void __launch_bounds__(kDThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
     constexpr int NCODE = (2 * VPL + 31) / 32;
     constexpr int NPW = W / 32;         // 32-bit words per value
     constexpr int RPL = VPL * w / 128;  // 128-byte rows per lane
-    static_assert(RPL >= 1, "lane geometry");
+    constexpr uint32_t b = (uint32_t)(LPB * VPL);
+    constexpr uint32_t G = tile_blocks(b, (uint32_t)w);
+    static_assert(RPL >= 1 && G * b * w == 32768u * RPL, "lane geometry");
 
     extern __shared__ __align__(16) uint8_t smem_raw[];  // realigned to 1024 below
-    // full: record, mu and state bits copied in; done: tile decoded into the
-    // stage; empty: tile stored, stage free
-    __shared__ __align__(8) uint64_t full[kDStages], done[kDStages], empty[kDStages];
+    // full: record, mu and state bits copied in; consumed: every decoding warp
+    // is done reading the stage
+    __shared__ __align__(8) uint64_t full[kDStages], consumed[kDStages];
     // st_bad: set by the producer (index or header fault); st_dbad: set by a
-    // decoder (bad codes), read only after the first barrier
-    __shared__ uint32_t st_tile[kDStages], st_size[kDStages], st_bad[kDStages], st_dbad[kDStages],
-        st_boff[kDStages], st_store[kDStages];
-    __shared__ uint32_t s_abort;
+    // decoder (bad codes), read only after the barrier
+    __shared__ uint32_t st_size[kDStages], st_bad[kDStages], st_dbad[kDStages], st_boff[kDStages];
+    __shared__ uint32_t s_abort;  // a decoder's wait ran out: the CTA stops after the barrier
 
     uint8_t *smem = smem_raw + ((1024u - (smem_addr(smem_raw) & 1023u)) & 1023u);
     const Geometry &g = a.g;
-    const uint32_t b = g.b, G = g.G;
     const DSmem L = decompress_smem(G, b, w);
-    const DecodeLut *lut = reinterpret_cast<const DecodeLut *>(smem + L.lut);
+    const uint32_t *lut = reinterpret_cast<const uint32_t *>(smem + L.lut);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    constexpr uint32_t kNone = 0xFFFFFFFFu;
 
     {
         const uint4 *src = reinterpret_cast<const uint4 *>(&kDecodeLut);
@@ -193,18 +195,16 @@ __global__ void __launch_bounds__(kDThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
     if (tid == 0) {
         for (int i = 0; i < kDStages; ++i) {
             mbar_init(&full[i], 1);
-            mbar_init(&done[i], kDConsumers / 32);
-            mbar_init(&empty[i], 1);
-            st_tile[i] = kNone;
-            st_size[i] = st_bad[i] = st_dbad[i] = st_boff[i] = st_store[i] = 0;
+            mbar_init(&consumed[i], kDWarps);
+            st_size[i] = st_bad[i] = st_dbad[i] = st_boff[i] = 0;
         }
-        fence_mbar_init();
         s_abort = 0;
+        fence_mbar_init();
     }
     __syncthreads();
 
     if (warp == kDProducerWarp) {
-        // ---- producer: record, mu and state-bit copies into the ring --------
+        // ---- producer: record, mu and state-bit copies into the stages ------
         if (lane != 0) return;
         const uint32_t rec_max = record_max_bytes(G, b, w);
         const uint64_t *idx = reinterpret_cast<const uint64_t *>(a.in + g.off_index);
@@ -217,10 +217,11 @@ __global__ void __launch_bounds__(kDThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
             n1 = idx[blockIdx.x + 1];
         }
         for (uint32_t it = 0;; ++it) {
+            const uint64_t tile64 = (uint64_t)blockIdx.x + (uint64_t)it * gridDim.x;
+            if (tile64 >= g.ntiles) break;
+            const uint32_t tile = (uint32_t)tile64;
             const int st = (int)(it % kDStages);
             const uint32_t k = it / kDStages;
-            const uint64_t tile64 = (uint64_t)blockIdx.x + (uint64_t)it * gridDim.x;
-            const uint32_t tile = tile64 < g.ntiles ? (uint32_t)tile64 : kNone;
             const uint64_t r0 = n0, r1 = n1;
             // load the following tile's entries now; they arrive while this
             // iteration waits for its stage
@@ -229,28 +230,25 @@ __global__ void __launch_bounds__(kDThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
                 n0 = idx[next];
                 n1 = idx[next + 1];
             }
-            if (it >= kDStages && !mbar_wait_bounded(&empty[st], (k - 1) & 1u, 8 * a.copy_ns)) {
+            if (it >= kDStages && !mbar_wait_bounded(&consumed[st], (k - 1) & 1u, 8 * a.copy_ns)) {
                 flag_status(a.status, 6u);
                 break;
             }
-            uint32_t bad = 0, size = 0;
-            if (tile != kNone) {
-                if (a.check_header && tile == 0) {
-                    const uint32_t *h32 = reinterpret_cast<const uint32_t *>(a.in);
-                    const uint64_t *h64 = reinterpret_cast<const uint64_t *>(a.in);
-                    if (h32[0] != kMagic || (h32[1] & 0xFFFFu) != (kVersion | (a.dtype << 8)) || h32[2] != b ||
-                        h32[3] != G || h64[2] != g.n || h64[7] != a.total_bytes)
-                        bad = 1;
-                }
-                if (r0 > r1 || r1 > a.rec_total || (r0 & 15) || (r1 & 15) || r1 - r0 > rec_max) bad = 1;
-                if (tile == g.ntiles - 1 && r1 != a.rec_total) bad = 1;
-                size = bad ? 0u : (uint32_t)(r1 - r0);
+            uint32_t bad = 0;
+            if (a.check_header && tile == 0) {
+                const uint32_t *h32 = reinterpret_cast<const uint32_t *>(a.in);
+                const uint64_t *h64 = reinterpret_cast<const uint64_t *>(a.in);
+                if (h32[0] != kMagic || (h32[1] & 0xFFFFu) != (kVersion | (a.dtype << 8)) || h32[2] != b ||
+                    h32[3] != G || h64[2] != g.n || h64[7] != a.total_bytes)
+                    bad = 1;
             }
-            st_tile[st] = tile;
+            if (r0 > r1 || r1 > a.rec_total || (r0 & 15) || (r1 & 15) || r1 - r0 > rec_max) bad = 1;
+            if (tile == g.ntiles - 1 && r1 != a.rec_total) bad = 1;
+            const uint32_t size = bad ? 0u : (uint32_t)(r1 - r0);
             st_size[st] = size;
             st_bad[st] = bad;
             st_dbad[st] = 0;
-            if (tile != kNone && !bad) {
+            if (!bad) {
                 const uint64_t k0 = (uint64_t)tile * G;
                 const uint32_t Gt = (uint32_t)min_u64(G, g.nb - k0);
                 // mu values: G * w is a multiple of 32, and the section is
@@ -261,17 +259,17 @@ __global__ void __launch_bounds__(kDThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
                 const uint64_t sbA = sb0 & ~uint64_t(15);
                 const uint64_t sbE = pad16(g.off_state + (k0 + Gt + 7) / 8);
                 st_boff[st] = (uint32_t)(sb0 - sbA);
+                uint8_t *stage = smem + st * L.stage;
                 mbar_arrive_expect_tx(&full[st], size + mu_bytes + (uint32_t)(sbE - sbA));
-                if (size) bulk_g2s(smem + st * L.stage, a.in + g.off_rec + r0, size, &full[st]);
-                bulk_g2s(smem + st * L.stage + L.mu, a.in + g.off_mu + k0 * w, mu_bytes, &full[st]);
-                bulk_g2s(smem + st * L.stage + L.bits, a.in + sbA, (uint32_t)(sbE - sbA), &full[st]);
+                if (size) bulk_g2s(stage, a.in + g.off_rec + r0, size, &full[st]);
+                bulk_g2s(stage + L.mu, a.in + g.off_mu + k0 * w, mu_bytes, &full[st]);
+                bulk_g2s(stage + L.bits, a.in + sbA, (uint32_t)(sbE - sbA), &full[st]);
                 copy_last |= 1u << st;
                 copy_par = (copy_par & ~(1u << st)) | ((k & 1u) << st);
             } else {
                 dmbar_arrive(&full[st]);
                 copy_last &= ~(1u << st);
             }
-            if (tile == kNone) break;
         }
         // do not leave while a copy may still be writing into shared memory
         for (int st = 0; st < kDStages; ++st)
@@ -279,86 +277,68 @@ __global__ void __launch_bounds__(kDThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
         return;
     }
 
-    if (warp == kDStorerWarp) {
-        // ---- storer: tensor stores of decoded tiles ------------------------
-        if (lane != 0) return;
-        for (uint32_t it = 0;; ++it) {
-            const int st = (int)(it % kDStages);
-            const uint32_t k = it / kDStages;
-            if (!mbar_wait_bounded(&done[st], k & 1u, 8 * a.copy_ns)) {
-                flag_status(a.status, 6u);
-                break;
-            }
-            const uint32_t tile = st_tile[st];
-            if (tile >= g.ntiles) break;
-            const uint64_t row0 = (uint64_t)tile * 256 * RPL;
-            if (st_store[st] && a.use_tma && row0 < a.rows_full) {
-#pragma unroll
-                for (int i = 0; i < RPL; ++i) {
-                    const uint64_t y = row0 + 256 * (uint64_t)i;
-                    if (y < a.rows_full) {
-                        asm volatile(
-                            "cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(
-                                reinterpret_cast<uint64_t>(&tmap)),
-                            "r"(0), "r"((int)y), "r"(smem_addr(smem + st * L.stage + i * 32768))
-                            : "memory");
-                    }
-                }
-                bulk_commit();
-                bulk_wait_read_all();  // the stage may be refilled once the store has read it
-            }
-            dmbar_arrive(&empty[st]);
-        }
-        bulk_wait_all();
-        return;
-    }
-
     // ---- decoders (warps 0..7) ---------------------------------------------
+    uint8_t *wbuf = smem + L.wbuf + warp * L.wbuf_bytes;
+    const uint32_t lane_row0 = (uint32_t)(lane * RPL);  // inside the warp's rows
     for (uint32_t it = 0;; ++it) {
+        const uint64_t tile64 = (uint64_t)blockIdx.x + (uint64_t)it * gridDim.x;
+        if (tile64 >= g.ntiles) break;
+        const uint32_t tile = (uint32_t)tile64;
         const int st = (int)(it % kDStages);
         const uint32_t k = it / kDStages;
-        if (!mbar_wait_bounded(&full[st], k & 1u, a.copy_ns)) s_abort = 1;
-        const uint32_t tile = st_tile[st];
+        // a wait that ran out still joins the barrier below (every decoding
+        // warp must), then the whole CTA stops
+        const bool waited = mbar_wait_bounded(&full[st], k & 1u, a.copy_ns);
+        if (!waited) s_abort = 1;
         const uint32_t size = st_size[st];
+        const bool pbad = st_bad[st] != 0 || !waited;
         uint8_t *rec = smem + st * L.stage;
-        uint32_t *sm_mk = reinterpret_cast<uint32_t *>(smem + st * L.stage + L.mk);
+        uint32_t *sm_mk = reinterpret_cast<uint32_t *>(rec + L.mk);
         const uint64_t k0 = (uint64_t)tile * G;
-        const uint32_t Gt = tile < g.ntiles ? (uint32_t)min_u64(G, g.nb - k0) : 0u;
+        const uint32_t Gt = (uint32_t)min_u64(G, g.nb - k0);
 
         // ---- ranks, codes, mid-byte counts --------------------------------
         const int sub = lane % LPB;
         const uint32_t blk = (uint32_t)(warp * BPW + lane / LPB);
-        const bool exists = blk < Gt && !st_bad[st];
+        const bool exists = blk < Gt && !pbad;
         const uint64_t kg = k0 + blk;
         const int len = exists ? (int)min_u64(b, g.n - kg * b) : 0;
         int nvalid = len - sub * VPL;
         nvalid = nvalid < 0 ? 0 : (nvalid > VPL ? VPL : nvalid);
         const bool full_lane = nvalid == VPL;
         // rank of the block among the tile's non-constant blocks: a popcount
-        // of the tile's state bits below it (the tile's bits start at a byte)
-        uint32_t rank = 0;
+        // of the tile's state bits below it
+        uint32_t rank = 0, nn_t = 0;
         bool nonconst = false;
-        uint32_t nn_t = 0;
-        if (tile < g.ntiles && !st_bad[st]) {
-            const uint8_t *stb = smem + st * L.stage + L.bits + st_boff[st];
-            for (uint32_t i = 0; i < (Gt + 7) / 8; i += 4) {
-                uint32_t wv = 0;
+        if (!pbad) {
+            const uint8_t *stb = rec + L.bits + st_boff[st];
+            if constexpr (G >= 32) {
+                // the tile's bits start at a multiple of 4 bytes
+                const uint32_t *sw = reinterpret_cast<const uint32_t *>(stb);
 #pragma unroll
-                for (int j = 0; j < 4; ++j)
-                    if (i + j < (Gt + 7) / 8) wv |= (uint32_t)stb[i + j] << (8 * j);
-                const uint32_t base = i * 8;
-                if (Gt - base < 32) wv &= (1u << (Gt - base)) - 1u;
-                nn_t += __popc(wv);
-                if (exists && blk >= base) {
-                    if (blk < base + 32) {
-                        rank += __popc(wv & ((1u << (blk - base)) - 1u));
-                        nonconst = (wv >> (blk - base)) & 1u;
-                    } else {
-                        rank += __popc(wv);
+                for (uint32_t i = 0; i < G / 32; ++i) {
+                    if (32 * i < Gt) {
+                        uint32_t wv = sw[i];
+                        if (Gt - 32 * i < 32) wv &= (1u << (Gt - 32 * i)) - 1u;
+                        nn_t += __popc(wv);
+                        if (blk >= 32 * i + 32) {
+                            rank += __popc(wv);
+                        } else if (blk >= 32 * i) {
+                            rank += __popc(wv & ((1u << (blk - 32 * i)) - 1u));
+                            nonconst = (wv >> (blk - 32 * i)) & 1u;
+                        }
                     }
                 }
+            } else {
+                uint32_t wv = stb[0];
+                if (G > 8) wv |= (uint32_t)stb[1] << 8;
+                wv &= (1u << Gt) - 1u;
+                nn_t = __popc(wv);
+                rank = __popc(wv & ((1u << blk) - 1u));
+                nonconst = (wv >> blk) & 1u;
             }
         }
+        nonconst = nonconst && exists;
         bool ok = (uint64_t)nn_t * (b / 4 + 1) <= size;
         nonconst = nonconst && ok;
         const int rq = nonconst ? (int)rec[nn_t * (b / 4) + rank] : 0;
@@ -392,48 +372,40 @@ __global__ void __launch_bounds__(kDThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
         uint32_t suml = 0;
 #pragma unroll
         for (int i = 0; i < NCODE; ++i) suml += __popc(codes[i] & 0x55555555u) + 2 * __popc(codes[i] & 0xAAAAAAAAu);
-        uint32_t mk = coded ? (uint32_t)(nvalid * q) - suml : (raw ? (uint32_t)nvalid * w : 0u);
+        const uint32_t mk_lane = coded ? (uint32_t)(nvalid * q) - suml : (raw ? (uint32_t)nvalid * w : 0u);
         const uint32_t segmask = (LPB == 32 ? kFull : ((1u << LPB) - 1u)) << (lane & ~(LPB - 1));
         {
             const uint32_t bal = __ballot_sync(kFull, ok);
             ok = (bal & segmask) == segmask;
         }
-#pragma unroll
-        for (int d = 1; d < LPB; d <<= 1) mk += __shfl_xor_sync(kFull, mk, d);
-        if (blk < G && sub == 0) sm_mk[blk] = (exists && nonconst) ? mk : 0u;
+        // the warp's blocks in order: an exclusive scan over lanes gives each
+        // block's mid-byte offset inside the warp's share of the record
+        uint32_t wtotal;
+        const uint32_t lane_excl = warp_exclusive_scan(mk_lane, &wtotal);
+        const uint32_t blk_excl = __shfl_sync(kFull, lane_excl, lane & ~(LPB - 1));
+        if (lane == 0) sm_mk[warp] = wtotal;
         if (!ok && exists) st_dbad[st] = 1;
         decoder_sync();
-        if (s_abort || tile >= g.ntiles) {
-            // hand the stage to the storer (it stops on the same tile), and stop
-            if (tid == 0) st_tile[st] = kNone;
-            decoder_sync();
-            if (lane == 0) dmbar_arrive(&done[st]);
-            break;
-        }
 
-        // ---- mid-byte offsets: every warp scans the tile's counts ----------
-        uint32_t midoff, total;
-        {
-            const uint32_t per = (Gt + 31) / 32;
-            const uint32_t lo = min(lane * per, Gt), hi = min(lo + per, Gt);
-            uint32_t c = 0;
-            for (uint32_t kk = lo; kk < hi; ++kk) c += sm_mk[kk];
-            uint32_t e = warp_exclusive_scan(c, &total);
-            const uint32_t chunk = blk / (per ? per : 1u);
-            uint32_t before = __shfl_sync(kFull, e, chunk < 32 ? (int)chunk : 0);
-            for (uint32_t kk = chunk * per; kk < blk && kk < Gt; ++kk) before += sm_mk[kk];
-            midoff = before;
+        // ---- mid-byte offsets: warps before this one -----------------------
+        uint32_t before = 0, total = 0;
+#pragma unroll
+        for (int i = 0; i < kDWarps; ++i) {
+            const uint32_t m = sm_mk[i];
+            total += m;
+            if (i < warp) before += m;
         }
         const uint32_t used = nn_t * (b / 4 + 1) + total;
-        // uniform over the CTA: st_bad and the counts were fixed before the barrier
-        const bool bad = st_bad[st] || st_dbad[st] || pad16(used) != size;
+        // uniform over the CTA: the flags and the counts were fixed before the barrier
+        const bool abort = s_abort != 0;
+        const bool bad = abort || st_bad[st] || st_dbad[st] || pad16(used) != size;
         U x[VPL];
         if (bad) {
-            if (tid == 0) flag_status(a.status, 3u);
+            if (tid == 0) flag_status(a.status, abort ? 6u : 3u);
         } else {
             // ---- decode --------------------------------------------------
-            const uint32_t mbase = nn_t * (b / 4 + 1) + midoff;
-            const U mu_bits = exists ? reinterpret_cast<const U *>(smem + st * L.stage + L.mu)[blk] : U(0);
+            const uint32_t mbase = nn_t * (b / 4 + 1) + before + blk_excl;
+            const U mu_bits = exists ? reinterpret_cast<const U *>(rec + L.mu)[blk] : U(0);
 
             using CntT = std::conditional_t<(LPB * VPL > 1023), unsigned long long, uint32_t>;
             constexpr int FB = LPB * VPL > 1023 ? 16 : 10;
@@ -494,38 +466,34 @@ __global__ void __launch_bounds__(kDThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
                         code8 |= inval;
                         dense8 = inval;
                     }
-                    // plane words: byte k = byte j of value 4gq + k
+                    // plane words: byte k = byte j of value 4gq + k; a leading
+                    // byte takes the nearest earlier owner's, or the carry
                     uint32_t P[W / 8];
 #pragma unroll
                     for (int j = 0; j < W / 8; ++j) P[j] = 0;
                     {
-                        const uint32_t e0 = lut->expand[code8];
-                        P[0] = dprmt(load_run(rec, pos0), 0, e0);
+                        const uint32_t e0 = lut[code8];
+                        P[0] = dprmt(load_run(rec, pos0), carry[0], e0);
                         pos0 += e0 >> 16;
-                        const uint32_t e1 = lut->expand[256 + code8];
-                        P[1] = dprmt(load_run(rec, pos1), 0, e1);
+                        carry[0] = P[0] >> 24;
+                        const uint32_t e1 = lut[256 + code8];
+                        P[1] = dprmt(load_run(rec, pos1), carry[1], e1);
                         pos1 += e1 >> 16;
+                        carry[1] = P[1] >> 24;
                         if (q >= 3) {
-                            const uint32_t e2 = lut->expand[512 + code8];
-                            P[2] = dprmt(load_run(rec, pos2), 0, e2);
+                            const uint32_t e2 = lut[512 + code8];
+                            P[2] = dprmt(load_run(rec, pos2), carry[2], e2);
                             pos2 += e2 >> 16;
+                            carry[2] = P[2] >> 24;
                         }
                         if (q >= 4) {
-                            const uint32_t sel = full_lane ? 0x3210u : lut->expand[512 + dense8];
+                            // dense planes: every valid value owns its byte
+                            const uint32_t sel = full_lane ? 0x3210u : lut[512 + dense8];
 #pragma unroll
                             for (int j = 3; j < W / 8; ++j)
                                 if (j < q)
                                     P[j] = dprmt(load_run(rec, dense0 + (uint32_t)(j - 3) * len + 4 * gq), 0, sel);
                         }
-                    }
-                    // leading bytes: copy the nearest earlier owner forward
-                    P[0] = dprmt(P[0], carry[0], lut->carry[code8]);
-                    carry[0] = P[0] >> 24;
-                    P[1] = dprmt(P[1], carry[1], lut->carry[256 + code8]);
-                    carry[1] = P[1] >> 24;
-                    if (lmax >= 3) {
-                        P[2] = dprmt(P[2], carry[2], lut->carry[512 + code8]);
-                        carry[2] = P[2] >> 24;
                     }
                     // planes back to words: t = (P0.k, P1.k, P2.k, P3.k), most significant first
                     U t[4];
@@ -559,61 +527,76 @@ __global__ void __launch_bounds__(kDThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
 #pragma unroll
                 for (int m = 0; m < VPL; ++m) x[m] = mu_bits;
             }
-
             // strictness: the record's pad bytes must be zero
             if (warp == 0)
                 for (uint32_t i = used + lane; i < size; i += 32)
                     if (rec[i]) flag_status(a.status, 3u);
         }
-        decoder_sync();  // the record is no longer read: the stage takes the output
+        // this warp no longer reads the stage
+        __syncwarp();
+        if (lane == 0) dmbar_arrive(&consumed[st]);
+        if (abort) break;
+        if (bad) continue;
 
-        if (!bad) {
-            if (exists && nvalid > 0) {
-                const uint32_t lane_row0 = (uint32_t)((warp * 32 + lane) * RPL);
-                const uint64_t grow0 = (uint64_t)tile * 256 * RPL + lane_row0;
+        // ---- output: full rows through the warp's buffer and a tensor store,
+        // the ragged last row with plain stores ------------------------------
+        const uint64_t wrow0 = (uint64_t)tile * 256 * RPL + (uint64_t)warp * 32 * RPL;  // warp's first row
+        const bool tma_rows = a.use_tma && wrow0 < a.rows_full;
+        if (tma_rows) {
+            // the buffer is free once the previous tile's store has read it
+            if (lane == 0) bulk_wait_read_all();
+            __syncwarp();
+        }
+        if (exists && nvalid > 0) {
 #pragma unroll
-                for (int rr = 0; rr < RPL; ++rr) {
-                    constexpr int VPR = 128 / w;  // values per row
-                    const int nv = nvalid - rr * VPR;
-                    if (nv <= 0) continue;
-                    if (a.use_tma && grow0 + rr < a.rows_full) {
-                        // full row: 128-byte-swizzled into the stage for the tensor store
-                        const uint32_t rowi = lane_row0 + rr;
-                        uint8_t *row = smem + st * L.stage + (rowi << 7);
+            for (int rr = 0; rr < RPL; ++rr) {
+                constexpr int VPR = 128 / w;  // values per row
+                const int nv = nvalid - rr * VPR;
+                if (nv <= 0) continue;
+                const uint32_t rowi = lane_row0 + rr;
+                if (a.use_tma && wrow0 + rowi < a.rows_full) {
+                    uint8_t *row = wbuf + (rowi << 7);
+#pragma unroll
+                    for (int c = 0; c < 8; ++c) {
+                        uint4 v;
+                        U *u = reinterpret_cast<U *>(&v);
+#pragma unroll
+                        for (int kk = 0; kk < 16 / w; ++kk) u[kk] = x[rr * VPR + c * (16 / w) + kk];
+                        *reinterpret_cast<uint4 *>(row + ((c ^ (rowi & 7u)) << 4)) = v;
+                    }
+                } else {
+                    U *dst = reinterpret_cast<U *>(a.out) + kg * b + sub * VPL + rr * VPR;
+                    if (nv >= VPR) {
 #pragma unroll
                         for (int c = 0; c < 8; ++c) {
                             uint4 v;
                             U *u = reinterpret_cast<U *>(&v);
 #pragma unroll
                             for (int kk = 0; kk < 16 / w; ++kk) u[kk] = x[rr * VPR + c * (16 / w) + kk];
-                            *reinterpret_cast<uint4 *>(row + ((c ^ (rowi & 7u)) << 4)) = v;
+                            reinterpret_cast<uint4 *>(dst)[c] = v;
                         }
                     } else {
-                        U *dst = reinterpret_cast<U *>(a.out) + kg * b + sub * VPL + rr * VPR;
-                        if (nv >= VPR) {
 #pragma unroll
-                            for (int c = 0; c < 8; ++c) {
-                                uint4 v;
-                                U *u = reinterpret_cast<U *>(&v);
-#pragma unroll
-                                for (int kk = 0; kk < 16 / w; ++kk) u[kk] = x[rr * VPR + c * (16 / w) + kk];
-                                reinterpret_cast<uint4 *>(dst)[c] = v;
-                            }
-                        } else {
-#pragma unroll
-                            for (int m = 0; m < VPR; ++m)
-                                if (m < nv) dst[m] = x[rr * VPR + m];
-                        }
+                        for (int m = 0; m < VPR; ++m)
+                            if (m < nv) dst[m] = x[rr * VPR + m];
                     }
                 }
             }
         }
-        if (tid == 0) st_store[st] = bad ? 0u : 1u;
-        // the storer takes the stage once every warp has written its rows
-        fence_proxy_async_smem();
-        __syncwarp();
-        if (lane == 0) dmbar_arrive(&done[st]);
+        if (tma_rows) {
+            fence_proxy_async_smem();
+            __syncwarp();
+            if (lane == 0) {
+                asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(
+                                 reinterpret_cast<uint64_t>(&tmap)),
+                             "r"(0), "r"((int)wrow0), "r"(smem_addr(wbuf))
+                             : "memory");
+                bulk_commit();
+            }
+        }
     }
+    // stores must finish reading shared memory (and land) before the CTA leaves
+    if (lane == 0) bulk_wait_all();
 }
 
 // ---------------------------------------------------------------------------
@@ -651,7 +634,9 @@ cudaError_t launch_decompress(const void *in, uint64_t in_bytes, uint64_t total_
     a.copy_ns = 1000ull * wait_limit_from_env("SZX_COPY_US", 1000000u);
     a.rows_full = n * (dtype == 0 ? 4 : 8) / 128;
     CUtensorMap tm;
-    a.use_tma = encode_row_map(&tm, out, a.rows_full) ? 1u : 0u;
+    // one box per decoding warp: its 32 lanes' rows
+    const uint32_t box_rows = (dtype == 1 && block == 1024) ? 64u : 32u;
+    a.use_tma = encode_row_map(&tm, out, a.rows_full, box_rows) ? 1u : 0u;
     if (dtype == 0) {
         switch (block) {
             case 32: return launch_t<float, 1, 32>(tm, a, stream);

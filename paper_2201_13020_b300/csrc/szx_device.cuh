@@ -246,7 +246,7 @@ __device__ __forceinline__ void st_release_u64(uint64_t *p, uint64_t v) {
 
 __host__ __device__ __forceinline__ uint64_t pad16(uint64_t x) { return (x + 15) & ~uint64_t(15); }
 
-__host__ __device__ __forceinline__ uint32_t tile_blocks(uint32_t b, uint32_t w) {
+__host__ __device__ constexpr uint32_t tile_blocks(uint32_t b, uint32_t w) {
     uint32_t g = 32768u / (b * w);
     return g < 8 ? 8 : g;
 }

@@ -12,9 +12,10 @@ namespace szx {
 uint32_t wait_limit_from_env(const char *name, uint32_t fallback);
 
 // Encode a 2-D TMA tensor map over `rows` rows of 128 bytes at base (32-bit
-// elements, 32 x 256 box = 32 KiB, 128-byte swizzle).  False if rows is 0 or
-// >= 2^31, or the driver entry point is unavailable or rejects the map.
-bool encode_row_map(CUtensorMap *tm, const void *base, uint64_t rows);
+// elements, a box of 32 x box_rows (<= 256), 128-byte swizzle).  False if
+// rows is 0 or >= 2^31, or the driver entry point is unavailable or rejects
+// the map.
+bool encode_row_map(CUtensorMap *tm, const void *base, uint64_t rows, uint32_t box_rows);
 
 // Enqueue the compression of n values (dtype 0 = f32, 1 = f64) with bound bits
 // e_bits into the stream at out; the workspace starts ws_offset bytes into
