@@ -191,7 +191,7 @@ __device__ __forceinline__ bool bound_check_needed(T mn, T mx, T mu, int R, type
 template <typename T, int LPB, int VPL, bool FULL>
 __device__ __forceinline__ void encode_lane(typename Fmt<T>::U (&x)[VPL], uint32_t (&codes)[(2 * VPL + 31) / 32],
                                             int &kind, int &req, int &req0, T &mu_out, uint32_t &mk_out,
-                                            const uint8_t *buf, uint32_t lane_row0, int nvalid, bool exists, T e,
+                                            const typename Fmt<T>::U *src, int nvalid, bool exists, T e,
                                             uint64_t e_bits, Workspace *ws, uint32_t tile) {
     using F = Fmt<T>;
     using U = typename F::U;
@@ -297,10 +297,9 @@ __device__ __forceinline__ void encode_lane(typename Fmt<T>::U (&x)[VPL], uint32
 #pragma unroll
             for (int m = 0; m < VPL; ++m) {
                 if (m < nvalid) {
-                    const uint32_t byte = (uint32_t)(m * w);
-                    const uint32_t rowi = lane_row0 + (byte >> 7), cb = byte & 127u;
-                    const uint32_t phys = (rowi << 7) | ((((cb >> 4) ^ (rowi & 7u))) << 4) | (cb & 15u);
-                    const T xv = F::from(*reinterpret_cast<const U *>(buf + phys));
+                    // the lane's input values (its shared-memory rows are
+                    // already cleared for the record): re-read from global
+                    const T xv = F::from(src[m]);
                     const U t = (F::bits(F::sub(xv, mu)) >> s) & mask;
                     ok2 = ok2 && within(xv, F::add(F::from((U)(t << s)), mu), e);
                     x[m] = t;
@@ -339,10 +338,8 @@ __device__ __forceinline__ void encode_lane(typename Fmt<T>::U (&x)[VPL], uint32
     uint32_t suml = 0;
 #pragma unroll
     for (int i = 0; i < NCODE; ++i) suml += __popc(codes[i] & 0x55555555u) + 2 * __popc(codes[i] & 0xAAAAAAAAu);
-    uint32_t mk = kind == kNonConst ? (uint32_t)(nvalid * q) - suml : (kind == kRaw ? (uint32_t)nvalid * w : 0u);
-#pragma unroll
-    for (int d = 1; d < LPB; d <<= 1) mk += __shfl_xor_sync(kFull, mk, d);
-    mk_out = mk;
+    // this lane's mid bytes (raw: its verbatim bytes)
+    mk_out = kind == kNonConst ? (uint32_t)(nvalid * q) - suml : (kind == kRaw ? (uint32_t)nvalid * w : 0u);
 }
 
 // Shared-memory layout of the compress kernel: kStages tile buffers (each
@@ -358,7 +355,7 @@ static_assert(kConsumers == kThreads, "a tile is laid out over 8 warps");
 struct CSmem {
     uint32_t buf_stride, buf_bytes;  // tile buffer st at st * buf_stride (1024-aligned)
     uint32_t meta0, meta_stride;     // metadata block st at meta0 + st * meta_stride
-    uint32_t m_kind, m_req, m_mk, m_mu, m_rank, m_midoff;  // offsets inside a metadata block
+    uint32_t m_kind, m_w;  // offsets inside a metadata block: block kinds, per-warp totals
     uint32_t lut, total;
 };
 __host__ __device__ inline CSmem compress_smem(uint32_t G, uint32_t b, uint32_t w) {
@@ -376,11 +373,7 @@ __host__ __device__ inline CSmem compress_smem(uint32_t G, uint32_t b, uint32_t 
         return at;
     };
     s.m_kind = mtake(G);
-    s.m_req = mtake(G);
-    s.m_mk = mtake(4 * G);
-    s.m_mu = mtake(w * G);
-    s.m_rank = mtake(4 * G);
-    s.m_midoff = mtake(4 * G);
+    s.m_w = mtake(16 * kConsumerWarps);
     s.meta_stride = (m + 15) & ~15u;
     s.meta0 = (kStages - 1) * s.buf_stride + s.buf_bytes;  // after the last buffer (16-aligned)
     s.lut = s.meta0 + kStages * s.meta_stride;
@@ -388,8 +381,6 @@ __host__ __device__ inline CSmem compress_smem(uint32_t G, uint32_t b, uint32_t 
     s.total = ((o + 1023) & ~1023u) + 1024;  // + slack to realign the dynamic base
     return s;
 }
-
-__device__ __forceinline__ void consumer_sync() { asm volatile("bar.sync 1, %0;" ::"n"(kConsumers) : "memory"); }
 
 __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
     asm volatile(
@@ -413,11 +404,11 @@ __global__ void __launch_bounds__(kCThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
     static_assert(RPL >= 1 && NCODE >= 1, "lane geometry");
 
     extern __shared__ __align__(16) uint8_t smem_raw[];  // realigned to 1024 below
-    // full: tile copied in; ready: record written; empty: record stored
-    __shared__ __align__(8) uint64_t full[kStages], ready[kStages], empty[kStages];
-    __shared__ uint32_t st_tile[kStages], st_nn[kStages], st_mid[kStages], st_nraw[kStages], st_nesc[kStages],
-        st_rec[kStages], st_fail[kStages];
-    __shared__ uint32_t s_abort;
+    // full: tile copied in; encoded: every consumer warp has its blocks'
+    // totals in place; ready: record written; empty: record stored
+    __shared__ __align__(8) uint64_t full[kStages], encoded[kStages], ready[kStages], empty[kStages];
+    __shared__ uint32_t st_tile[kStages], st_nn[kStages], st_nraw[kStages], st_nesc[kStages], st_rec[kStages],
+        st_fail[kStages];
 
     // the 128-byte swizzle of the tensor copy needs 1024-byte aligned buffers
     uint8_t *smem = smem_raw + ((1024u - (smem_addr(smem_raw) & 1023u)) & 1023u);
@@ -435,14 +426,14 @@ __global__ void __launch_bounds__(kCThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
     if (tid == 0) {
         for (int i = 0; i < kStages; ++i) {
             mbar_init(&full[i], 1);
-            mbar_init(&ready[i], kConsumers);
+            mbar_init(&encoded[i], kConsumerWarps);
+            mbar_init(&ready[i], kConsumerWarps);
             mbar_init(&empty[i], 1);
         }
         fence_mbar_init();
-        s_abort = 0;
         for (int i = 0; i < kStages; ++i) {
             st_tile[i] = 0xFFFFFFFFu;
-            st_nn[i] = st_mid[i] = st_nraw[i] = st_nesc[i] = st_rec[i] = st_fail[i] = 0;
+            st_nn[i] = st_nraw[i] = st_nesc[i] = st_rec[i] = st_fail[i] = 0;
         }
     }
     __syncthreads();
@@ -493,7 +484,8 @@ __global__ void __launch_bounds__(kCThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
     }
 
     if (warp == kStorerWarp) {
-        // ---- storer: look-back, index entry, record store, state and mu ----
+        // ---- storer: look-back, index entry, record store --------------------
+        unsigned long long c_nn = 0, c_raw = 0, c_esc = 0;  // this CTA's counts
         for (uint32_t it = 0;; ++it) {
             const int st = (int)(it % kStages);
             const uint32_t k = it / kStages;
@@ -503,12 +495,7 @@ __global__ void __launch_bounds__(kCThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
             }
             const uint32_t tile = st_tile[st];
             if (tile >= g.ntiles) break;
-            const uint8_t *meta = smem + (L.meta0 + st * L.meta_stride);
-            const uint8_t *m_kind = meta + L.m_kind;
-            const U *m_mu = reinterpret_cast<const U *>(meta + L.m_mu);
             const uint32_t rec_bytes = st_rec[st];
-            const uint64_t k0 = (uint64_t)tile * G;
-            const uint32_t Gt = (uint32_t)min_u64(G, g.nb - k0);
             // warp-parallel decoupled look-back: 32 predecessors per probe,
             // lane i looking at tile - 1 - i; stop at the nearest inclusive
             // prefix, adding the aggregates in between
@@ -519,7 +506,7 @@ __global__ void __launch_bounds__(kCThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
                 int64_t base = (int64_t)tile - 1;
                 while (base >= 0) {
                     const int64_t j = base - lane;
-                    const uint64_t wv = j >= 0 ? ld_acquire_u64(&a.lookback[j]) : kFlagPrefix;
+                    const uint64_t wv = j >= 0 ? ld_relaxed_u64(&a.lookback[j]) : kFlagPrefix;
                     const uint64_t flag = wv & ~kValueMask;
                     const uint32_t pre = __ballot_sync(kFull, flag == kFlagPrefix);
                     const uint32_t inv = __ballot_sync(kFull, flag == 0);
@@ -543,6 +530,7 @@ __global__ void __launch_bounds__(kCThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
                 }
             }
             if (lane == 0) {
+                st_relaxed_u64(&a.lookback[tile], kFlagPrefix | (excl + rec_bytes));
                 if (st_fail[st]) {
                     atomicOr(&a.ws->err, kErrTmaTimeout);
                     atomicAdd(&a.ws->tma_timeouts, 1u);
@@ -553,7 +541,6 @@ __global__ void __launch_bounds__(kCThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
                     atomicAdd(&a.ws->lookback_timeouts, 1ull);
                     atomicCAS(&a.ws->first_lb_tile, 0u, tile + 1);
                 }
-                st_release_u64(&a.lookback[tile], kFlagPrefix | (excl + rec_bytes));
                 uint64_t *idx = reinterpret_cast<uint64_t *>(a.out + g.off_index);
                 idx[tile] = excl;
                 if (tile == g.ntiles - 1) {
@@ -568,106 +555,81 @@ __global__ void __launch_bounds__(kCThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
                     bulk_s2g(a.out + g.off_rec + excl, smem + st * L.buf_stride, rec_bytes);
                     bulk_commit();
                 }
-                atomicAdd(&a.ws->nn, (unsigned long long)st_nn[st]);
-                atomicAdd(&a.ws->nraw, (unsigned long long)st_nraw[st]);
-                atomicAdd(&a.ws->nesc, (unsigned long long)st_nesc[st]);
-            }
-            // state bits and mu values of the tile (fixed positions)
-            {
-                uint8_t *state = a.out + g.off_state + (size_t)k0 / 8;
-                for (uint32_t i = lane; i < (Gt + 7) / 8; i += 32) {
-                    uint32_t byte = 0;
-                    for (int j = 0; j < 8; ++j) {
-                        const uint32_t kk = i * 8 + j;
-                        if (kk < Gt && m_kind[kk] != kConst) byte |= 1u << j;
-                    }
-                    state[i] = (uint8_t)byte;
-                }
-                U *mu_dst = reinterpret_cast<U *>(a.out + g.off_mu) + k0;
-                for (uint32_t i = lane; i < Gt; i += 32) mu_dst[i] = m_mu[i];
-            }
-            __syncwarp();
-            if (lane == 0) {
+                c_nn += st_nn[st];
+                c_raw += st_nraw[st];
+                c_esc += st_nesc[st];
                 // the buffer is free once the store has read it
                 if (rec_bytes) bulk_wait_read_all();
                 mbar_arrive(&empty[st]);
-                __threadfence();
-                const uint32_t done = atomicAdd(&a.ws->done, 1u);
-                if (done == g.ntiles - 1) {
-                    __threadfence();
-                    volatile Workspace *ws = a.ws;
-                    const uint64_t rec_total = reinterpret_cast<volatile uint64_t *>(a.out + g.off_index)[g.ntiles];
-                    const uint64_t total = g.off_rec + rec_total;
-                    uint32_t *h32 = reinterpret_cast<uint32_t *>(a.out);
-                    uint64_t *h64 = reinterpret_cast<uint64_t *>(a.out);
-                    h32[0] = kMagic;
-                    h32[1] = kVersion | (a.dtype << 8);
-                    h32[2] = b;
-                    h32[3] = G;
-                    h64[2] = g.n;
-                    h64[3] = a.e_bits;
-                    h64[4] = ws->nn;
-                    h64[5] = ws->nraw;
-                    h64[6] = ws->nesc;
-                    h64[7] = total;
-                    const uint64_t status = (ws->err & (kErrTimeout | kErrTmaTimeout)) ? 6ull
-                                            : (ws->err & kErrInternal)                 ? 5ull
-                                                                                       : 0ull;
-                    ws->result[0] = total;
-                    ws->result[1] = status;
-                    if (a.d_result) {
-                        a.d_result[0] = total;
-                        a.d_result[1] = status;
-                    }
-                }
             }
             __syncwarp();
+        }
+        if (lane == 0) {
+            // this CTA's counts; the last CTA to get here writes the header
+            atomicAdd(&a.ws->nn, c_nn);
+            atomicAdd(&a.ws->nraw, c_raw);
+            atomicAdd(&a.ws->nesc, c_esc);
+            __threadfence();
+            const uint32_t done = atomicAdd(&a.ws->done, 1u);
+            if (done == gridDim.x - 1) {
+                __threadfence();
+                volatile Workspace *ws = a.ws;
+                const uint64_t rec_total = reinterpret_cast<volatile uint64_t *>(a.out + g.off_index)[g.ntiles];
+                const uint64_t total = g.off_rec + rec_total;
+                uint32_t *h32 = reinterpret_cast<uint32_t *>(a.out);
+                uint64_t *h64 = reinterpret_cast<uint64_t *>(a.out);
+                h32[0] = kMagic;
+                h32[1] = kVersion | (a.dtype << 8);
+                h32[2] = b;
+                h32[3] = G;
+                h64[2] = g.n;
+                h64[3] = a.e_bits;
+                h64[4] = ws->nn;
+                h64[5] = ws->nraw;
+                h64[6] = ws->nesc;
+                h64[7] = total;
+                const uint64_t status = (ws->err & (kErrTimeout | kErrTmaTimeout)) ? 6ull
+                                        : (ws->err & kErrInternal)                 ? 5ull
+                                                                                   : 0ull;
+                ws->result[0] = total;
+                ws->result[1] = status;
+                if (a.d_result) {
+                    a.d_result[0] = total;
+                    a.d_result[1] = status;
+                }
+            }
         }
         return;
     }
 
     // ---- consumers (warps 0..7): encode tiles into records ------------------
+    // The warps of a CTA meet once per tile (the `encoded` mbarrier, after
+    // which the tile's totals are known); every wait is bounded.
     const T e = F::from((U)a.e_bits);
     for (uint32_t it = 0;; ++it) {
         const int st = (int)(it % kStages);
         const uint32_t k = it / kStages;
-        if (!mbar_wait_bounded(&full[st], k & 1u, a.copy_ns)) s_abort = 1;
-        consumer_sync();
-        const uint32_t tile = st_tile[st];
-        if (s_abort || tile >= g.ntiles) {
-            // hand the stage to the storer (it stops on the same tile), and stop
-            if (s_abort && tid == 0) st_tile[st] = 0xFFFFFFFFu;
-            consumer_sync();
-            mbar_arrive(&ready[st]);
-            if (s_abort && tid == 0) atomicOr(&a.ws->err, kErrTmaTimeout);
+        const bool waited = mbar_wait_bounded(&full[st], k & 1u, a.copy_ns);
+        const uint32_t tile = waited ? st_tile[st] : 0xFFFFFFFFu;
+        if (tile >= g.ntiles) {
+            // the producer is done (or the copy never arrived): hand the stage
+            // to the storer, which stops on it, and stop
+            if (!waited && lane == 0) {
+                atomicOr(&a.ws->err, kErrTmaTimeout);
+                st_tile[st] = 0xFFFFFFFFu;
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&ready[st]);
             break;
         }
         uint8_t *buf = smem + st * L.buf_stride;
         uint8_t *meta = smem + (L.meta0 + st * L.meta_stride);
         uint8_t *sm_kind = meta + L.m_kind;
-        uint8_t *sm_req = meta + L.m_req;
-        uint32_t *sm_mk = reinterpret_cast<uint32_t *>(meta + L.m_mk);
-        U *sm_mu = reinterpret_cast<U *>(meta + L.m_mu);
-        uint32_t *sm_rank = reinterpret_cast<uint32_t *>(meta + L.m_rank);
-        uint32_t *sm_midoff = reinterpret_cast<uint32_t *>(meta + L.m_midoff);
+        uint4 *sm_w = reinterpret_cast<uint4 *>(meta + L.m_w);  // per warp: nn, mid, raw, escalated
         const uint64_t k0 = (uint64_t)tile * G;
         const uint32_t Gt = (uint32_t)min_u64(G, g.nb - k0);
         const uint64_t row0 = (uint64_t)tile * 256 * RPL;
         const bool tma = a.use_tma && row0 < a.rows_full;
-        // rows beyond the fully-covered ones (the input's ragged end, or every
-        // row when the tensor copy is not used): plain loads, swizzled layout
-        {
-            const uint64_t tile_vals = min_u64((uint64_t)G * b, g.n - k0 * b);
-            const uint64_t first_plain = tma ? min_u64((a.rows_full - row0) * (128 / w), tile_vals) : 0;
-            const uint64_t in0 = k0 * b;
-            for (uint64_t i = first_plain + tid; i < tile_vals; i += kConsumers) {
-                const uint32_t byte = (uint32_t)(i * w);
-                const uint32_t row = byte >> 7, chunk = (byte >> 4) & 7u;
-                const uint32_t phys = (row << 7) | ((chunk ^ (row & 7u)) << 4) | (byte & 15u);
-                *reinterpret_cast<U *>(buf + phys) = reinterpret_cast<const U *>(a.in)[in0 + i];
-            }
-            if (first_plain < tile_vals) consumer_sync();
-        }
 
         // ---- 1. block statistics and encoding (registers) -------------------
         const int sub = lane % LPB;
@@ -679,82 +641,117 @@ __global__ void __launch_bounds__(kCThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
         nvalid = nvalid < 0 ? 0 : (nvalid > VPL ? VPL : nvalid);
         const bool full_lane = nvalid == VPL;
         const uint32_t lane_row0 = (uint32_t)((warp * 32 + lane) * RPL);
+        // the lane's values in global memory (read only below nvalid)
+        const U *src = reinterpret_cast<const U *>(a.in) + kg * b + sub * VPL;
 
+        // rows the tensor copy brought in come from shared memory; the
+        // input's ragged end (or every row without the tensor copy) from global
+        constexpr int VPR = 128 / w;  // values per row
         U x[VPL];
 #pragma unroll
         for (int rr = 0; rr < RPL; ++rr) {
             const uint32_t rowi = lane_row0 + rr;
+            if (tma && row0 + rowi < a.rows_full) {
 #pragma unroll
-            for (int c = 0; c < 8; ++c) {
-                const uint4 v = *reinterpret_cast<const uint4 *>(buf + (rowi << 7) + ((c ^ (rowi & 7u)) << 4));
-                const U *u = reinterpret_cast<const U *>(&v);
+                for (int c = 0; c < 8; ++c) {
+                    const uint4 v = *reinterpret_cast<const uint4 *>(buf + (rowi << 7) + ((c ^ (rowi & 7u)) << 4));
+                    const U *u = reinterpret_cast<const U *>(&v);
 #pragma unroll
-                for (int kk = 0; kk < 16 / w; ++kk) x[rr * (128 / w) + c * (16 / w) + kk] = u[kk];
+                    for (int kk = 0; kk < 16 / w; ++kk) x[rr * VPR + c * (16 / w) + kk] = u[kk];
+                }
+            } else {
+#pragma unroll
+                for (int m = 0; m < VPR; ++m) x[rr * VPR + m] = rr * VPR + m < nvalid ? src[rr * VPR + m] : U(0);
             }
+        }
+        // this lane's rows are read: clear them, the buffer becomes the record
+        // (the exact slow path below re-reads the input from global memory)
+        {
+            const uint4 z = make_uint4(0, 0, 0, 0);
+#pragma unroll
+            for (int rr = 0; rr < RPL; ++rr) {
+                const uint32_t rowi = lane_row0 + rr;
+#pragma unroll
+                for (int c = 0; c < 8; ++c) *reinterpret_cast<uint4 *>(buf + (rowi << 7) + ((c ^ (rowi & 7u)) << 4)) = z;
+            }
+            if (warp == kConsumerWarps - 1)
+                for (uint32_t i = 32768u * RPL + 16u * lane; i < L.buf_bytes; i += 16u * 32u)
+                    *reinterpret_cast<uint4 *>(buf + i) = z;
         }
         uint32_t codes[NCODE];
         int kind, req, req0;
         T mu;
-        uint32_t mk;
+        uint32_t mk_lane;
         if (__all_sync(kFull, full_lane)) {
-            encode_lane<T, LPB, VPL, true>(x, codes, kind, req, req0, mu, mk, buf, lane_row0, nvalid, exists, e,
+            encode_lane<T, LPB, VPL, true>(x, codes, kind, req, req0, mu, mk_lane, src, nvalid, exists, e,
                                            a.e_bits, a.ws, tile);
         } else {
-            encode_lane<T, LPB, VPL, false>(x, codes, kind, req, req0, mu, mk, buf, lane_row0, nvalid, exists, e,
+            encode_lane<T, LPB, VPL, false>(x, codes, kind, req, req0, mu, mk_lane, src, nvalid, exists, e,
                                             a.e_bits, a.ws, tile);
         }
-        if (SZX_CHECKS && exists && sub == 0 && mk > (uint32_t)len * w) report_bad(a.ws, tile, 4);
-        if (exists && sub == 0) {
+        const bool lead = exists && sub == 0;  // the block's first lane
+        if (lead) {
             sm_kind[blk] = (uint8_t)kind;
-            sm_req[blk] = kind == kNonConst ? (uint8_t)req : (uint8_t)0xFF;
-            sm_mk[blk] = mk;
-            sm_mu[blk] = kind == kRaw ? U(0) : F::bits(mu);
-            if (kind == kNonConst && req > req0) atomicAdd(&st_nesc[st], 1u);
+            reinterpret_cast<U *>(a.out + g.off_mu)[kg] = kind == kRaw ? U(0) : F::bits(mu);
         }
-        consumer_sync();
-
-        // ---- 2. clear the buffer for the record; tile scan -----------------
-        {
-            uint4 *p = reinterpret_cast<uint4 *>(buf);
-            const uint4 z = make_uint4(0, 0, 0, 0);
-            for (uint32_t i = tid; i < L.buf_bytes / 16; i += kConsumers) p[i] = z;
-        }
-        if (warp == 0) {
-            const uint32_t per = (Gt + 31) / 32;
-            const uint32_t lo = min(lane * per, Gt), hi = min(lo + per, Gt);
-            uint32_t c_nn = 0, c_mid = 0, c_raw = 0;
-            for (uint32_t kk = lo; kk < hi; ++kk) {
-                if (sm_kind[kk] != kConst) {
-                    c_nn += 1;
-                    c_mid += sm_mk[kk];
-                    c_raw += sm_kind[kk] == kRaw;
-                }
-            }
-            uint32_t t_nn, t_mid, t_raw;
-            uint32_t e_nn = warp_exclusive_scan(c_nn, &t_nn);
-            uint32_t e_mid = warp_exclusive_scan(c_mid, &t_mid);
-            warp_exclusive_scan(c_raw, &t_raw);
-            for (uint32_t kk = lo; kk < hi; ++kk) {
-                sm_rank[kk] = e_nn;
-                sm_midoff[kk] = e_mid;
-                if (sm_kind[kk] != kConst) {
-                    e_nn += 1;
-                    e_mid += sm_mk[kk];
-                }
-            }
+        // the warp's totals; its blocks are consecutive, so an exclusive scan
+        // over lanes gives each block's mid-byte offset inside the warp's share
+        uint32_t mid_w;
+        const uint32_t lane_excl = warp_exclusive_scan(mk_lane, &mid_w);
+        const uint32_t nonc_bal = __ballot_sync(kFull, lead && kind != kConst);
+        const uint32_t raw_bal = __ballot_sync(kFull, lead && kind == kRaw);
+        const uint32_t esc_bal = __ballot_sync(kFull, lead && kind == kNonConst && req > req0);
+        if (lane == 0) sm_w[warp] = make_uint4(__popc(nonc_bal), mid_w, __popc(raw_bal), __popc(esc_bal));
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&encoded[st]);
+        if (!mbar_wait_bounded(&encoded[st], k & 1u, a.lookback_ns + a.copy_ns)) {
+            // a warp of this CTA never finished the tile: give up
             if (lane == 0) {
-                uint32_t rec = (uint32_t)pad16((uint64_t)t_nn * (b / 4 + 1) + t_mid);
-                if (SZX_CHECKS && rec > record_max_bytes(G, b, w)) {
-                    report_bad(a.ws, tile, 2);
-                    rec = 0;
+                atomicOr(&a.ws->err, kErrTimeout);
+                st_tile[st] = 0xFFFFFFFFu;
+                mbar_arrive(&ready[st]);
+            }
+            break;
+        }
+
+        // ---- 2. tile totals, the aggregate for the look-back, state bits ----
+        uint32_t nn_before = 0, mid_before = 0, nn_t = 0, mid_t = 0, raw_t = 0, esc_t = 0;
+#pragma unroll
+        for (int i = 0; i < kConsumerWarps; ++i) {
+            const uint4 v = sm_w[i];
+            if (i < warp) {
+                nn_before += v.x;
+                mid_before += v.y;
+            }
+            nn_t += v.x;
+            mid_t += v.y;
+            raw_t += v.z;
+            esc_t += v.w;
+        }
+        const uint32_t rec_bytes = (uint32_t)pad16((uint64_t)nn_t * (b / 4 + 1) + mid_t);
+        if (warp == 0) {
+            if (lane == 0) {
+                st_nn[st] = nn_t;
+                st_nraw[st] = raw_t;
+                st_nesc[st] = esc_t;
+                st_rec[st] = rec_bytes;
+                st_relaxed_u64(&a.lookback[tile], kFlagAgg | rec_bytes);
+            }
+            // state bits: bit i of byte j is set when block 8j + i is not constant
+            uint8_t *state = a.out + g.off_state + (size_t)k0 / 8;
+            for (uint32_t j = lane; j < (Gt + 7) / 8; j += 32) {
+                uint32_t byte = 0;
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    const uint32_t kk = j * 8 + i;
+                    if (kk < Gt && sm_kind[kk] != kConst) byte |= 1u << i;
                 }
-                st_nn[st] = t_nn;
-                st_mid[st] = t_mid;
-                st_nraw[st] = t_raw;
-                st_rec[st] = rec;
-                st_release_u64(&a.lookback[tile], kFlagAgg | rec);
+                state[j] = (uint8_t)byte;
             }
         }
+        if (SZX_CHECKS && rec_bytes > record_max_bytes(G, b, w) && tid == 0) report_bad(a.ws, tile, 2);
+        const uint32_t rank = nn_before + __popc(nonc_bal & ((1u << (lane & ~(LPB - 1))) - 1u));
+        const uint32_t mk_blk_excl = __shfl_sync(kFull, lane_excl, lane & ~(LPB - 1));
 
         // per-lane counts of values with code <= j (j = 0, 1, 2), packed in
         // FB-bit fields, and their exclusive scan over the block's lanes.
@@ -782,11 +779,8 @@ __global__ void __launch_bounds__(kCThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
         }
         const CntT tot = __shfl_sync(kFull, incl, (lane & ~(LPB - 1)) + LPB - 1);
         const CntT off = incl - cnt;
-        consumer_sync();
 
         // ---- 3. the record --------------------------------------------------
-        const uint32_t nn_t = st_nn[st];
-        const uint32_t rec_bytes = st_rec[st];
         uint32_t *words = reinterpret_cast<uint32_t *>(buf);
         // every record write goes through put(): a self-checked build verifies
         // that it lands inside the record
@@ -798,8 +792,7 @@ __global__ void __launch_bounds__(kCThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
             or_bytes(words, p, run, c);
         };
         if (exists && kind != kConst) {
-            const uint32_t rank = sm_rank[blk];
-            const uint32_t mbase = nn_t * (b / 4 + 1) + sm_midoff[blk];
+            const uint32_t mbase = nn_t * (b / 4 + 1) + mid_before + mk_blk_excl;
             if (sub == 0) {
                 // the reqBits byte's word may also hold mid bytes: OR it in too
                 const uint32_t p = nn_t * (b / 4) + rank;
@@ -888,9 +881,11 @@ __global__ void __launch_bounds__(kCThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
         // hand the record to the storer (its bulk store reads it through the
         // async proxy)
         fence_proxy_async_smem();
-        mbar_arrive(&ready[st]);
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&ready[st]);
     }
 }
+
 
 // ---------------------------------------------------------------------------
 // host side
