@@ -112,6 +112,18 @@ __device__ __forceinline__ float max_nan(float a, float b) {
     return r;
 }
 
+// three-input forms (one instruction for two values)
+__device__ __forceinline__ float min3_nan(float a, float b, float c) {
+    float r;
+    asm("min.NaN.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
+__device__ __forceinline__ float max3_nan(float a, float b, float c) {
+    float r;
+    asm("max.NaN.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
+
 __device__ __forceinline__ uint32_t prmt(uint32_t a, uint32_t b, uint32_t s) { return __byte_perm(a, b, s); }
 
 // OR a run of cnt <= 4 bytes (little-endian in `run`) into the zero-initialised
@@ -206,11 +218,21 @@ __device__ __forceinline__ void encode_lane(typename Fmt<T>::U (&x)[VPL], uint32
     S kmn = std::numeric_limits<S>::max(), kmx = std::numeric_limits<S>::min();
     if constexpr (sizeof(T) == 4) {
         float lmn = F::from(x[0]), lmx = F::from(x[0]);
+        if constexpr (FULL && VPL % 2 == 0) {
 #pragma unroll
-        for (int m = 1; m < VPL; ++m) {
-            if (FULL || m < nvalid) {
-                lmn = min_nan(lmn, F::from(x[m]));
-                lmx = max_nan(lmx, F::from(x[m]));
+            for (int m = 1; m + 1 < VPL; m += 2) {
+                lmn = min3_nan(lmn, F::from(x[m]), F::from(x[m + 1]));
+                lmx = max3_nan(lmx, F::from(x[m]), F::from(x[m + 1]));
+            }
+            lmn = min_nan(lmn, F::from(x[VPL - 1]));
+            lmx = max_nan(lmx, F::from(x[VPL - 1]));
+        } else {
+#pragma unroll
+            for (int m = 1; m < VPL; ++m) {
+                if (FULL || m < nvalid) {
+                    lmn = min_nan(lmn, F::from(x[m]));
+                    lmx = max_nan(lmx, F::from(x[m]));
+                }
             }
         }
         if (FULL || nvalid > 0) {
@@ -326,10 +348,11 @@ __device__ __forceinline__ void encode_lane(typename Fmt<T>::U (&x)[VPL], uint32
     {
         U prev = __shfl_up_sync(kFull, x[VPL - 1], 1);
         if (sub == 0) prev = 0;
+        // a set bit in byte lmax (counted from the top) caps the count at lmax
+        const U cap = U(1) << (W - 1 - 8 * lmax);
 #pragma unroll
         for (int m = 0; m < VPL; ++m) {
-            int l = F::clz(x[m] ^ prev) >> 3;
-            l = l < lmax ? l : lmax;
+            int l = F::clz((x[m] ^ prev) | cap) >> 3;
             if (!FULL && m >= nvalid) l = 0;
             codes[m >> 4] += (uint32_t)l << (2 * (m & 15));
             prev = x[m];
