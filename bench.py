@@ -148,6 +148,21 @@ def time_oracle(x_host, eb, max_seconds=12.0):
             "cpu": cpu_model(), "seconds": t_c + t_d}
 
 
+def kernel_sources_sha256():
+    """Hash of the CUDA sources (names and bytes, sorted by path)."""
+    import glob
+    import hashlib
+    csrc = os.path.join(ROOT, "paper_2201_13020_b300", "csrc")
+    files = sorted(glob.glob(os.path.join(csrc, "*.cu")) + glob.glob(os.path.join(csrc, "*.cuh")) +
+                   glob.glob(os.path.join(csrc, "*.h")))
+    h = hashlib.sha256()
+    for f in files:
+        h.update(os.path.basename(f).encode())
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
 def make_field(device, seed):
     from paper_2201_13020_b300 import inputs
     g = inputs.grf_3d(tuple(SHAPE_RUN), -5.0 / 3.0, seed=seed, device=device)
@@ -288,13 +303,14 @@ def main():
     deco_alg = alg_bytes / (statistics.mean(deco_ms) * 1e-3) / 1e9
     dominant = "compress_kernel" if statistics.mean(comp_ms) >= statistics.mean(deco_ms) else "decompress_kernel"
     achieved = comp_alg if dominant == "compress_kernel" else deco_alg
-    # ncu DRAM traffic per launch of the dominant kernel, if a capture of the
-    # current build is recorded
+    # ncu DRAM traffic per launch of the dominant kernel, when the recorded
+    # capture was taken on the current kernel sources (else null)
     traffic = None
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
             tj = json.load(f)
-        traffic = tj.get(dominant)
+        if tj.get("sources_sha256") == kernel_sources_sha256() and args.size == 512:
+            traffic = tj.get(dominant)
     except Exception:
         pass
 
@@ -317,8 +333,10 @@ def main():
             torch.cuda.synchronize()
             if i:
                 times.append(time.perf_counter() - a)
+        # device-to-host per step: the compress result (16 B), the stream
+        # header (64 B), the decompress status (4 B) and the values
         e2e = {"value": in_bytes / statistics.median(times) / 1e9, "unit": "GB/s",
-               "h2d_bytes_per_step": in_bytes, "d2h_bytes_per_step": in_bytes + 16}
+               "h2d_bytes_per_step": in_bytes, "d2h_bytes_per_step": in_bytes + 16 + 64 + 4}
         ok = torch.equal(yh, y.cpu())
         if not ok:
             raise RuntimeError("e2e decode differs from the device-resident decode")
