@@ -12,8 +12,8 @@
  * Method (Sec. IV, Algorithm 1): the array is cut into consecutive blocks of
  * `block` values (128 by default, Sec. V-A.2).  A block whose values all lie
  * within e of mu, the mean of its min and max, is "constant" and stores only
- * mu.  Other blocks are normalised by mu, each value keeps the bits Eq. 3
- * requires, right-shifted by Eq. 4 so they fill whole bytes, and only the bytes
+ * mu.  Other blocks are normalised by mu, each value keeps the bits Eq. 4
+ * requires, right-shifted by Eq. 5 so they fill whole bytes, and only the bytes
  * that differ from the previous value ("mid-bytes") are stored, with a 2-bit
  * code per value counting the identical leading bytes.
  *
@@ -70,7 +70,7 @@ typedef struct {
     uint64_t e_bits;       /* bit pattern of the bound used (f32 in the low 32 bits) */
     uint64_t nonconst;     /* non-constant blocks, raw ones included */
     uint64_t raw;          /* blocks stored verbatim */
-    uint64_t escalated;    /* blocks whose reqBits grew past Eq. 3 to meet e */
+    uint64_t escalated;    /* blocks whose reqBits grew past Eq. 4 to meet e */
     uint64_t total_bytes;  /* stream size */
 } szx_header;
 
@@ -88,7 +88,7 @@ size_t szx_stream_max_bytes(size_t n, szx_dtype dtype, uint32_t block);
 
 /*
  * Compress n values at d_in into the stream at d_out (Algorithm 1 with the
- * Eq. 3 / Eq. 4 byte-aligned packing; Sec. V-B for the GPU design it
+ * Eq. 4 / Eq. 5 byte-aligned packing; Sec. V-B for the GPU design it
  * replaces).  out_capacity must be >= szx_compress_bound(n, dtype, block).
  * On SZX_OK, *out_bytes holds the stream size; the stream occupies
  * d_out[0 .. *out_bytes), and the bytes after it up to out_capacity are

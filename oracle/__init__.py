@@ -112,7 +112,7 @@ def error_bound(eb, dtype):
 
 
 def shift_overhead_bits(arr, eb, block=128):
-    """(bits with the Eq. 4 right shift, bits of an unshifted bit-granular packing)."""
+    """(bits with the Eq. 5 right shift, bits of an unshifted bit-granular packing)."""
     arr = np.ascontiguousarray(arr)
     c = ctypes.c_uint64(0)
     ab = ctypes.c_uint64(0)

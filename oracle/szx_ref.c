@@ -7,7 +7,7 @@
  * value at a time, one block at a time, in the paper's order.
  *
  * ---------------------------------------------------------------------------
- * What the paper fixes (Sec. III-IV, Algorithm 1, Eq. 3, Eq. 4):
+ * What the paper fixes (Sec. III-IV, Algorithm 1, Eq. 4, Eq. 5):
  *   - the data are cut into consecutive 1-D blocks of b values (Alg. 1, loop
  *     over blocks; b = 128 by default, Sec. V-A.2);
  *   - mu_k is the mean of the block's min and max, r_k its variation radius
@@ -15,7 +15,7 @@
  *   - a block is "constant" iff every |d_i - mu_k| <= e; it then stores only
  *     mu_k (Alg. 1, constant branch);
  *   - otherwise values are normalised, v_i = d_i - mu_k, and keep the bits
- *     that Eq. 3 requires; Eq. 4 right-shifts them so the kept bits fill
+ *     that Eq. 4 requires; Eq. 5 right-shifts them so the kept bits fill
  *     whole bytes (Sec. V-A, "Solution C");
  *   - v_i is XORed with v_{i-1}; the number of identical leading bytes
  *     (0..3) is a 2-bit code in the lead-code array, and only the remaining
@@ -33,12 +33,12 @@
  *   R3  The constant test of Alg. 1 is evaluated exactly (no rounding of
  *       d_i - mu) with an error-free transform.
  *   R4  e for f32 is the largest float <= eb (rounded toward zero); for f64
- *       e = eb.  p(x) in Eq. 3 is the unbiased exponent field of x (zero and
+ *       e = eb.  p(x) in Eq. 4 is the unbiased exponent field of x (zero and
  *       subnormals give the field's minimum, 0 - bias).
- *   R5  Eq. 3's clamp "sizeof(type)" is the mantissa width M (23 / 52): R_k
+ *   R5  Eq. 4's clamp "sizeof(type)" is the mantissa width M (23 / 52): R_k
  *       counts mantissa bits, and sign + exponent (1 + E bits) are always
  *       kept, so reqBits = 1 + E + R_k.
- *   R6  Eq. 4 is applied to reqBits (not to R_k alone): s = (8 - reqBits % 8)
+ *   R6  Eq. 5 is applied to reqBits (not to R_k alone): s = (8 - reqBits % 8)
  *       % 8, so that the kept prefix is q = (reqBits + s) / 8 whole bytes.
  *       t_i = (bits(v_i) >> s) masked to its top 8q bits; the decoder uses
  *       v'_i = t_i << s and d'_i = RN(v'_i + mu).
@@ -121,7 +121,7 @@ static int is_finite(const fmt_t *f, uint64_t a)
 
 static int sign_bit(const fmt_t *f, uint64_t a) { return (int)((a >> (f->W - 1)) & 1); }
 
-/* p(x) of Eq. 3: the exponent field minus the bias (reading R4). */
+/* p(x) of Eq. 4: the exponent field minus the bias (reading R4). */
 static int exponent_of(const fmt_t *f, uint64_t a)
 {
     return (int)((a >> f->M) & ((1u << f->E) - 1)) - f->bias;
@@ -334,7 +334,7 @@ static void encode_block(const fmt_t *f, const uint8_t *vals, size_t len,
         }
     }
 
-    /* Eq. 3: required mantissa bits R_k, clamped to [0, M] (R4, R5) */
+    /* Eq. 4: required mantissa bits R_k, clamped to [0, M] (R4, R5) */
     int R = exponent_of(f, r) - exponent_of(f, e);
     if (R < 0) R = 0;
     if (R > f->M) R = f->M;
@@ -344,7 +344,7 @@ static void encode_block(const fmt_t *f, const uint8_t *vals, size_t len,
     for (size_t i = 0; i < len; i++)
         v[i] = sub_rn(f, load_value(f, vals + i * f->w), mu);
 
-    /* Eq. 4 right shift, truncation, and the per-value check (R6, R7) */
+    /* Eq. 5 right shift, truncation, and the per-value check (R6, R7) */
     int req = req0, ok = 0, q = 0, s = 0;
     for (; req <= f->W; req++) {
         s = (8 - req % 8) % 8;
@@ -586,7 +586,7 @@ int szx_ref_decompress(const void *in, size_t in_bytes, void *out, size_t cap,
     return status;
 }
 
-/* ---- Eq. 5 diagnostics ---------------------------------------------------- */
+/* ---- Eq. 6 diagnostics ---------------------------------------------------- */
 
 int szx_ref_shift_overhead_bits(const void *in, size_t n, int dtype, double eb,
                                 uint32_t block, uint64_t *bits_c,

@@ -7,7 +7,7 @@
  * it, and the two share no source, header, table or helper.
  *
  * It is a plain, single-threaded restatement of Algorithm 1 of the paper
- * (Sec. IV), Eq. 3 (required bits), Eq. 4 (byte-alignment right shift) and
+ * (Sec. IV), Eq. 4 (required bits), Eq. 5 (byte-alignment right shift) and
  * the lead-code / mid-byte description that follows Algorithm 1, plus the
  * exact inverse (decompression, Sec. V-B).  It fixes the byte layout of the
  * compressed stream, which the paper leaves open; the layout and every
@@ -59,7 +59,7 @@ int szx_ref_decompress(const void *in, size_t in_bytes, void *out, size_t cap,
 uint64_t szx_ref_error_bound_bits(double eb, int dtype);
 
 /*
- * Diagnostics of Sec. V-A.1 (Eq. 5): over the non-constant, non-raw blocks,
+ * Diagnostics of Sec. V-A.1 (Eq. 6): over the non-constant, non-raw blocks,
  * bits_c = sum over values of (reqBits + s - 8 L_i), the bits stored with the
  * right shift, and bits_ab = sum over values of (reqBits - 8 L0_i), the bits an
  * unshifted, bit-granular packing (Solutions A/B) stores, where L0_i counts

@@ -21,7 +21,7 @@
 // for a look-back or a store.  Per tile:
 //   1. block statistics (Algorithm 1): NaN-propagating min/max per lane,
 //      reduced over the block's lanes with shuffles; mu, r, the exact constant
-//      test, reqBits (Eq. 3), the Eq. 4 shift and truncation.  The per-value
+//      test, reqBits (Eq. 4), the Eq. 5 shift and truncation.  The per-value
 //      bound check is skipped when a block-level bound proves it passes
 //      (see bound_check_needed); otherwise a fast test runs and an exact slow
 //      path re-checks a block that fails it, raising reqBits while a value

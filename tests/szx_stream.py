@@ -2,7 +2,7 @@
 
 It parses every section and rebuilds each block's truncated words t_i from the
 lead codes and mid-byte planes, so the tests can check what each stored field
-means (Eq. 3 reqBits, identical-leading-byte counts, the Eq. 4 shift, the
+means (Eq. 4 reqBits, identical-leading-byte counts, the Eq. 5 shift, the
 byte-count formula) against its definition.  It is written from the format
 description alone and shares no code with the C oracle or the CUDA library.
 Slow: for small streams only.

@@ -216,7 +216,7 @@ def test_error_bound_every_value(dtype, block):
 
 @pytest.mark.parametrize("dtype", [np.float32, np.float64])
 def test_error_bound_power_of_two_bounds(dtype):
-    # e exactly a power of two is the tightest case for Eq. 3: the chop error
+    # e exactly a power of two is the tightest case for Eq. 4: the chop error
     # can approach 2^p(e) = e, so rounding in v = d - mu and d' = v' + mu
     # decides; the per-value check (reading R7) must keep every value within e.
     rng = np.random.default_rng(3)
@@ -315,7 +315,7 @@ def _semantics_case(name, dtype):
         x = x.astype(dtype)
         x[4000:4200] = 5.0  # constant stretch
         return x, 1e-3 * float(x.max() - x.min())
-    # subnormal bound: p(e) of Eq. 3 is the exponent field's minimum, which
+    # subnormal bound: p(e) of Eq. 4 is the exponent field's minimum, which
     # overstates e, so the per-value check must escalate reqBits (reading R7)
     if dtype == np.float32:
         return (x * 1e-36).astype(dtype), 1e-42
@@ -346,7 +346,7 @@ def test_stream_semantics(dtype, case):
         mu = ss.bits_to_float(b.mu_bits, w)
         mn, mx = float(seg.min()), float(seg.max())
         r = float(dtype(dtype(mx) - dtype(mn)) * dtype(0.5))
-        # Eq. 3 (reading R5): reqBits = 1 + E + clamp(p(r) - p(e), 0, M), possibly
+        # Eq. 4 (reading R5): reqBits = 1 + E + clamp(p(r) - p(e), 0, M), possibly
         # escalated (reading R7)
         req0 = 1 + E + min(max(_p(r, w) - _p(e, w), 0), M)
         assert b.req >= req0
@@ -354,7 +354,7 @@ def test_stream_semantics(dtype, case):
             nesc += 1
         sft = (8 - b.req % 8) % 8
         q = (b.req + sft) // 8
-        assert (b.req + sft) % 8 == 0  # Eq. 4: kept bits fill whole bytes
+        assert (b.req + sft) % 8 == 0  # Eq. 5: kept bits fill whole bytes
         # the truncated words keep exactly the top reqBits bits of v = d - mu
         v_bits = [ss.float_bits(dtype(dtype(d) - dtype(mu)), w) for d in seg.tolist()]
         keep = ((1 << W) - 1) ^ ((1 << (W - b.req)) - 1)
@@ -436,7 +436,7 @@ def test_invalid_arguments():
 
 
 def test_shift_overhead_eq5_is_small_on_smooth_data():
-    # Sec. V-A.1: the right shift of Eq. 4 costs some space (the paper reports
+    # Sec. V-A.1: the right shift of Eq. 5 costs some space (the paper reports
     # < 12% of the compressed size on its ~100 real fields).  On this synthetic
     # field it must at least stay positive and well below the at most 7 extra
     # bits a value can carry.
