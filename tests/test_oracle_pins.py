@@ -435,7 +435,7 @@ def test_invalid_arguments():
             oracle.compress(x, 1e-3, block)
 
 
-def test_shift_overhead_eq5_is_small_on_smooth_data():
+def test_shift_overhead_eq6_is_small_on_smooth_data():
     # Sec. V-A.1: the right shift of Eq. 5 costs some space (the paper reports
     # < 12% of the compressed size on its ~100 real fields).  On this synthetic
     # field it must at least stay positive and well below the at most 7 extra
