@@ -191,6 +191,87 @@ szx_status szx_decompress_async(const void *d_in, size_t in_bytes,
                                 size_t out_capacity, uint32_t *d_status,
                                 szx_stream_t stream);
 
+/* ------------------------------------------------------------------------
+ * Batches: many fields in few launches.  The paper has no batch interface; it
+ * is a throughput form of szx_compress / szx_decompress for many independent
+ * arrays (Sec. III's problem applied to each).  Streams and decoded values are
+ * byte-identical to the single-field calls'.
+ *
+ * Life cycle: plan (host only) -> szx_batch_workspace_bytes -> szx_batch_upload
+ * (writes the plan's descriptor tables into the caller's device workspace;
+ * synchronous on `stream`) -> szx_batch_run any number of times (enqueues one
+ * memset and one persistent kernel launch per (dtype, block) group, no host
+ * synchronisation; the same sequence can be captured in a CUDA graph) ->
+ * szx_batch_destroy.  A plan remembers the workspace it was uploaded to;
+ * running it with another one returns SZX_ERR_INVALID.  Buffers named in the
+ * fields must stay valid while the plan is run; runs of one plan must not
+ * overlap in time (they share the workspace).
+ * ------------------------------------------------------------------------ */
+
+/* One field to compress: as the arguments of szx_compress_async. */
+typedef struct {
+    const void *d_in;    /* n values, 16-byte aligned */
+    size_t n;
+    szx_dtype dtype;
+    double eb;           /* absolute bound, finite and > 0 */
+    uint32_t block;      /* power of two in [32, 1024] */
+    void *d_out;         /* the field's stream, 16-byte aligned */
+    size_t out_capacity; /* >= szx_stream_max_bytes(n, dtype, block) */
+} szx_field;
+
+/* One stream to decompress. */
+typedef struct {
+    const void *d_in;    /* the stream, 16-byte aligned */
+    size_t in_bytes;
+    szx_header header;   /* its header (szx_header_read, or the compressing side) */
+    void *d_out;         /* n values, 16-byte aligned */
+    size_t out_capacity; /* >= n * 4 or n * 8 bytes */
+    uint32_t *d_status;  /* device word for the stream's szx_status, or NULL */
+} szx_stream_field;
+
+typedef struct szx_batch_plan szx_batch_plan; /* opaque, host memory */
+
+/* Plan the compression of `count` fields (host only; allocates host memory).
+ * Errors: SZX_ERR_INVALID (a field's arguments, as for szx_compress_async),
+ * SZX_ERR_TOO_SMALL (a field's out_capacity), SZX_ERR_NOMEM. */
+szx_status szx_batch_compress_plan(const szx_field *fields, int count,
+                                   szx_batch_plan **plan);
+
+/* Plan the decompression of `count` streams (host only).  Errors:
+ * SZX_ERR_INVALID, SZX_ERR_CORRUPT (header inconsistent with in_bytes),
+ * SZX_ERR_TOO_SMALL, SZX_ERR_NOMEM.  Every stream is still checked on the
+ * device; its status word receives SZX_ERR_CORRUPT if it is malformed. */
+szx_status szx_batch_decompress_plan(const szx_stream_field *streams, int count,
+                                     szx_batch_plan **plan);
+
+/* Device workspace bytes the plan needs (0 for a NULL plan). */
+size_t szx_batch_workspace_bytes(const szx_batch_plan *plan);
+
+/* Write the plan's tables into d_ws (device, 256-byte aligned, at least
+ * szx_batch_workspace_bytes).  d_results (compression plans): device array of
+ * 2 * count uint64_t receiving {stream bytes, szx_status} per field, in the
+ * caller's field order, after each run; may be NULL (the sizes are also in
+ * each stream's header).  Synchronous on `stream`. */
+szx_status szx_batch_upload(szx_batch_plan *plan, void *d_ws, size_t ws_bytes,
+                            uint64_t *d_results, szx_stream_t stream);
+
+/* Enqueue one run of the plan on `stream`. */
+szx_status szx_batch_run(const szx_batch_plan *plan, void *d_ws,
+                         szx_stream_t stream);
+
+/* Choose, per group, how many CTAs of the kernel share an SM (1 or 2, where
+ * two fit) by timing runs of that group on `stream`; the choice is kept in the
+ * plan.  Runs the plan's own work, so it overwrites the outputs (with the same
+ * bytes).  Synchronous. */
+szx_status szx_batch_autotune(szx_batch_plan *plan, void *d_ws,
+                              szx_stream_t stream);
+
+/* Number of groups; writes up to `capacity` CTAs-per-SM choices (0 = as many
+ * as fit) into ctas_per_sm. */
+int szx_batch_groups(const szx_batch_plan *plan, int *ctas_per_sm, int capacity);
+
+void szx_batch_destroy(szx_batch_plan *plan);
+
 /* Human-readable name of a status code. */
 const char *szx_status_string(szx_status s);
 

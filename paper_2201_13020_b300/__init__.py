@@ -9,10 +9,11 @@ and streams; the codec itself runs in the library's sm_103a CUDA kernels.
 """
 import ctypes
 
-from ._lib import SZX_F32, SZX_F64, STATUS, SzxHeader, lib
+from ._lib import SZX_F32, SZX_F64, STATUS, SzxField, SzxHeader, SzxStreamField, lib
 
 __all__ = ["compress", "decompress", "compress_async", "decompress_async", "compress_bound",
-           "stream_max_bytes", "header", "SzxError", "SZX_F32", "SZX_F64"]
+           "stream_max_bytes", "header", "Batch", "batch_compress", "batch_decompress", "SzxError", "SZX_F32",
+           "SZX_F64"]
 
 
 class SzxError(RuntimeError):
@@ -119,3 +120,102 @@ def decompress_async(buf, h, out, status=None, stream=None):
                                       ctypes.c_void_p(out.data_ptr()), out.numel() * out.element_size(),
                                       ctypes.c_void_p(status.data_ptr() if status is not None else 0),
                                       _stream_handle(stream)), "szx_decompress_async")
+
+
+class Batch:
+    """A planned batch (see szx_batch_* in include/szx.h) with its device workspace.
+
+    run() enqueues one run (one memset and one persistent launch per
+    (dtype, block) group) on the stream; it can be captured in a CUDA graph.
+    """
+
+    def __init__(self, plan, ws, keep):
+        self._plan = plan
+        self.ws = ws
+        self._keep = keep  # tensors the plan points to
+
+    def run(self, stream=None):
+        _check(lib().szx_batch_run(self._plan, ctypes.c_void_p(self.ws.data_ptr()), _stream_handle(stream)),
+               "szx_batch_run")
+
+    def autotune(self, stream=None):
+        _check(lib().szx_batch_autotune(self._plan, ctypes.c_void_p(self.ws.data_ptr()), _stream_handle(stream)),
+               "szx_batch_autotune")
+        return self.groups()
+
+    def groups(self):
+        buf = (ctypes.c_int * 64)()
+        n = lib().szx_batch_groups(self._plan, buf, 64)
+        return [buf[i] for i in range(min(n, 64))]
+
+    def close(self):
+        if self._plan:
+            lib().szx_batch_destroy(self._plan)
+            self._plan = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _upload(plan, device, results, stream):
+    torch = _torch()
+    nbytes = lib().szx_batch_workspace_bytes(plan)
+    ws = torch.empty(max(nbytes, 256) + 256, dtype=torch.uint8, device=device)
+    off = (-ws.data_ptr()) % 256
+    ws = ws[off:off + max(nbytes, 256)]
+    st = lib().szx_batch_upload(plan, ctypes.c_void_p(ws.data_ptr()), ws.numel(),
+                                ctypes.c_void_p(results.data_ptr() if results is not None else 0),
+                                _stream_handle(stream))
+    if st != 0:
+        lib().szx_batch_destroy(plan)
+        raise SzxError(st, "szx_batch_upload")
+    return ws
+
+
+def batch_compress(xs, ebs, blocks=128, outs=None, stream=None):
+    """Plan and upload the compression of CUDA tensors xs (one bound each).
+
+    Returns (batch, outs, results): outs are uint8 buffers of
+    stream_max_bytes each; after batch.run() and a synchronisation, field i's
+    stream is outs[i][:results[2*i]] and results[2*i+1] its status.
+    """
+    torch = _torch()
+    k = len(xs)
+    if isinstance(blocks, int):
+        blocks = [blocks] * k
+    if outs is None:
+        outs = [torch.empty(stream_max_bytes(x.numel(), _dtype_code(x), bk), dtype=torch.uint8, device=x.device)
+                for x, bk in zip(xs, blocks)]
+    arr = (SzxField * k)()
+    for i, (x, eb, bk, o) in enumerate(zip(xs, ebs, blocks, outs)):
+        if not x.is_cuda or not x.is_contiguous():
+            raise ValueError("fields must be contiguous CUDA tensors")
+        arr[i] = SzxField(x.data_ptr(), x.numel(), _dtype_code(x), float(eb), bk, o.data_ptr(), o.numel())
+    plan = ctypes.c_void_p(0)
+    _check(lib().szx_batch_compress_plan(arr, k, ctypes.byref(plan)), "szx_batch_compress_plan")
+    results = torch.zeros(2 * k, dtype=torch.int64, device=xs[0].device)
+    ws = _upload(plan, xs[0].device, results, stream)
+    return Batch(plan, ws, (list(xs), list(outs), results)), outs, results
+
+
+def batch_decompress(bufs, headers, outs=None, statuses=None, stream=None):
+    """Plan and upload the decompression of streams (CUDA uint8 tensors) whose
+    headers are known.  Returns (batch, outs, statuses)."""
+    torch = _torch()
+    k = len(bufs)
+    if outs is None:
+        outs = [torch.empty(h.n, dtype=torch.float32 if h.dtype == SZX_F32 else torch.float64, device=b.device)
+                for b, h in zip(bufs, headers)]
+    if statuses is None:
+        statuses = torch.zeros(k, dtype=torch.int32, device=bufs[0].device)
+    arr = (SzxStreamField * k)()
+    for i, (b, h, o) in enumerate(zip(bufs, headers, outs)):
+        arr[i] = SzxStreamField(b.data_ptr(), b.numel(), h, o.data_ptr(), o.numel() * o.element_size(),
+                                statuses.data_ptr() + 4 * i)
+    plan = ctypes.c_void_p(0)
+    _check(lib().szx_batch_decompress_plan(arr, k, ctypes.byref(plan)), "szx_batch_decompress_plan")
+    ws = _upload(plan, bufs[0].device, None, stream)
+    return Batch(plan, ws, (list(bufs), list(outs), statuses)), outs, statuses

@@ -21,6 +21,16 @@ class SzxHeader(ctypes.Structure):
                 ("raw", ctypes.c_uint64), ("escalated", ctypes.c_uint64), ("total_bytes", ctypes.c_uint64)]
 
 
+class SzxField(ctypes.Structure):
+    _fields_ = [("d_in", ctypes.c_void_p), ("n", ctypes.c_size_t), ("dtype", ctypes.c_int), ("eb", ctypes.c_double),
+                ("block", ctypes.c_uint32), ("d_out", ctypes.c_void_p), ("out_capacity", ctypes.c_size_t)]
+
+
+class SzxStreamField(ctypes.Structure):
+    _fields_ = [("d_in", ctypes.c_void_p), ("in_bytes", ctypes.c_size_t), ("header", SzxHeader),
+                ("d_out", ctypes.c_void_p), ("out_capacity", ctypes.c_size_t), ("d_status", ctypes.c_void_p)]
+
+
 _lib = None
 
 
@@ -51,6 +61,23 @@ def lib():
     L.szx_decompress.argtypes = [vp, sz, vp, sz, ctypes.POINTER(sz), ctypes.POINTER(i), vp]
     L.szx_decompress_async.restype = i
     L.szx_decompress_async.argtypes = [vp, sz, ctypes.POINTER(SzxHeader), vp, sz, vp, vp]
+    pp = ctypes.POINTER(ctypes.c_void_p)
+    L.szx_batch_compress_plan.restype = i
+    L.szx_batch_compress_plan.argtypes = [ctypes.POINTER(SzxField), i, pp]
+    L.szx_batch_decompress_plan.restype = i
+    L.szx_batch_decompress_plan.argtypes = [ctypes.POINTER(SzxStreamField), i, pp]
+    L.szx_batch_workspace_bytes.restype = sz
+    L.szx_batch_workspace_bytes.argtypes = [vp]
+    L.szx_batch_upload.restype = i
+    L.szx_batch_upload.argtypes = [vp, vp, sz, vp, vp]
+    L.szx_batch_run.restype = i
+    L.szx_batch_run.argtypes = [vp, vp, vp]
+    L.szx_batch_autotune.restype = i
+    L.szx_batch_autotune.argtypes = [vp, vp, vp]
+    L.szx_batch_groups.restype = i
+    L.szx_batch_groups.argtypes = [vp, ctypes.POINTER(i), i]
+    L.szx_batch_destroy.restype = None
+    L.szx_batch_destroy.argtypes = [vp]
     L.szx_status_string.restype = ctypes.c_char_p
     L.szx_status_string.argtypes = [i]
     L.szx_version.restype = ctypes.c_char_p
@@ -60,4 +87,6 @@ def lib():
 
 
 EXPORTED = ["szx_compress_bound", "szx_stream_max_bytes", "szx_compress", "szx_compress_async",
-            "szx_compress_static_async", "szx_header_read", "szx_decompress", "szx_decompress_async", "szx_status_string", "szx_version"]
+            "szx_compress_static_async", "szx_batch_compress_plan", "szx_batch_decompress_plan",
+            "szx_batch_workspace_bytes", "szx_batch_upload", "szx_batch_run", "szx_batch_autotune", "szx_batch_groups",
+            "szx_batch_destroy", "szx_header_read", "szx_decompress", "szx_decompress_async", "szx_status_string", "szx_version"]

@@ -57,20 +57,35 @@
 
 namespace szx {
 
-struct CompressArgs {
-    const uint8_t *in;
-    uint8_t *out;
-    Workspace *ws;
-    uint64_t *lookback;
-    uint64_t *d_result;
-    Geometry g;
-    uint64_t e_bits;
-    uint64_t rows_full;    // 128-byte input rows fully inside the input
+struct CompressLaunch {
+    const CField *fields;  // device table of nfields fields, or null: the single field
+    uint32_t nfields;
+    uint64_t total_tiles;
+    uint32_t *ticket;  // launch counters, zeroed before the launch
+    uint32_t *done;
+    uint32_t *err;     // launch-wide kErr* bits (folded into every field's status)
     uint64_t lookback_ns;  // wall-time limit of the look-back wait
     uint64_t copy_ns;      // wall-time limit of a tile copy wait
-    uint32_t dtype;
-    uint32_t use_tma;
 };
+
+template <bool BATCH>
+__device__ __forceinline__ const CField *field_ptr(const CField &one, const CompressLaunch &lc, uint32_t f) {
+    if constexpr (BATCH) return lc.fields + f;
+    else return &one;  // the kernel parameter itself (param space)
+}
+
+// The field holding global tile t: the last one whose first tile is <= t.
+template <bool BATCH>
+__device__ __forceinline__ uint32_t field_of(const CompressLaunch &lc, uint64_t t) {
+    if constexpr (!BATCH) return 0;
+    uint32_t lo = 0, hi = lc.nfields - 1;
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi + 1) / 2;
+        if (lc.fields[mid].tile0 <= t) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
 
 // ---------------------------------------------------------------------------
 // compaction table: for plane j in 0..2 and the 2-bit codes of four values
@@ -414,9 +429,9 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
 
 // ---------------------------------------------------------------------------
 
-template <typename T, int LPB, int VPL>
+template <typename T, int LPB, int VPL, bool BATCH>
 __global__ void __launch_bounds__(kCThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
-    compress_kernel(const __grid_constant__ CUtensorMap tmap, CompressArgs a) {
+    compress_kernel(const __grid_constant__ CField one, const __grid_constant__ CompressLaunch lc) {
     using F = Fmt<T>;
     using U = typename F::U;
     constexpr int w = F::w;
@@ -430,13 +445,14 @@ __global__ void __launch_bounds__(kCThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
     // full: tile copied in; encoded: every consumer warp has its blocks'
     // totals in place; ready: record written; empty: record stored
     __shared__ __align__(8) uint64_t full[kStages], encoded[kStages], ready[kStages], empty[kStages];
-    __shared__ uint32_t st_tile[kStages], st_nn[kStages], st_nraw[kStages], st_nesc[kStages], st_rec[kStages],
-        st_fail[kStages];
+    // per stage: the field and its local tile (0xFFFFFFFF: no more tiles)
+    __shared__ uint32_t st_field[kStages], st_tile[kStages], st_nn[kStages], st_nraw[kStages], st_nesc[kStages],
+        st_rec[kStages], st_fail[kStages];
 
     // the 128-byte swizzle of the tensor copy needs 1024-byte aligned buffers
     uint8_t *smem = smem_raw + ((1024u - (smem_addr(smem_raw) & 1023u)) & 1023u);
-    const Geometry &g = a.g;
-    const uint32_t b = g.b, G = g.G;
+    constexpr uint32_t b = (uint32_t)(LPB * VPL);
+    constexpr uint32_t G = tile_blocks(b, (uint32_t)w);
     const CSmem L = compress_smem(G, b, w);
     uint32_t *lut = reinterpret_cast<uint32_t *>(smem + L.lut);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -456,6 +472,7 @@ __global__ void __launch_bounds__(kCThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
         fence_mbar_init();
         for (int i = 0; i < kStages; ++i) {
             st_tile[i] = 0xFFFFFFFFu;
+            st_field[i] = 0;
             st_nn[i] = st_nraw[i] = st_nesc[i] = st_rec[i] = st_fail[i] = 0;
         }
     }
@@ -470,16 +487,22 @@ __global__ void __launch_bounds__(kCThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
         for (uint32_t it = 0;; ++it) {
             const int st = (int)(it % kStages);
             const uint32_t k = it / kStages;
-            if (it >= kStages && !mbar_wait_bounded(&empty[st], (k - 1) & 1u, a.lookback_ns + a.copy_ns)) {
-                atomicOr(&a.ws->err, kErrTimeout);
+            if (it >= kStages && !mbar_wait_bounded(&empty[st], (k - 1) & 1u, lc.lookback_ns + lc.copy_ns)) {
+                atomicOr(lc.err, kErrTimeout);
                 break;
             }
-            const uint32_t t = atomicAdd(&a.ws->ticket, 1u);
-            st_tile[st] = t;
+            // a ticket is a tile of the launch's global list; find its field
+            const uint64_t t = atomicAdd(lc.ticket, 1u);
+            const bool more = t < lc.total_tiles;
+            const uint32_t f = more ? field_of<BATCH>(lc, t) : 0u;
+            const CField *F = field_ptr<BATCH>(one, lc, f);
+            const uint32_t tile = more ? (uint32_t)(t - F->tile0) : 0xFFFFFFFFu;
+            st_field[st] = f;
+            st_tile[st] = tile;
             st_fail[st] = 0;
             st_nesc[st] = 0;
-            const uint64_t row0 = (uint64_t)t * 256 * RPL;
-            if (t < g.ntiles && a.use_tma && row0 < a.rows_full) {
+            const uint64_t row0 = (uint64_t)tile * 256 * RPL;
+            if (more && F->use_tma && row0 < F->rows_full) {
                 mbar_arrive_expect_tx(&full[st], 256u * 128u * RPL);
 #pragma unroll
                 for (int i = 0; i < RPL; ++i) {
@@ -488,7 +511,7 @@ __global__ void __launch_bounds__(kCThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
                     asm volatile(
                         "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, "
                         "{%2, %3}], [%4];" ::"r"(dst),
-                        "l"(reinterpret_cast<uint64_t>(&tmap)), "r"(0), "r"(y), "r"(smem_addr(&full[st]))
+                        "l"(reinterpret_cast<uint64_t>(&F->tmap)), "r"(0), "r"(y), "r"(smem_addr(&full[st]))
                         : "memory");
                 }
                 copy_last |= 1u << st;
@@ -498,26 +521,28 @@ __global__ void __launch_bounds__(kCThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
                 mbar_arrive(&full[st]);
                 copy_last &= ~(1u << st);
             }
-            if (t >= g.ntiles) break;
+            if (!more) break;
         }
         // do not leave while a copy may still be writing into shared memory
         for (int st = 0; st < kStages; ++st)
-            if ((copy_last >> st) & 1u) mbar_wait_bounded(&full[st], (copy_par >> st) & 1u, a.copy_ns);
+            if ((copy_last >> st) & 1u) mbar_wait_bounded(&full[st], (copy_par >> st) & 1u, lc.copy_ns);
         return;
     }
 
     if (warp == kStorerWarp) {
         // ---- storer: look-back, index entry, record store --------------------
-        unsigned long long c_nn = 0, c_raw = 0, c_esc = 0;  // this CTA's counts
         for (uint32_t it = 0;; ++it) {
             const int st = (int)(it % kStages);
             const uint32_t k = it / kStages;
-            if (!mbar_wait_bounded(&ready[st], k & 1u, a.lookback_ns + 4 * a.copy_ns)) {
-                if (lane == 0) atomicOr(&a.ws->err, kErrTimeout);
+            if (!mbar_wait_bounded(&ready[st], k & 1u, lc.lookback_ns + 4 * lc.copy_ns)) {
+                if (lane == 0) atomicOr(lc.err, kErrTimeout);
                 break;
             }
             const uint32_t tile = st_tile[st];
-            if (tile >= g.ntiles) break;
+            if (tile == 0xFFFFFFFFu) break;
+            const CField *F = field_ptr<BATCH>(one, lc, st_field[st]);
+            const Geometry &g = F->g;
+            uint64_t *lookback = F->lookback;
             const uint32_t rec_bytes = st_rec[st];
             // warp-parallel decoupled look-back: 32 predecessors per probe,
             // lane i looking at tile - 1 - i; stop at the nearest inclusive
@@ -529,7 +554,7 @@ __global__ void __launch_bounds__(kCThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
                 int64_t base = (int64_t)tile - 1;
                 while (base >= 0) {
                     const int64_t j = base - lane;
-                    const uint64_t wv = j >= 0 ? ld_relaxed_u64(&a.lookback[j]) : kFlagPrefix;
+                    const uint64_t wv = j >= 0 ? ld_relaxed_u64(&lookback[j]) : kFlagPrefix;
                     const uint64_t flag = wv & ~kValueMask;
                     const uint32_t pre = __ballot_sync(kFull, flag == kFlagPrefix);
                     const uint32_t inv = __ballot_sync(kFull, flag == 0);
@@ -537,7 +562,7 @@ __global__ void __launch_bounds__(kCThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
                     const uint32_t need = first_p >= 31 ? kFull : ((2u << first_p) - 1u);
                     if (inv & need) {
                         // one lane's clock decides, so the warp stays converged
-                        if (__shfl_sync(kFull, (int)(globaltimer_ns() - t0 > a.lookback_ns), 0)) {
+                        if (__shfl_sync(kFull, (int)(globaltimer_ns() - t0 > lc.lookback_ns), 0)) {
                             timed_out = true;
                             break;
                         }
@@ -553,72 +578,80 @@ __global__ void __launch_bounds__(kCThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
                 }
             }
             if (lane == 0) {
-                st_relaxed_u64(&a.lookback[tile], kFlagPrefix | (excl + rec_bytes));
+                st_relaxed_u64(&lookback[tile], kFlagPrefix | (excl + rec_bytes));
+                Workspace *ws = F->ws;
                 if (st_fail[st]) {
-                    atomicOr(&a.ws->err, kErrTmaTimeout);
-                    atomicAdd(&a.ws->tma_timeouts, 1u);
-                    atomicCAS(&a.ws->first_tma_tile, 0u, tile + 1);
+                    atomicOr(&ws->err, kErrTmaTimeout);
+                    atomicAdd(&ws->tma_timeouts, 1u);
+                    atomicCAS(&ws->first_tma_tile, 0u, tile + 1);
                 }
                 if (timed_out) {
-                    atomicOr(&a.ws->err, kErrTimeout);
-                    atomicAdd(&a.ws->lookback_timeouts, 1ull);
-                    atomicCAS(&a.ws->first_lb_tile, 0u, tile + 1);
+                    atomicOr(&ws->err, kErrTimeout);
+                    atomicAdd(&ws->lookback_timeouts, 1ull);
+                    atomicCAS(&ws->first_lb_tile, 0u, tile + 1);
                 }
-                uint64_t *idx = reinterpret_cast<uint64_t *>(a.out + g.off_index);
+                uint8_t *out = F->out;
+                uint64_t *idx = reinterpret_cast<uint64_t *>(out + g.off_index);
                 idx[tile] = excl;
                 if (tile == g.ntiles - 1) {
                     idx[g.ntiles] = excl + rec_bytes;
                     const uint64_t state_end = g.off_state + (g.nb + 7) / 8;
-                    for (uint64_t i = state_end; i < g.off_mu; ++i) a.out[i] = 0;
-                    for (uint64_t i = g.off_mu + g.nb * w; i < g.off_index; ++i) a.out[i] = 0;
-                    for (uint64_t i = g.off_index + 8 * (g.ntiles + 1); i < g.off_rec; ++i) a.out[i] = 0;
+                    for (uint64_t i = state_end; i < g.off_mu; ++i) out[i] = 0;
+                    for (uint64_t i = g.off_mu + g.nb * w; i < g.off_index; ++i) out[i] = 0;
+                    for (uint64_t i = g.off_index + 8 * (g.ntiles + 1); i < g.off_rec; ++i) out[i] = 0;
                 }
                 if (rec_bytes) {
                     fence_proxy_async_smem();
-                    bulk_s2g(a.out + g.off_rec + excl, smem + st * L.buf_stride, rec_bytes);
+                    bulk_s2g(out + g.off_rec + excl, smem + st * L.buf_stride, rec_bytes);
                     bulk_commit();
                 }
-                c_nn += st_nn[st];
-                c_raw += st_nraw[st];
-                c_esc += st_nesc[st];
+                // the field's counts (the header is written once every CTA is done)
+                if (st_nn[st]) atomicAdd(&ws->nn, (unsigned long long)st_nn[st]);
+                if (st_nraw[st]) atomicAdd(&ws->nraw, (unsigned long long)st_nraw[st]);
+                if (st_nesc[st]) atomicAdd(&ws->nesc, (unsigned long long)st_nesc[st]);
                 // the buffer is free once the store has read it
                 if (rec_bytes) bulk_wait_read_all();
                 mbar_arrive(&empty[st]);
             }
             __syncwarp();
         }
+        // the last CTA to get here writes every field's header and result
+        uint32_t last = 0;
         if (lane == 0) {
-            // this CTA's counts; the last CTA to get here writes the header
-            atomicAdd(&a.ws->nn, c_nn);
-            atomicAdd(&a.ws->nraw, c_raw);
-            atomicAdd(&a.ws->nesc, c_esc);
             __threadfence();
-            const uint32_t done = atomicAdd(&a.ws->done, 1u);
-            if (done == gridDim.x - 1) {
-                __threadfence();
-                volatile Workspace *ws = a.ws;
-                const uint64_t rec_total = reinterpret_cast<volatile uint64_t *>(a.out + g.off_index)[g.ntiles];
+            last = atomicAdd(lc.done, 1u) == gridDim.x - 1 ? 1u : 0u;
+            if (last) __threadfence();
+        }
+        last = __shfl_sync(kFull, last, 0);
+        if (last) {
+            const uint32_t launch_err = *reinterpret_cast<volatile uint32_t *>(lc.err);
+            for (uint32_t f = lane; f < lc.nfields; f += 32) {
+                const CField *F = field_ptr<BATCH>(one, lc, f);
+                const Geometry &g = F->g;
+                volatile Workspace *ws = F->ws;
+                const uint64_t rec_total = reinterpret_cast<volatile uint64_t *>(F->out + g.off_index)[g.ntiles];
                 const uint64_t total = g.off_rec + rec_total;
-                uint32_t *h32 = reinterpret_cast<uint32_t *>(a.out);
-                uint64_t *h64 = reinterpret_cast<uint64_t *>(a.out);
+                uint32_t *h32 = reinterpret_cast<uint32_t *>(F->out);
+                uint64_t *h64 = reinterpret_cast<uint64_t *>(F->out);
                 h32[0] = kMagic;
-                h32[1] = kVersion | (a.dtype << 8);
+                h32[1] = kVersion | (F->dtype << 8);
                 h32[2] = b;
                 h32[3] = G;
                 h64[2] = g.n;
-                h64[3] = a.e_bits;
+                h64[3] = F->e_bits;
                 h64[4] = ws->nn;
                 h64[5] = ws->nraw;
                 h64[6] = ws->nesc;
                 h64[7] = total;
-                const uint64_t status = (ws->err & (kErrTimeout | kErrTmaTimeout)) ? 6ull
-                                        : (ws->err & kErrInternal)                 ? 5ull
-                                                                                   : 0ull;
+                const uint32_t err = ws->err | launch_err;
+                const uint64_t status = (err & (kErrTimeout | kErrTmaTimeout)) ? 6ull
+                                        : (err & kErrInternal)                 ? 5ull
+                                                                               : 0ull;
                 ws->result[0] = total;
                 ws->result[1] = status;
-                if (a.d_result) {
-                    a.d_result[0] = total;
-                    a.d_result[1] = status;
+                if (F->d_result) {
+                    F->d_result[0] = total;
+                    F->d_result[1] = status;
                 }
             }
         }
@@ -628,23 +661,25 @@ __global__ void __launch_bounds__(kCThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
     // ---- consumers (warps 0..7): encode tiles into records ------------------
     // The warps of a CTA meet once per tile (the `encoded` mbarrier, after
     // which the tile's totals are known); every wait is bounded.
-    const T e = F::from((U)a.e_bits);
     for (uint32_t it = 0;; ++it) {
         const int st = (int)(it % kStages);
         const uint32_t k = it / kStages;
-        const bool waited = mbar_wait_bounded(&full[st], k & 1u, a.copy_ns);
+        const bool waited = mbar_wait_bounded(&full[st], k & 1u, lc.copy_ns);
         const uint32_t tile = waited ? st_tile[st] : 0xFFFFFFFFu;
-        if (tile >= g.ntiles) {
+        if (tile == 0xFFFFFFFFu) {
             // the producer is done (or the copy never arrived): hand the stage
             // to the storer, which stops on it, and stop
             if (!waited && lane == 0) {
-                atomicOr(&a.ws->err, kErrTmaTimeout);
+                atomicOr(lc.err, kErrTmaTimeout);
                 st_tile[st] = 0xFFFFFFFFu;
             }
             __syncwarp();
             if (lane == 0) mbar_arrive(&ready[st]);
             break;
         }
+        const CField *Fd = field_ptr<BATCH>(one, lc, st_field[st]);
+        const Geometry &g = Fd->g;
+        const T e = F::from((U)Fd->e_bits);
         uint8_t *buf = smem + st * L.buf_stride;
         uint8_t *meta = smem + (L.meta0 + st * L.meta_stride);
         uint8_t *sm_kind = meta + L.m_kind;
@@ -652,7 +687,8 @@ __global__ void __launch_bounds__(kCThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
         const uint64_t k0 = (uint64_t)tile * G;
         const uint32_t Gt = (uint32_t)min_u64(G, g.nb - k0);
         const uint64_t row0 = (uint64_t)tile * 256 * RPL;
-        const bool tma = a.use_tma && row0 < a.rows_full;
+        const uint64_t rows_full = Fd->rows_full;
+        const bool tma = Fd->use_tma && row0 < rows_full;
 
         // ---- 1. block statistics and encoding (registers) -------------------
         const int sub = lane % LPB;
@@ -665,7 +701,7 @@ __global__ void __launch_bounds__(kCThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
         const bool full_lane = nvalid == VPL;
         const uint32_t lane_row0 = (uint32_t)((warp * 32 + lane) * RPL);
         // the lane's values in global memory (read only below nvalid)
-        const U *src = reinterpret_cast<const U *>(a.in) + kg * b + sub * VPL;
+        const U *src = reinterpret_cast<const U *>(Fd->in) + kg * b + sub * VPL;
 
         // rows the tensor copy brought in come from shared memory; the
         // input's ragged end (or every row without the tensor copy) from global
@@ -674,7 +710,7 @@ __global__ void __launch_bounds__(kCThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
 #pragma unroll
         for (int rr = 0; rr < RPL; ++rr) {
             const uint32_t rowi = lane_row0 + rr;
-            if (tma && row0 + rowi < a.rows_full) {
+            if (tma && row0 + rowi < rows_full) {
 #pragma unroll
                 for (int c = 0; c < 8; ++c) {
                     const uint4 v = *reinterpret_cast<const uint4 *>(buf + (rowi << 7) + ((c ^ (rowi & 7u)) << 4));
@@ -707,15 +743,15 @@ __global__ void __launch_bounds__(kCThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
         uint32_t mk_lane;
         if (__all_sync(kFull, full_lane)) {
             encode_lane<T, LPB, VPL, true>(x, codes, kind, req, req0, mu, mk_lane, src, nvalid, exists, e,
-                                           a.e_bits, a.ws, tile);
+                                           Fd->e_bits, Fd->ws, tile);
         } else {
             encode_lane<T, LPB, VPL, false>(x, codes, kind, req, req0, mu, mk_lane, src, nvalid, exists, e,
-                                            a.e_bits, a.ws, tile);
+                                            Fd->e_bits, Fd->ws, tile);
         }
         const bool lead = exists && sub == 0;  // the block's first lane
         if (lead) {
             sm_kind[blk] = (uint8_t)kind;
-            reinterpret_cast<U *>(a.out + g.off_mu)[kg] = kind == kRaw ? U(0) : F::bits(mu);
+            reinterpret_cast<U *>(Fd->out + g.off_mu)[kg] = kind == kRaw ? U(0) : F::bits(mu);
         }
         // the warp's totals; its blocks are consecutive, so an exclusive scan
         // over lanes gives each block's mid-byte offset inside the warp's share
@@ -727,10 +763,10 @@ __global__ void __launch_bounds__(kCThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
         if (lane == 0) sm_w[warp] = make_uint4(__popc(nonc_bal), mid_w, __popc(raw_bal), __popc(esc_bal));
         __syncwarp();
         if (lane == 0) mbar_arrive(&encoded[st]);
-        if (!mbar_wait_bounded(&encoded[st], k & 1u, a.lookback_ns + a.copy_ns)) {
+        if (!mbar_wait_bounded(&encoded[st], k & 1u, lc.lookback_ns + lc.copy_ns)) {
             // a warp of this CTA never finished the tile: give up
             if (lane == 0) {
-                atomicOr(&a.ws->err, kErrTimeout);
+                atomicOr(lc.err, kErrTimeout);
                 st_tile[st] = 0xFFFFFFFFu;
                 mbar_arrive(&ready[st]);
             }
@@ -758,10 +794,10 @@ __global__ void __launch_bounds__(kCThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
                 st_nraw[st] = raw_t;
                 st_nesc[st] = esc_t;
                 st_rec[st] = rec_bytes;
-                st_relaxed_u64(&a.lookback[tile], kFlagAgg | rec_bytes);
+                st_relaxed_u64(&Fd->lookback[tile], kFlagAgg | rec_bytes);
             }
             // state bits: bit i of byte j is set when block 8j + i is not constant
-            uint8_t *state = a.out + g.off_state + (size_t)k0 / 8;
+            uint8_t *state = Fd->out + g.off_state + (size_t)k0 / 8;
             for (uint32_t j = lane; j < (Gt + 7) / 8; j += 32) {
                 uint32_t byte = 0;
 #pragma unroll
@@ -772,7 +808,7 @@ __global__ void __launch_bounds__(kCThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
                 state[j] = (uint8_t)byte;
             }
         }
-        if (SZX_CHECKS && rec_bytes > record_max_bytes(G, b, w) && tid == 0) report_bad(a.ws, tile, 2);
+        if (SZX_CHECKS && rec_bytes > record_max_bytes(G, b, w) && tid == 0) report_bad(Fd->ws, tile, 2);
         const uint32_t rank = nn_before + __popc(nonc_bal & ((1u << (lane & ~(LPB - 1))) - 1u));
         const uint32_t mk_blk_excl = __shfl_sync(kFull, lane_excl, lane & ~(LPB - 1));
 
@@ -809,7 +845,7 @@ __global__ void __launch_bounds__(kCThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
         // that it lands inside the record
         auto put = [&](uint32_t p, uint32_t run, uint32_t c) {
             if (SZX_CHECKS && (p + 8 > L.buf_bytes || p + c > rec_bytes)) {
-                report_bad(a.ws, tile, 1);
+                report_bad(Fd->ws, tile, 1);
                 return;
             }
             or_bytes(words, p, run, c);
@@ -823,7 +859,7 @@ __global__ void __launch_bounds__(kCThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
             }
             if (kind == kRaw) {
                 // verbatim input bytes, value-major
-                const U *src = reinterpret_cast<const U *>(a.in) + kg * b + sub * VPL;
+                const U *src = reinterpret_cast<const U *>(Fd->in) + kg * b + sub * VPL;
                 for (int m = 0; m < nvalid; ++m) {
                     const U v = src[m];
                     const uint32_t p = mbase + (uint32_t)(sub * VPL + m) * w;
@@ -832,7 +868,7 @@ __global__ void __launch_bounds__(kCThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
                 }
             } else {
                 // lead codes: this lane's values are bytes [sub*VPL/4, (sub+1)*VPL/4)
-                if (SZX_CHECKS && (rank + 1) * (b / 4) > nn_t * (b / 4)) report_bad(a.ws, tile, 6);
+                if (SZX_CHECKS && (rank + 1) * (b / 4) > nn_t * (b / 4)) report_bad(Fd->ws, tile, 6);
                 uint8_t *lead = buf + rank * (b / 4) + sub * (VPL / 4);
                 if constexpr (NCODE == 2) {
                     *reinterpret_cast<uint2 *>(lead) = make_uint2(codes[0], codes[1]);
@@ -916,9 +952,10 @@ __global__ void __launch_bounds__(kCThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
 namespace {
 
 template <typename T, int LPB, int VPL>
-cudaError_t launch_t(const CUtensorMap &tm, const CompressArgs &a, cudaStream_t stream) {
-    const CSmem L = compress_smem(a.g.G, a.g.b, Fmt<T>::w);
-    auto kern = compress_kernel<T, LPB, VPL>;
+cudaError_t launch_t(const CField &one, const CompressLaunch &lc, int ctas_per_sm, cudaStream_t stream) {
+    constexpr uint32_t b = (uint32_t)(LPB * VPL), w = (uint32_t)Fmt<T>::w;
+    const CSmem L = compress_smem(tile_blocks(b, w), b, w);
+    auto kern = lc.fields ? compress_kernel<T, LPB, VPL, true> : compress_kernel<T, LPB, VPL, false>;
     cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total);
     if (err != cudaSuccess) return err;
     int dev = 0, sms = 0, per_sm = 0;
@@ -927,9 +964,34 @@ cudaError_t launch_t(const CUtensorMap &tm, const CompressArgs &a, cudaStream_t 
     if ((err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kCThreads, L.total)) != cudaSuccess)
         return err;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
-    const uint64_t grid = min_u64(a.g.ntiles, (uint64_t)sms * per_sm);
-    kern<<<(unsigned)grid, kCThreads, L.total, stream>>>(tm, a);
+    if (ctas_per_sm > 0 && ctas_per_sm < per_sm) per_sm = ctas_per_sm;
+    const uint64_t grid = min_u64(lc.total_tiles, (uint64_t)sms * per_sm);
+    kern<<<(unsigned)grid, kCThreads, L.total, stream>>>(one, lc);
     return cudaGetLastError();
+}
+
+cudaError_t dispatch(int dtype, uint32_t block, const CField &one, const CompressLaunch &lc, int ctas_per_sm,
+                     cudaStream_t stream) {
+    if (dtype == 0) {
+        switch (block) {
+            case 32: return launch_t<float, 1, 32>(one, lc, ctas_per_sm, stream);
+            case 64: return launch_t<float, 2, 32>(one, lc, ctas_per_sm, stream);
+            case 128: return launch_t<float, 4, 32>(one, lc, ctas_per_sm, stream);
+            case 256: return launch_t<float, 8, 32>(one, lc, ctas_per_sm, stream);
+            case 512: return launch_t<float, 16, 32>(one, lc, ctas_per_sm, stream);
+            case 1024: return launch_t<float, 32, 32>(one, lc, ctas_per_sm, stream);
+        }
+    } else {
+        switch (block) {
+            case 32: return launch_t<double, 2, 16>(one, lc, ctas_per_sm, stream);
+            case 64: return launch_t<double, 4, 16>(one, lc, ctas_per_sm, stream);
+            case 128: return launch_t<double, 8, 16>(one, lc, ctas_per_sm, stream);
+            case 256: return launch_t<double, 16, 16>(one, lc, ctas_per_sm, stream);
+            case 512: return launch_t<double, 32, 16>(one, lc, ctas_per_sm, stream);
+            case 1024: return launch_t<double, 32, 32>(one, lc, ctas_per_sm, stream);
+        }
+    }
+    return cudaErrorInvalidValue;
 }
 
 }  // namespace
@@ -940,45 +1002,57 @@ cudaError_t launch_compress(const void *in, uint64_t n, int dtype, uint64_t e_bi
                               d_result, stream);
 }
 
+void fill_compress_field(CField *f, const void *in, uint64_t n, int dtype, uint64_t e_bits, uint32_t block,
+                         void *out, void *ws, uint64_t *d_result, uint64_t tile0) {
+    CField &c = *f;
+    std::memset(&c, 0, sizeof(c));
+    const uint32_t w = dtype == 0 ? 4 : 8;
+    c.in = static_cast<const uint8_t *>(in);
+    c.out = static_cast<uint8_t *>(out);
+    c.g = make_geometry(n, block, w);
+    c.ws = reinterpret_cast<Workspace *>(ws);
+    c.lookback = reinterpret_cast<uint64_t *>(static_cast<uint8_t *>(ws) + kWsHeader);
+    c.d_result = d_result;
+    c.e_bits = e_bits;
+    c.dtype = (uint32_t)dtype;
+    c.rows_full = n * w / 128;
+    c.tile0 = tile0;
+    c.use_tma = encode_row_map(&c.tmap, in, c.rows_full, 256) ? 1u : 0u;
+}
+
 cudaError_t launch_compress_ws(const void *in, uint64_t n, int dtype, uint64_t e_bits, uint32_t block,
                                void *out, void *ws, uint64_t *d_result, cudaStream_t stream) {
-    CompressArgs a;
-    const uint32_t w = dtype == 0 ? 4 : 8;
-    a.in = static_cast<const uint8_t *>(in);
-    a.out = static_cast<uint8_t *>(out);
-    a.g = make_geometry(n, block, w);
-    a.ws = reinterpret_cast<Workspace *>(ws);
-    a.lookback = reinterpret_cast<uint64_t *>(static_cast<uint8_t *>(ws) + kWsHeader);
-    a.d_result = d_result;
-    a.e_bits = e_bits;
-    a.dtype = (uint32_t)dtype;
-    a.lookback_ns = 1000ull * wait_limit_from_env("SZX_LOOKBACK_US", 1000000u);
-    a.copy_ns = 1000ull * wait_limit_from_env("SZX_COPY_US", 1000000u);
-    a.rows_full = n * w / 128;
-    CUtensorMap tm;
-    a.use_tma = encode_row_map(&tm, in, a.rows_full, 256) ? 1u : 0u;
-    cudaError_t err = cudaMemsetAsync(a.ws, 0, workspace_bytes(a.g.ntiles), stream);
+    CField one;
+    fill_compress_field(&one, in, n, dtype, e_bits, block, out, ws, d_result, 0);
+    Workspace *w = reinterpret_cast<Workspace *>(ws);
+    CompressLaunch lc;
+    lc.fields = nullptr;
+    lc.nfields = 1;
+    lc.total_tiles = one.g.ntiles;
+    lc.ticket = &w->ticket;
+    lc.done = &w->done;
+    lc.err = &w->err;
+    lc.lookback_ns = 1000ull * wait_limit_from_env("SZX_LOOKBACK_US", 1000000u);
+    lc.copy_ns = 1000ull * wait_limit_from_env("SZX_COPY_US", 1000000u);
+    cudaError_t err = cudaMemsetAsync(ws, 0, workspace_bytes(one.g.ntiles), stream);
     if (err != cudaSuccess) return err;
-    if (dtype == 0) {
-        switch (block) {
-            case 32: return launch_t<float, 1, 32>(tm, a, stream);
-            case 64: return launch_t<float, 2, 32>(tm, a, stream);
-            case 128: return launch_t<float, 4, 32>(tm, a, stream);
-            case 256: return launch_t<float, 8, 32>(tm, a, stream);
-            case 512: return launch_t<float, 16, 32>(tm, a, stream);
-            case 1024: return launch_t<float, 32, 32>(tm, a, stream);
-        }
-    } else {
-        switch (block) {
-            case 32: return launch_t<double, 2, 16>(tm, a, stream);
-            case 64: return launch_t<double, 4, 16>(tm, a, stream);
-            case 128: return launch_t<double, 8, 16>(tm, a, stream);
-            case 256: return launch_t<double, 16, 16>(tm, a, stream);
-            case 512: return launch_t<double, 32, 16>(tm, a, stream);
-            case 1024: return launch_t<double, 32, 32>(tm, a, stream);
-        }
-    }
-    return cudaErrorInvalidValue;
+    return dispatch(dtype, block, one, lc, 0, stream);
+}
+
+cudaError_t launch_compress_batch(const void *d_fields, uint32_t nfields, uint64_t total_tiles, uint32_t *d_counters,
+                                  int dtype, uint32_t block, int ctas_per_sm, cudaStream_t stream) {
+    CField one;
+    std::memset(&one, 0, sizeof(one));
+    CompressLaunch lc;
+    lc.fields = static_cast<const CField *>(d_fields);
+    lc.nfields = nfields;
+    lc.total_tiles = total_tiles;
+    lc.ticket = d_counters;
+    lc.done = d_counters + 1;
+    lc.err = d_counters + 2;
+    lc.lookback_ns = 1000ull * wait_limit_from_env("SZX_LOOKBACK_US", 1000000u);
+    lc.copy_ns = 1000ull * wait_limit_from_env("SZX_COPY_US", 1000000u);
+    return dispatch(dtype, block, one, lc, ctas_per_sm, stream);
 }
 
 // ---------------------------------------------------------------------------

@@ -37,6 +37,7 @@
 //      v' = t << s and d' = RN(v' + mu);
 //   4. after a second barrier (the record is no longer read) the values go to
 //      the stage buffer and the storer takes over.
+#include <cstring>
 #include <type_traits>
 
 #include "szx_device.cuh"
@@ -44,20 +45,31 @@
 
 namespace szx {
 
-struct DecompressArgs {
-    const uint8_t *in;
-    uint64_t in_bytes;
-    uint8_t *out;
-    uint32_t *status;
-    Geometry g;
-    uint64_t rec_total;
-    uint32_t dtype;
-    uint32_t check_header;  // re-check the stream header on the device
-    uint64_t total_bytes;
-    uint64_t copy_ns;    // wall-time limit of the record copy wait
-    uint64_t rows_full;  // 128-byte output rows fully inside the output
-    uint32_t use_tma;    // store full rows with the tensor store (else plain stores)
+struct DecompressLaunch {
+    const DField *fields;  // device table of nfields fields, or null: the single field
+    uint32_t nfields;
+    uint64_t total_tiles;  // tiles of all fields, field after field
+    uint64_t copy_ns;      // wall-time limit of a copy wait
 };
+
+template <bool BATCH>
+__device__ __forceinline__ const DField *dfield_ptr(const DField &one, const DecompressLaunch &lc, uint32_t f) {
+    if constexpr (BATCH) return lc.fields + f;
+    else return &one;  // the kernel parameter itself (param space)
+}
+
+// The field holding global tile t: the last one whose first tile is <= t.
+template <bool BATCH>
+__device__ __forceinline__ uint32_t dfield_of(const DecompressLaunch &lc, uint64_t t) {
+    if constexpr (!BATCH) return 0;
+    uint32_t lo = 0, hi = lc.nfields - 1;
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi + 1) / 2;
+        if (lc.fields[mid].tile0 <= t) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
 
 __device__ __forceinline__ void flag_status(uint32_t *status, uint32_t code) {
     if (status) atomicMax(status, code);
@@ -157,9 +169,9 @@ __device__ __forceinline__ void dmbar_arrive(uint64_t *bar) {
 }
 
 // Persistent decoder: tile = blockIdx.x + it * gridDim.x for it = 0, 1, ...
-template <typename T, int LPB, int VPL>
+template <typename T, int LPB, int VPL, bool BATCH>
 __global__ void __launch_bounds__(kDThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
-    decompress_kernel(const __grid_constant__ CUtensorMap tmap, DecompressArgs a) {
+    decompress_kernel(const __grid_constant__ DField one, const __grid_constant__ DecompressLaunch lc) {
     using F = Fmt<T>;
     using U = typename F::U;
     constexpr int w = F::w;
@@ -179,10 +191,10 @@ __global__ void __launch_bounds__(kDThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
     // st_bad: set by the producer (index or header fault); st_dbad: set by a
     // decoder (bad codes), read only after the barrier
     __shared__ uint32_t st_size[kDStages], st_bad[kDStages], st_dbad[kDStages], st_boff[kDStages];
+    __shared__ uint32_t st_field[kDStages], st_tile[kDStages];  // the stage's field and its local tile
     __shared__ uint32_t s_abort;  // a decoder's wait ran out: the CTA stops after the barrier
 
     uint8_t *smem = smem_raw + ((1024u - (smem_addr(smem_raw) & 1023u)) & 1023u);
-    const Geometry &g = a.g;
     const DSmem L = decompress_smem(G, b, w);
     const uint32_t *lut = reinterpret_cast<const uint32_t *>(smem + L.lut);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -196,7 +208,7 @@ __global__ void __launch_bounds__(kDThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
         for (int i = 0; i < kDStages; ++i) {
             mbar_init(&full[i], 1);
             mbar_init(&consumed[i], kDWarps);
-            st_size[i] = st_bad[i] = st_dbad[i] = st_boff[i] = 0;
+            st_size[i] = st_bad[i] = st_dbad[i] = st_boff[i] = st_field[i] = st_tile[i] = 0;
         }
         s_abort = 0;
         fence_mbar_init();
@@ -207,44 +219,50 @@ __global__ void __launch_bounds__(kDThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
         // ---- producer: record, mu and state-bit copies into the stages ------
         if (lane != 0) return;
         const uint32_t rec_max = record_max_bytes(G, b, w);
-        const uint64_t *idx = reinterpret_cast<const uint64_t *>(a.in + g.off_index);
         // per stage (bit st): is its last phase a copy (then it may still be in
         // flight when the producer is done), and that phase's parity
         uint32_t copy_last = 0, copy_par = 0;
-        uint64_t n0 = 0, n1 = 0;  // index entries of the next tile
-        if (blockIdx.x < g.ntiles) {
-            n0 = idx[blockIdx.x];
-            n1 = idx[blockIdx.x + 1];
-        }
+        // the next tile (its field, local index and index entries), loaded one
+        // tile ahead so that its entries arrive while this iteration waits
+        uint32_t nf = 0, ntile = 0;
+        uint64_t n0 = 0, n1 = 0;
+        auto load_next = [&](uint64_t t) {
+            if (t >= lc.total_tiles) return;
+            nf = dfield_of<BATCH>(lc, t);
+            const DField *F = dfield_ptr<BATCH>(one, lc, nf);
+            ntile = (uint32_t)(t - F->tile0);
+            const uint64_t *idx = reinterpret_cast<const uint64_t *>(F->in + F->g.off_index);
+            n0 = idx[ntile];
+            n1 = idx[ntile + 1];
+        };
+        load_next(blockIdx.x);
         for (uint32_t it = 0;; ++it) {
             const uint64_t tile64 = (uint64_t)blockIdx.x + (uint64_t)it * gridDim.x;
-            if (tile64 >= g.ntiles) break;
-            const uint32_t tile = (uint32_t)tile64;
+            if (tile64 >= lc.total_tiles) break;
+            const uint32_t f = nf, tile = ntile;
+            const DField *F = dfield_ptr<BATCH>(one, lc, f);
+            const Geometry &g = F->g;
             const int st = (int)(it % kDStages);
             const uint32_t k = it / kDStages;
             const uint64_t r0 = n0, r1 = n1;
-            // load the following tile's entries now; they arrive while this
-            // iteration waits for its stage
-            const uint64_t next = tile64 + gridDim.x;
-            if (next < g.ntiles) {
-                n0 = idx[next];
-                n1 = idx[next + 1];
-            }
-            if (it >= kDStages && !mbar_wait_bounded(&consumed[st], (k - 1) & 1u, 8 * a.copy_ns)) {
-                flag_status(a.status, 6u);
+            load_next(tile64 + gridDim.x);
+            if (it >= kDStages && !mbar_wait_bounded(&consumed[st], (k - 1) & 1u, 8 * lc.copy_ns)) {
+                flag_status(F->status, 6u);
                 break;
             }
             uint32_t bad = 0;
-            if (a.check_header && tile == 0) {
-                const uint32_t *h32 = reinterpret_cast<const uint32_t *>(a.in);
-                const uint64_t *h64 = reinterpret_cast<const uint64_t *>(a.in);
-                if (h32[0] != kMagic || (h32[1] & 0xFFFFu) != (kVersion | (a.dtype << 8)) || h32[2] != b ||
-                    h32[3] != G || h64[2] != g.n || h64[7] != a.total_bytes)
+            if (F->check_header && tile == 0) {
+                const uint32_t *h32 = reinterpret_cast<const uint32_t *>(F->in);
+                const uint64_t *h64 = reinterpret_cast<const uint64_t *>(F->in);
+                if (h32[0] != kMagic || (h32[1] & 0xFFFFu) != (kVersion | (F->dtype << 8)) || h32[2] != b ||
+                    h32[3] != G || h64[2] != g.n || h64[7] != F->total_bytes)
                     bad = 1;
             }
-            if (r0 > r1 || r1 > a.rec_total || (r0 & 15) || (r1 & 15) || r1 - r0 > rec_max) bad = 1;
-            if (tile == g.ntiles - 1 && r1 != a.rec_total) bad = 1;
+            if (r0 > r1 || r1 > F->rec_total || (r0 & 15) || (r1 & 15) || r1 - r0 > rec_max) bad = 1;
+            if (tile == g.ntiles - 1 && r1 != F->rec_total) bad = 1;
             const uint32_t size = bad ? 0u : (uint32_t)(r1 - r0);
+            st_field[st] = f;
+            st_tile[st] = tile;
             st_size[st] = size;
             st_bad[st] = bad;
             st_dbad[st] = 0;
@@ -261,9 +279,9 @@ __global__ void __launch_bounds__(kDThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
                 st_boff[st] = (uint32_t)(sb0 - sbA);
                 uint8_t *stage = smem + st * L.stage;
                 mbar_arrive_expect_tx(&full[st], size + mu_bytes + (uint32_t)(sbE - sbA));
-                if (size) bulk_g2s(stage, a.in + g.off_rec + r0, size, &full[st]);
-                bulk_g2s(stage + L.mu, a.in + g.off_mu + k0 * w, mu_bytes, &full[st]);
-                bulk_g2s(stage + L.bits, a.in + sbA, (uint32_t)(sbE - sbA), &full[st]);
+                if (size) bulk_g2s(stage, F->in + g.off_rec + r0, size, &full[st]);
+                bulk_g2s(stage + L.mu, F->in + g.off_mu + k0 * w, mu_bytes, &full[st]);
+                bulk_g2s(stage + L.bits, F->in + sbA, (uint32_t)(sbE - sbA), &full[st]);
                 copy_last |= 1u << st;
                 copy_par = (copy_par & ~(1u << st)) | ((k & 1u) << st);
             } else {
@@ -273,7 +291,7 @@ __global__ void __launch_bounds__(kDThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
         }
         // do not leave while a copy may still be writing into shared memory
         for (int st = 0; st < kDStages; ++st)
-            if ((copy_last >> st) & 1u) mbar_wait_bounded(&full[st], (copy_par >> st) & 1u, a.copy_ns);
+            if ((copy_last >> st) & 1u) mbar_wait_bounded(&full[st], (copy_par >> st) & 1u, lc.copy_ns);
         return;
     }
 
@@ -282,14 +300,16 @@ __global__ void __launch_bounds__(kDThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
     const uint32_t lane_row0 = (uint32_t)(lane * RPL);  // inside the warp's rows
     for (uint32_t it = 0;; ++it) {
         const uint64_t tile64 = (uint64_t)blockIdx.x + (uint64_t)it * gridDim.x;
-        if (tile64 >= g.ntiles) break;
-        const uint32_t tile = (uint32_t)tile64;
+        if (tile64 >= lc.total_tiles) break;
         const int st = (int)(it % kDStages);
         const uint32_t k = it / kDStages;
         // a wait that ran out still joins the barrier below (every decoding
         // warp must), then the whole CTA stops
-        const bool waited = mbar_wait_bounded(&full[st], k & 1u, a.copy_ns);
+        const bool waited = mbar_wait_bounded(&full[st], k & 1u, lc.copy_ns);
         if (!waited) s_abort = 1;
+        const DField *Fd = dfield_ptr<BATCH>(one, lc, st_field[st]);
+        const Geometry &g = Fd->g;
+        const uint32_t tile = st_tile[st];
         const uint32_t size = st_size[st];
         const bool pbad = st_bad[st] != 0 || !waited;
         uint8_t *rec = smem + st * L.stage;
@@ -401,7 +421,7 @@ __global__ void __launch_bounds__(kDThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
         const bool bad = abort || st_bad[st] || st_dbad[st] || pad16(used) != size;
         U x[VPL];
         if (bad) {
-            if (tid == 0) flag_status(a.status, abort ? 6u : 3u);
+            if (tid == 0) flag_status(Fd->status, abort ? 6u : 3u);
         } else {
             // ---- decode --------------------------------------------------
             const uint32_t mbase = nn_t * (b / 4 + 1) + before + blk_excl;
@@ -530,7 +550,7 @@ __global__ void __launch_bounds__(kDThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
             // strictness: the record's pad bytes must be zero
             if (warp == 0)
                 for (uint32_t i = used + lane; i < size; i += 32)
-                    if (rec[i]) flag_status(a.status, 3u);
+                    if (rec[i]) flag_status(Fd->status, 3u);
         }
         // this warp no longer reads the stage
         __syncwarp();
@@ -541,7 +561,7 @@ __global__ void __launch_bounds__(kDThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
         // ---- output: full rows through the warp's buffer and a tensor store,
         // the ragged last row with plain stores ------------------------------
         const uint64_t wrow0 = (uint64_t)tile * 256 * RPL + (uint64_t)warp * 32 * RPL;  // warp's first row
-        const bool tma_rows = a.use_tma && wrow0 < a.rows_full;
+        const bool tma_rows = Fd->use_tma && wrow0 < Fd->rows_full;
         if (tma_rows) {
             // the buffer is free once the previous tile's store has read it
             if (lane == 0) bulk_wait_read_all();
@@ -554,7 +574,7 @@ __global__ void __launch_bounds__(kDThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
                 const int nv = nvalid - rr * VPR;
                 if (nv <= 0) continue;
                 const uint32_t rowi = lane_row0 + rr;
-                if (a.use_tma && wrow0 + rowi < a.rows_full) {
+                if (Fd->use_tma && wrow0 + rowi < Fd->rows_full) {
                     uint8_t *row = wbuf + (rowi << 7);
 #pragma unroll
                     for (int c = 0; c < 8; ++c) {
@@ -565,7 +585,7 @@ __global__ void __launch_bounds__(kDThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
                         *reinterpret_cast<uint4 *>(row + ((c ^ (rowi & 7u)) << 4)) = v;
                     }
                 } else {
-                    U *dst = reinterpret_cast<U *>(a.out) + kg * b + sub * VPL + rr * VPR;
+                    U *dst = reinterpret_cast<U *>(Fd->out) + kg * b + sub * VPL + rr * VPR;
                     if (nv >= VPR) {
 #pragma unroll
                         for (int c = 0; c < 8; ++c) {
@@ -588,7 +608,7 @@ __global__ void __launch_bounds__(kDThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
             __syncwarp();
             if (lane == 0) {
                 asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(
-                                 reinterpret_cast<uint64_t>(&tmap)),
+                                 reinterpret_cast<uint64_t>(&Fd->tmap)),
                              "r"(0), "r"((int)wrow0), "r"(smem_addr(wbuf))
                              : "memory");
                 bulk_commit();
@@ -601,10 +621,13 @@ __global__ void __launch_bounds__(kDThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
 
 // ---------------------------------------------------------------------------
 
+namespace {
+
 template <typename T, int LPB, int VPL>
-static cudaError_t launch_t(const CUtensorMap &tm, const DecompressArgs &a, cudaStream_t stream) {
-    const DSmem L = decompress_smem(a.g.G, a.g.b, Fmt<T>::w);
-    auto kern = decompress_kernel<T, LPB, VPL>;
+cudaError_t launch_t(const DField &one, const DecompressLaunch &lc, int ctas_per_sm, cudaStream_t stream) {
+    constexpr uint32_t b = (uint32_t)(LPB * VPL), w = (uint32_t)Fmt<T>::w;
+    const DSmem L = decompress_smem(tile_blocks(b, w), b, w);
+    auto kern = lc.fields ? decompress_kernel<T, LPB, VPL, true> : decompress_kernel<T, LPB, VPL, false>;
     cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total);
     if (err != cudaSuccess) return err;
     int dev = 0, sms = 0, per_sm = 0;
@@ -613,50 +636,84 @@ static cudaError_t launch_t(const CUtensorMap &tm, const DecompressArgs &a, cuda
     if ((err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kDThreads, L.total)) != cudaSuccess)
         return err;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
-    const uint64_t grid = min_u64(a.g.ntiles, (uint64_t)sms * per_sm);
-    kern<<<(unsigned)grid, kDThreads, L.total, stream>>>(tm, a);
+    if (ctas_per_sm > 0 && ctas_per_sm < per_sm) per_sm = ctas_per_sm;
+    const uint64_t grid = min_u64(lc.total_tiles, (uint64_t)sms * per_sm);
+    kern<<<(unsigned)grid, kDThreads, L.total, stream>>>(one, lc);
     return cudaGetLastError();
+}
+
+cudaError_t ddispatch(int dtype, uint32_t block, const DField &one, const DecompressLaunch &lc, int ctas_per_sm,
+                      cudaStream_t stream) {
+    if (dtype == 0) {
+        switch (block) {
+            case 32: return launch_t<float, 1, 32>(one, lc, ctas_per_sm, stream);
+            case 64: return launch_t<float, 2, 32>(one, lc, ctas_per_sm, stream);
+            case 128: return launch_t<float, 4, 32>(one, lc, ctas_per_sm, stream);
+            case 256: return launch_t<float, 8, 32>(one, lc, ctas_per_sm, stream);
+            case 512: return launch_t<float, 16, 32>(one, lc, ctas_per_sm, stream);
+            case 1024: return launch_t<float, 32, 32>(one, lc, ctas_per_sm, stream);
+        }
+    } else {
+        switch (block) {
+            case 32: return launch_t<double, 2, 16>(one, lc, ctas_per_sm, stream);
+            case 64: return launch_t<double, 4, 16>(one, lc, ctas_per_sm, stream);
+            case 128: return launch_t<double, 8, 16>(one, lc, ctas_per_sm, stream);
+            case 256: return launch_t<double, 16, 16>(one, lc, ctas_per_sm, stream);
+            case 512: return launch_t<double, 32, 16>(one, lc, ctas_per_sm, stream);
+            case 1024: return launch_t<double, 32, 32>(one, lc, ctas_per_sm, stream);
+        }
+    }
+    return cudaErrorInvalidValue;
+}
+
+uint64_t copy_limit_ns() { return 1000ull * wait_limit_from_env("SZX_COPY_US", 1000000u); }
+
+}  // namespace
+
+void fill_decompress_field(DField *f, const void *in, uint64_t total_bytes, uint64_t n, int dtype, uint32_t block,
+                           void *out, uint32_t *d_status, bool check_header, uint64_t tile0) {
+    DField &a = *f;
+    std::memset(&a, 0, sizeof(a));
+    const uint32_t w = dtype == 0 ? 4 : 8;
+    a.in = static_cast<const uint8_t *>(in);
+    a.out = static_cast<uint8_t *>(out);
+    a.status = d_status;
+    a.g = make_geometry(n, block, w);
+    a.rec_total = total_bytes - a.g.off_rec;
+    a.total_bytes = total_bytes;
+    a.rows_full = n * w / 128;
+    a.tile0 = tile0;
+    a.dtype = (uint32_t)dtype;
+    a.check_header = check_header ? 1u : 0u;
+    // one box per decoding warp: its 32 lanes' rows
+    const uint32_t box_rows = (dtype == 1 && block == 1024) ? 64u : 32u;
+    a.use_tma = encode_row_map(&a.tmap, out, a.rows_full, box_rows) ? 1u : 0u;
 }
 
 cudaError_t launch_decompress(const void *in, uint64_t in_bytes, uint64_t total_bytes, uint64_t n, int dtype,
                               uint32_t block, void *out, uint32_t *d_status, bool check_header,
                               cudaStream_t stream) {
-    DecompressArgs a;
-    a.in = static_cast<const uint8_t *>(in);
-    a.in_bytes = in_bytes;
-    a.out = static_cast<uint8_t *>(out);
-    a.status = d_status;
-    a.g = make_geometry(n, block, dtype == 0 ? 4 : 8);
-    a.rec_total = total_bytes - a.g.off_rec;
-    a.dtype = (uint32_t)dtype;
-    a.check_header = check_header ? 1u : 0u;
-    a.total_bytes = total_bytes;
-    a.copy_ns = 1000ull * wait_limit_from_env("SZX_COPY_US", 1000000u);
-    a.rows_full = n * (dtype == 0 ? 4 : 8) / 128;
-    CUtensorMap tm;
-    // one box per decoding warp: its 32 lanes' rows
-    const uint32_t box_rows = (dtype == 1 && block == 1024) ? 64u : 32u;
-    a.use_tma = encode_row_map(&tm, out, a.rows_full, box_rows) ? 1u : 0u;
-    if (dtype == 0) {
-        switch (block) {
-            case 32: return launch_t<float, 1, 32>(tm, a, stream);
-            case 64: return launch_t<float, 2, 32>(tm, a, stream);
-            case 128: return launch_t<float, 4, 32>(tm, a, stream);
-            case 256: return launch_t<float, 8, 32>(tm, a, stream);
-            case 512: return launch_t<float, 16, 32>(tm, a, stream);
-            case 1024: return launch_t<float, 32, 32>(tm, a, stream);
-        }
-    } else {
-        switch (block) {
-            case 32: return launch_t<double, 2, 16>(tm, a, stream);
-            case 64: return launch_t<double, 4, 16>(tm, a, stream);
-            case 128: return launch_t<double, 8, 16>(tm, a, stream);
-            case 256: return launch_t<double, 16, 16>(tm, a, stream);
-            case 512: return launch_t<double, 32, 16>(tm, a, stream);
-            case 1024: return launch_t<double, 32, 32>(tm, a, stream);
-        }
-    }
-    return cudaErrorInvalidValue;
+    (void)in_bytes;
+    DField one;
+    fill_decompress_field(&one, in, total_bytes, n, dtype, block, out, d_status, check_header, 0);
+    DecompressLaunch lc;
+    lc.fields = nullptr;
+    lc.nfields = 1;
+    lc.total_tiles = one.g.ntiles;
+    lc.copy_ns = copy_limit_ns();
+    return ddispatch(dtype, block, one, lc, 0, stream);
+}
+
+cudaError_t launch_decompress_batch(const void *d_fields, uint32_t nfields, uint64_t total_tiles, int dtype,
+                                    uint32_t block, int ctas_per_sm, cudaStream_t stream) {
+    DField one;
+    std::memset(&one, 0, sizeof(one));
+    DecompressLaunch lc;
+    lc.fields = static_cast<const DField *>(d_fields);
+    lc.nfields = nfields;
+    lc.total_tiles = total_tiles;
+    lc.copy_ns = copy_limit_ns();
+    return ddispatch(dtype, block, one, lc, ctas_per_sm, stream);
 }
 
 }  // namespace szx

@@ -6,6 +6,7 @@
 #pragma once
 
 #include <cstdint>
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 namespace szx {
@@ -307,5 +308,40 @@ constexpr uint64_t kValueMask = (1ull << 62) - 1;
 __host__ __device__ __forceinline__ uint64_t workspace_bytes(uint64_t ntiles) {
     return kWsHeader + 8 * ntiles;
 }
+
+// One field of a compression launch.  A launch covers one field (passed by
+// value) or a table of fields of the same dtype and block length in device
+// memory; its tiles form one global list, field after field.
+struct alignas(64) CField {
+    CUtensorMap tmap;  // the field's input rows (TMA), valid if use_tma
+    const uint8_t *in;
+    uint8_t *out;
+    Workspace *ws;  // the field's counters and result
+    uint64_t *lookback;  // the field's look-back words (one per tile, zeroed)
+    uint64_t *d_result;  // {stream bytes, status} on completion, or null
+    Geometry g;
+    uint64_t e_bits;
+    uint64_t rows_full;  // 128-byte input rows fully inside the input
+    uint64_t tile0;      // the field's first tile in the launch's global list
+    uint32_t dtype;
+    uint32_t use_tma;
+};
+
+
+// One field of a decompression launch (same arrangement as CField).
+struct alignas(64) DField {
+    CUtensorMap tmap;  // the field's output rows (one box per decoding warp), valid if use_tma
+    const uint8_t *in;  // the stream
+    uint8_t *out;       // n values
+    uint32_t *status;   // szx_status, folded in with atomicMax, or null
+    Geometry g;
+    uint64_t rec_total;    // bytes of the tile records
+    uint64_t total_bytes;  // stream size (the header's)
+    uint64_t rows_full;    // 128-byte output rows fully inside the output
+    uint64_t tile0;        // the field's first tile in the launch's global list
+    uint32_t dtype;
+    uint32_t check_header;  // re-check the stream header on the device
+    uint32_t use_tma;
+};
 
 }  // namespace szx

@@ -29,6 +29,34 @@ cudaError_t launch_compress(const void *in, uint64_t n, int dtype, uint64_t e_bi
 cudaError_t launch_compress_ws(const void *in, uint64_t n, int dtype, uint64_t e_bits, uint32_t block,
                                void *out, void *ws, uint64_t *d_result, cudaStream_t stream);
 
+struct CField;
+
+// Fill the descriptor of one field for a batched compression launch (host
+// memory; the tensor map is encoded here).  ws: the field's workspace
+// (workspace_bytes(ntiles), zeroed before the launch); tile0: the field's first
+// tile in the launch's global list.
+void fill_compress_field(CField *f, const void *in, uint64_t n, int dtype, uint64_t e_bits, uint32_t block,
+                         void *out, void *ws, uint64_t *d_result, uint64_t tile0);
+
+// Enqueue one persistent compression launch over the nfields descriptors at
+// d_fields (device memory, 64-byte aligned; all of dtype and block), whose
+// tiles number total_tiles.  d_counters: 3 zeroed words (ticket, done, error
+// bits).  ctas_per_sm: 0 = as many as fit, else at most that many.
+cudaError_t launch_compress_batch(const void *d_fields, uint32_t nfields, uint64_t total_tiles, uint32_t *d_counters,
+                                  int dtype, uint32_t block, int ctas_per_sm, cudaStream_t stream);
+
+struct DField;
+
+// Fill the descriptor of one stream for a batched decompression launch (host
+// memory; the output tensor map is encoded here).
+void fill_decompress_field(DField *f, const void *in, uint64_t total_bytes, uint64_t n, int dtype, uint32_t block,
+                           void *out, uint32_t *d_status, bool check_header, uint64_t tile0);
+
+// Enqueue one persistent decompression launch over nfields descriptors at
+// d_fields (device memory, 64-byte aligned; all of dtype and block).
+cudaError_t launch_decompress_batch(const void *d_fields, uint32_t nfields, uint64_t total_tiles, int dtype,
+                                    uint32_t block, int ctas_per_sm, cudaStream_t stream);
+
 // Enqueue the decompression of a stream of total_bytes whose header says
 // (n, dtype, block).  Errors are folded into *d_status with atomicMax as
 // szx_status codes (d_status may be null).

@@ -1,0 +1,146 @@
+"""Batched compression / decompression (many fields, one persistent launch per
+(dtype, block) group) through the C ABI: every stream byte-identical to the
+single-field call and to the oracle, every decode bit-identical."""
+import ctypes
+
+import numpy as np
+import pytest
+
+import oracle
+
+torch = pytest.importorskip("torch")
+import paper_2201_13020_b300 as szx  # noqa: E402
+from paper_2201_13020_b300 import _lib, inputs  # noqa: E402
+
+
+def _fields():
+    """Mixed dtypes, blocks and sizes (ragged ends, single block, several tiles)."""
+    rng = np.random.default_rng(21)
+    out = []
+    out.append((inputs.sinusoid_1d((1 << 16) + 77, seed=3), 1e-3, 128))
+    g = inputs.grf_3d((40, 37, 29), -5.0 / 3.0, 4).numpy()
+    out.append((g.reshape(-1), 1e-3, 128))
+    g64 = inputs.grf_3d((30, 31, 33), -11.0 / 3.0, 5, dtype=torch.float64).numpy()
+    out.append((g64.reshape(-1), 1e-4, 256))
+    out.append((rng.normal(size=5000).astype(np.float32), 1e-2, 64))
+    out.append((np.cumsum(rng.normal(size=100_003)).astype(np.float64), 1e-3, 128))
+    out.append((np.array([1.5], dtype=np.float32), 1e-3, 128))
+    out.append((rng.normal(size=50_000).astype(np.float32), 1e-3, 1024))
+    out.append((np.cumsum(rng.normal(size=70_001)).astype(np.float64), 1e-4, 1024))
+    out.append((inputs.sinusoid_1d(200_000, seed=9), 1e-4, 128))  # same group as field 0
+    # a single value has no range: its bound is absolute
+    return [(x, inputs.rel_to_abs(x, rel) if x.size > 1 else rel, b) for x, rel, b in out]
+
+
+@pytest.mark.gpu
+def test_batch_compress_and_decompress_match_single_and_oracle():
+    fields = _fields()
+    xs = [torch.from_numpy(np.ascontiguousarray(x)).cuda() for x, _, _ in fields]
+    batch, outs, results = szx.batch_compress(xs, [eb for _, eb, _ in fields], [b for _, _, b in fields])
+    assert len(batch.groups()) == 6
+    batch.run()
+    torch.cuda.synchronize()
+    res = results.cpu().numpy().reshape(-1, 2)
+    streams = []
+    for i, ((x, eb, b), xt) in enumerate(zip(fields, xs)):
+        assert res[i, 1] == 0, f"field {i}: status {res[i, 1]}"
+        got = outs[i][:int(res[i, 0])].cpu().numpy()
+        single = szx.compress(xt, eb, b).cpu().numpy()
+        assert np.array_equal(got, single), f"field {i}: batch stream differs from the single-field call"
+        ref = oracle.compress(x, eb, b)
+        assert np.array_equal(got, ref), f"field {i}: batch stream differs from the oracle"
+        streams.append(ref)
+    # batched decompression of the same streams
+    bufs = [torch.from_numpy(s).cuda() for s in streams]
+    headers = [szx.header(bb) for bb in bufs]
+    dbatch, ys, statuses = szx.batch_decompress(bufs, headers)
+    dbatch.run()
+    torch.cuda.synchronize()
+    assert statuses.cpu().tolist() == [0] * len(fields)
+    for i, (s, y) in enumerate(zip(streams, ys)):
+        ref = oracle.decompress(s)
+        u = np.uint32 if ref.dtype == np.float32 else np.uint64
+        assert np.array_equal(y.cpu().numpy().view(u), ref.view(u)), f"field {i}: decode differs"
+
+
+@pytest.mark.gpu
+def test_batch_graph_capture_replays_identically():
+    fields = _fields()[:5]
+    xs = [torch.from_numpy(np.ascontiguousarray(x)).cuda() for x, _, _ in fields]
+    batch, outs, results = szx.batch_compress(xs, [eb for _, eb, _ in fields], [b for _, _, b in fields])
+    batch.run()  # warm (kernel attributes set, modules loaded)
+    torch.cuda.synchronize()
+    first = [o.clone() for o in outs]
+    s = torch.cuda.Stream()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=s):
+        batch.run(stream=s)
+    for _ in range(2):
+        for o in outs:
+            o.zero_()
+        graph.replay()
+        torch.cuda.synchronize()
+        for i, (a, b_) in enumerate(zip(first, outs)):
+            n = int(results[2 * i].item())
+            assert torch.equal(a[:n], b_[:n]), f"field {i} differs after graph replay"
+            assert int(results[2 * i + 1].item()) == 0
+
+
+@pytest.mark.gpu
+def test_batch_autotune_keeps_streams():
+    fields = _fields()[:4]
+    xs = [torch.from_numpy(np.ascontiguousarray(x)).cuda() for x, _, _ in fields]
+    batch, outs, results = szx.batch_compress(xs, [eb for _, eb, _ in fields], [b for _, _, b in fields])
+    choice = batch.autotune()
+    assert all(c in (1, 2) for c in choice)
+    batch.run()
+    torch.cuda.synchronize()
+    for i, (x, eb, b) in enumerate(fields):
+        n = int(results[2 * i].item())
+        assert np.array_equal(outs[i][:n].cpu().numpy(), oracle.compress(x, eb, b))
+
+
+@pytest.mark.gpu
+def test_batch_corrupt_stream_is_flagged_alone():
+    fields = _fields()[:3]
+    streams = [oracle.compress(x, eb, b) for x, eb, b in fields]
+    bufs = [torch.from_numpy(s).cuda() for s in streams]
+    headers = [szx.header(bb) for bb in bufs]
+    # stream 1: make its second tile-index entry odd (offsets are multiples of 16)
+    h = headers[1]
+    nb = -(-h.n // h.block)
+    w = 4 if h.dtype == szx.SZX_F32 else 8
+    off_mu = 64 + ((nb + 7) // 8 + 15) // 16 * 16
+    off_index = off_mu + (nb * w + 15) // 16 * 16
+    bad = streams[1].copy()
+    bad[off_index + 8] ^= 0x01
+    bufs[1] = torch.from_numpy(bad).cuda()
+    dbatch, ys, statuses = szx.batch_decompress(bufs, headers)
+    dbatch.run()
+    torch.cuda.synchronize()
+    st = statuses.cpu().tolist()
+    assert st[1] == 3 and st[0] == 0 and st[2] == 0
+    for i in (0, 2):
+        ref = oracle.decompress(streams[i])
+        u = np.uint32 if ref.dtype == np.float32 else np.uint64
+        assert np.array_equal(ys[i].cpu().numpy().view(u), ref.view(u))
+
+
+def test_batch_plan_argument_checks_on_host():
+    # plan creation is host-only: fake aligned device addresses are never touched
+    L = _lib.lib()
+    F = _lib.SzxField
+    ok = F(256, 1000, _lib.SZX_F32, 1e-3, 128, 512, 1 << 20)
+    arr = (F * 2)(ok, F(256, 1000, _lib.SZX_F32, 1e-3, 100, 512, 1 << 20))
+    plan = ctypes.c_void_p(0)
+    assert L.szx_batch_compress_plan(arr, 2, ctypes.byref(plan)) == 1 and not plan.value
+    arr = (F * 1)(F(256, 1000, _lib.SZX_F32, 1e-3, 128, 512, 16))
+    assert L.szx_batch_compress_plan(arr, 1, ctypes.byref(plan)) == 2
+    arr = (F * 1)(F(257, 1000, _lib.SZX_F32, 1e-3, 128, 512, 1 << 20))
+    assert L.szx_batch_compress_plan(arr, 1, ctypes.byref(plan)) == 1
+    arr = (F * 2)(ok, F(256, 70_000, _lib.SZX_F64, 1e-3, 256, 512, 1 << 22))
+    assert L.szx_batch_compress_plan(arr, 2, ctypes.byref(plan)) == 0 and plan.value
+    assert L.szx_batch_workspace_bytes(plan) > 0
+    groups = (ctypes.c_int * 4)()
+    assert L.szx_batch_groups(plan, groups, 4) == 2
+    L.szx_batch_destroy(plan)
