@@ -15,6 +15,10 @@ given device for the large 3-D fields).
   state_vector -- unit-norm complex Gaussian amplitudes as interleaved re/im f64.
   rel_to_abs   -- value-range relative bound REL -> absolute bound (Sec. IV
                   footnote: e = REL * (max - min)).
+  sinusoid_1d_torch -- the 1-D recipe computed on a torch device (large sizes).
+  mixed_fields -- the many-field batch: sizes log-uniform in [lo, hi] bytes,
+                  70% f32 / 30% f64, 1-D / 2-D / 3-D generators, REL drawn
+                  from {1e-2, 1e-3, 1e-4}.
 """
 import hashlib
 import math
@@ -117,3 +121,62 @@ def sha256(arr):
 def field_sizes_loguniform(count, lo_bytes, hi_bytes, seed):
     rng = np.random.Generator(np.random.PCG64(seed))
     return [int(math.exp(v)) for v in rng.uniform(math.log(lo_bytes), math.log(hi_bytes), size=count)]
+
+
+def sinusoid_1d_torch(n, seed, device="cuda", dtype=None, const_frac=0.10, block=128):
+    """sinusoid_1d's recipe on a torch device (parameters drawn on the host)."""
+    import torch
+    dtype = dtype or torch.float32
+    rng = np.random.Generator(np.random.PCG64(seed))
+    amp = rng.uniform(0.1, 1.0, size=8)
+    freq = np.exp(rng.uniform(np.log(1.0), np.log(4096.0), size=8))
+    phase = rng.uniform(0.0, 2 * np.pi, size=8)
+    i = torch.arange(n, device=device, dtype=torch.float64)
+    clean = torch.zeros(n, device=device, dtype=torch.float64)
+    for a, f, ph in zip(amp, freq, phase):
+        clean += float(a) * torch.sin(i * (2 * np.pi * float(f) / n) + float(ph))
+    del i
+    span = float(clean.max() - clean.min())
+    gen = torch.Generator(device=device)
+    gen.manual_seed(seed)
+    x = clean + torch.randn(n, generator=gen, device=device, dtype=torch.float64) * (0.01 * span)
+    del clean
+    nb = n // block
+    if nb:
+        chosen = torch.from_numpy(rng.choice(nb, size=int(round(const_frac * nb)), replace=False)).to(device)
+        starts = chosen * block
+        idx = (starts[:, None] + torch.arange(block, device=device)[None, :]).reshape(-1)
+        x[idx] = x[starts].repeat_interleave(block)
+    return x.to(dtype)
+
+
+def mixed_fields(count, lo_bytes, hi_bytes, seed, device="cuda", block=128):
+    """The many-field batch: a list of (tensor, rel, kind) with sizes
+    log-uniform in [lo_bytes, hi_bytes] (rounded to whole blocks), 70% f32 and
+    30% f64, generators 1-D sinusoid, 2-D or 3-D GRF (spectrum exponent drawn
+    from {-5/3, -11/3}), REL drawn from {1e-2, 1e-3, 1e-4}."""
+    import torch
+    rng = np.random.Generator(np.random.PCG64(seed))
+    sizes = field_sizes_loguniform(count, lo_bytes, hi_bytes, seed)
+    out = []
+    for i, nbytes in enumerate(sizes):
+        f64 = rng.random() < 0.30
+        w = 8 if f64 else 4
+        n = max(block, (nbytes // (w * block)) * block)
+        dt = torch.float64 if f64 else torch.float32
+        kind = ["1d", "2d", "3d"][int(rng.integers(3))]
+        rel = float(rng.choice([1e-2, 1e-3, 1e-4]))
+        alpha = float(rng.choice([-5.0 / 3.0, -11.0 / 3.0]))
+        s = seed * 1000 + i
+        if kind == "1d":
+            x = sinusoid_1d_torch(n, s, device=device, dtype=dt)
+        else:
+            d = 2 if kind == "2d" else 3
+            edge = int(math.ceil(n ** (1.0 / d)))
+            while edge ** d < n:
+                edge += 1
+            g = grf_3d((edge,) * d, alpha, s, device=device, dtype=dt)
+            x = g.reshape(-1)[:n].contiguous()
+            del g
+        out.append((x, rel, f"{kind}/{'f64' if f64 else 'f32'}/a{alpha:.2f}"))
+    return out
