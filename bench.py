@@ -333,6 +333,104 @@ def run_batch96(args, world, rank, local):
     return 0
 
 
+def run_serve(args, world, rank, local):
+    """Serving: Poisson arrivals, 60% compress / 40% decompress of earlier
+    resident streams, sizes log-uniform 64 KiB - 256 MiB; half the compress
+    requests are complex f64 state vectors (unit-norm Gaussian, interleaved
+    re/im, 2^k amplitudes with 2^k * 16 bytes nearest the drawn size), half
+    f32 fields (the 1-D recipe); REL from {1e-2, 1e-3, 1e-4}; streams resident
+    in a 120 GB pool.  Two arms on the same requests: one slot (a plain queue)
+    and continuous batching (8 slots, overlapped on the device)."""
+    import math
+
+    import numpy as np
+    import torch
+
+    from paper_2201_13020_b300 import inputs, serve
+    torch.cuda.set_device(local)
+    rng = np.random.default_rng(77 + rank)
+    count, rate = args.requests, args.rate
+    specs = []
+    t = 0.0
+    comp = []
+    for i in range(count):
+        t += rng.exponential(1.0 / rate)
+        if comp and rng.random() < 0.40:
+            specs.append(("decompress", t, int(rng.choice(comp))))
+            continue
+        nbytes = math.exp(rng.uniform(math.log(64 << 10), math.log(256 << 20)))
+        rel = float(rng.choice([1e-2, 1e-3, 1e-4]))
+        if rng.random() < 0.5:
+            k = int(round(math.log2(nbytes / 16)))
+            specs.append(("compress", t, ("sv", 1 << max(12, min(24, k)), rel, i)))
+        else:
+            specs.append(("compress", t, ("f32", max(128, int(nbytes) // 4), rel, i)))
+        comp.append(len(specs) - 1)
+    data = {}
+    for kind, _, a in specs:
+        if kind == "compress":
+            what, n, rel, seed = a
+            x = (inputs.state_vector(n, seed=seed, device="cuda") if what == "sv"
+                 else inputs.sinusoid_1d_torch(n, seed=seed, device="cuda"))
+            data[seed] = (x, inputs.rel_to_abs(x, rel))
+    torch.cuda.synchronize()
+
+    def requests():
+        out = []
+        for kind, t, a in specs:
+            if kind == "compress":
+                x, eb = data[a[3]]
+                out.append(serve.Request("compress", t, x=x, eb=eb, block=BLOCK))
+            else:
+                out.append(serve.Request("decompress", t, source=a))
+        return out
+
+    arms = {}
+    for name, slots in (("queue_1slot", 1), ("continuous_8slots", 8)):
+        server = serve.Server(120 << 30, slots=slots)
+        # warm-up on the same server (module load, kernel set-up), then give
+        # its resident streams back
+        warm = [r for r in requests()[:12] if r.kind == "compress"]
+        server.run(warm)
+        for r in warm:
+            server.release(r.offset, r.nbytes)
+        reqs = requests()
+        with ClockSampler(local) as clocks:
+            span = server.run(reqs)
+        torch.cuda.synchronize()
+        bad = [i for i, r in enumerate(reqs) if r.status != 0]
+        if bad:
+            raise RuntimeError(f"{len(bad)} requests failed, first {bad[0]} status {reqs[bad[0]].status}")
+        lat = np.array([r.done_s - r.arrival for r in reqs]) * 1e3
+        lat_c = np.array([r.done_s - r.arrival for r in reqs if r.kind == "compress"]) * 1e3
+        lat_d = np.array([r.done_s - r.arrival for r in reqs if r.kind == "decompress"]) * 1e3
+        total = sum(r.nbytes_in for r in reqs)
+        arms[name] = {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                      "p50_compress_ms": float(np.percentile(lat_c, 50)),
+                      "p99_compress_ms": float(np.percentile(lat_c, 99)),
+                      "p50_decompress_ms": float(np.percentile(lat_d, 50)),
+                      "p99_decompress_ms": float(np.percentile(lat_d, 99)),
+                      "gbs": total / span / 1e9, "makespan_s": span, "input_bytes": total,
+                      "max_in_flight": server.max_in_flight, "clocks": clocks.summary(),
+                      "resident_stream_bytes": int(sum(r.nbytes for r in reqs if r.kind == "compress"))}
+        server.close()
+        del server, reqs
+        torch.cuda.empty_cache()
+    best = arms["continuous_8slots"]
+    if rank == 0:
+        line = {"metric": METRIC, "value": best["gbs"], "unit": "GB/s", "n_gpus": world, "steps": 1, "warmup": 1,
+                "ms_per_step": best["makespan_s"] * 1e3, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64(state vectors)+f32", "data": "synthetic",
+                "config": {"workload": f"serve_poisson{rate:g}_req{count}_64KiB-256MiB_60c40d",
+                           "requests": count, "compress": sum(k == "compress" for k, _, _ in specs),
+                           "decompress": sum(k == "decompress" for k, _, _ in specs), "pool_bytes": 120 << 30,
+                           "arrival_rate_per_s": rate, "block": BLOCK, "parallelism": f"replicas{world}"},
+                "p50_ms": best["p50_ms"], "p99_ms": best["p99_ms"], "arms": arms,
+                "gpu": torch.cuda.get_device_name(local)}
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def config_block(world):
     edge = SHAPE_RUN[0]
     return {"workload": f"grf{edge}_f32_k-5/3_zero-slabs25_rel1e-3_block128", "shape": list(SHAPE_RUN),
@@ -351,8 +449,11 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--size", type=int, default=512, help="cube edge (default 512; smaller only for captures)")
-    ap.add_argument("--workload", default="grf512", choices=["grf512", "batch96"],
-                    help="grf512: the 512^3 f32 field (default); batch96: 96 mixed fields, batched vs plain")
+    ap.add_argument("--workload", default="grf512", choices=["grf512", "batch96", "serve"],
+                    help="grf512: the 512^3 f32 field (default); batch96: 96 mixed fields, batched vs plain; "
+                         "serve: Poisson request mix through the serving loop")
+    ap.add_argument("--requests", type=int, default=600, help="serve: number of requests")
+    ap.add_argument("--rate", type=float, default=30000.0, help="serve: mean arrivals per second")
     args = ap.parse_args()
     SHAPE_RUN[:] = [args.size] * 3
     args.warmup = max(args.warmup, 3)
@@ -362,6 +463,8 @@ def main():
         return run_reference(args, world, rank)
     if args.workload == "batch96":
         return run_batch96(args, world, rank, local)
+    if args.workload == "serve":
+        return run_serve(args, world, rank, local)
 
     import numpy as np
     import torch

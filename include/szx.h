@@ -272,6 +272,71 @@ int szx_batch_groups(const szx_batch_plan *plan, int *ctas_per_sm, int capacity)
 
 void szx_batch_destroy(szx_batch_plan *plan);
 
+/* ------------------------------------------------------------------------
+ * Serving: requests that arrive over time, compressed streams resident in a
+ * device memory pool (the paper has no serving interface; it is a request
+ * form of szx_compress_async / szx_decompress_async).  A request is admitted,
+ * oldest first, as soon as one of the server's slots (CUDA streams) and room
+ * in the pool are free, so requests arriving while others run join them and
+ * overlap on the device.  The loop never synchronises the device; results and
+ * streams are byte-identical to the single calls'.
+ * ------------------------------------------------------------------------ */
+
+typedef struct szx_server szx_server; /* opaque, host memory */
+
+#define SZX_REQ_COMPRESS 0
+#define SZX_REQ_DECOMPRESS 1
+
+typedef struct {
+    int kind;           /* SZX_REQ_COMPRESS or SZX_REQ_DECOMPRESS */
+    double arrival_s;   /* arrival, seconds after the run starts */
+    /* compression: as szx_compress_async's arguments */
+    const void *d_in;
+    size_t n;
+    szx_dtype dtype;
+    double eb;
+    uint32_t block;
+    /* decompression: index (in the same run) of an earlier compression whose
+     * resident stream it decodes; keep_output: leave the decoded values
+     * allocated in the pool (at `offset`, `bytes` long) for the caller to read
+     * and release, else they are freed on completion */
+    int source;
+    int keep_output;
+    /* filled in by szx_server_run */
+    int status;         /* szx_status of the request (-1 if it never ran) */
+    double admit_s;     /* admission, seconds after the start */
+    double done_s;      /* first observation of completion */
+    uint64_t offset;    /* pool offset: compression's resident stream, or kept output */
+    uint64_t bytes;     /* stream bytes (compression) or output bytes */
+} szx_request;
+
+/* Create a server over the caller's device pool (256-byte aligned,
+ * pool_bytes long; the caller keeps ownership) with `slots` CUDA streams
+ * (1..64), on the current device.  Allocates its own small pinned and device
+ * status words.  Errors: SZX_ERR_INVALID, SZX_ERR_NOMEM, SZX_ERR_CUDA. */
+szx_status szx_server_create(void *d_pool, size_t pool_bytes, int slots,
+                             szx_server **server);
+
+/* The pool's base address, and its free bytes (not counting fragmentation). */
+void *szx_server_pool(const szx_server *server);
+size_t szx_server_free_bytes(const szx_server *server);
+
+/* Run `count` requests to completion (arrivals are timed from the call).
+ * Per-request outcomes are written into reqs; *max_in_flight (may be NULL)
+ * receives the largest number of requests that ran at once.  Returns
+ * SZX_ERR_NOMEM if a request could never fit in the pool (that request's
+ * status says so; the others still ran), else SZX_OK.  Resident streams of
+ * the run stay allocated until szx_server_release. */
+szx_status szx_server_run(szx_server *server, szx_request *reqs, int count,
+                          int *max_in_flight);
+
+/* Give back a pool range returned in a request (offset, bytes). */
+szx_status szx_server_release(szx_server *server, uint64_t offset,
+                              uint64_t bytes);
+
+/* Wait for the server's streams and free its resources (not the pool). */
+void szx_server_destroy(szx_server *server);
+
 /* Human-readable name of a status code. */
 const char *szx_status_string(szx_status s);
 

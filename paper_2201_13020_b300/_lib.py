@@ -89,4 +89,5 @@ def lib():
 EXPORTED = ["szx_compress_bound", "szx_stream_max_bytes", "szx_compress", "szx_compress_async",
             "szx_compress_static_async", "szx_batch_compress_plan", "szx_batch_decompress_plan",
             "szx_batch_workspace_bytes", "szx_batch_upload", "szx_batch_run", "szx_batch_autotune", "szx_batch_groups",
-            "szx_batch_destroy", "szx_header_read", "szx_decompress", "szx_decompress_async", "szx_status_string", "szx_version"]
+            "szx_batch_destroy", "szx_server_create", "szx_server_pool", "szx_server_free_bytes", "szx_server_run",
+            "szx_server_release", "szx_server_destroy", "szx_header_read", "szx_decompress", "szx_decompress_async", "szx_status_string", "szx_version"]

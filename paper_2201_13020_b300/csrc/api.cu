@@ -13,6 +13,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <mutex>
+#include <unordered_map>
 
 using namespace szx;
 
@@ -114,6 +115,49 @@ szx_status check_compress_args(const void *d_in, size_t n, szx_dtype dtype, doub
 }
 
 }  // namespace
+
+namespace {
+struct SetupKey {
+    int dev;
+    const void *kernel;
+    uint32_t smem;
+    bool operator==(const SetupKey &o) const { return dev == o.dev && kernel == o.kernel && smem == o.smem; }
+};
+struct SetupHash {
+    size_t operator()(const SetupKey &k) const {
+        return std::hash<const void *>()(k.kernel) ^ (size_t)k.dev * 0x9E3779B97F4A7C15ull ^ (size_t)k.smem << 17;
+    }
+};
+std::mutex g_setup_mu;
+std::unordered_map<SetupKey, std::pair<int, int>, SetupHash> g_setup;
+}  // namespace
+
+cudaError_t szx::launch_setup(const void *kernel, uint32_t smem, int threads, int *per_sm, int *sms) {
+    int dev = 0;
+    cudaError_t err = cudaGetDevice(&dev);
+    if (err != cudaSuccess) return err;
+    const SetupKey key{dev, kernel, smem};
+    {
+        std::lock_guard<std::mutex> lock(g_setup_mu);
+        auto it = g_setup.find(key);
+        if (it != g_setup.end()) {
+            *per_sm = it->second.first;
+            *sms = it->second.second;
+            return cudaSuccess;
+        }
+    }
+    if ((err = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
+        return err;
+    int n_sm = 0, fit = 0;
+    if ((err = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return err;
+    if ((err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, kernel, threads, smem)) != cudaSuccess) return err;
+    if (fit < 1) return cudaErrorInvalidConfiguration;
+    std::lock_guard<std::mutex> lock(g_setup_mu);
+    g_setup[key] = {fit, n_sm};
+    *per_sm = fit;
+    *sms = n_sm;
+    return cudaSuccess;
+}
 
 uint32_t szx::wait_limit_from_env(const char *name, uint32_t fallback) {
     const char *v = std::getenv(name);

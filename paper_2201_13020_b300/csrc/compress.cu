@@ -956,14 +956,11 @@ cudaError_t launch_t(const CField &one, const CompressLaunch &lc, int ctas_per_s
     constexpr uint32_t b = (uint32_t)(LPB * VPL), w = (uint32_t)Fmt<T>::w;
     const CSmem L = compress_smem(tile_blocks(b, w), b, w);
     auto kern = lc.fields ? compress_kernel<T, LPB, VPL, true> : compress_kernel<T, LPB, VPL, false>;
-    cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total);
+    // per device and kernel: the shared-memory attribute and the occupancy,
+    // set up on first use (a launch then only reads them)
+    int per_sm = 0, sms = 0;
+    cudaError_t err = launch_setup(reinterpret_cast<const void *>(kern), L.total, kCThreads, &per_sm, &sms);
     if (err != cudaSuccess) return err;
-    int dev = 0, sms = 0, per_sm = 0;
-    if ((err = cudaGetDevice(&dev)) != cudaSuccess) return err;
-    if ((err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return err;
-    if ((err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kCThreads, L.total)) != cudaSuccess)
-        return err;
-    if (per_sm < 1) return cudaErrorInvalidConfiguration;
     if (ctas_per_sm > 0 && ctas_per_sm < per_sm) per_sm = ctas_per_sm;
     const uint64_t grid = min_u64(lc.total_tiles, (uint64_t)sms * per_sm);
     kern<<<(unsigned)grid, kCThreads, L.total, stream>>>(one, lc);

@@ -11,6 +11,12 @@ namespace szx {
 // `name` (a positive integer) if set, else `fallback`.  Read on every launch.
 uint32_t wait_limit_from_env(const char *name, uint32_t fallback);
 
+// Per (device, kernel, shared-memory size), on first use: raise the kernel's
+// dynamic shared-memory limit to smem and look up how many CTAs of `threads`
+// threads fit on an SM and how many SMs the device has; later calls return the
+// cached values (a hash map under a mutex).
+cudaError_t launch_setup(const void *kernel, uint32_t smem, int threads, int *per_sm, int *sms);
+
 // Encode a 2-D TMA tensor map over `rows` rows of 128 bytes at base (32-bit
 // elements, a box of 32 x box_rows (<= 256), 128-byte swizzle).  False if
 // rows is 0 or >= 2^31, or the driver entry point is unavailable or rejects
