@@ -148,6 +148,23 @@ def time_oracle(x_host, eb, max_seconds=12.0):
             "cpu": cpu_model(), "seconds": t_c + t_d}
 
 
+def max_over_ranks(ms, world, device):
+    """The slowest rank's time (every rank gets it); a barrier precedes it in
+    the caller.  With one rank, the value itself."""
+    if world <= 1:
+        return ms
+    import torch
+    t = torch.tensor([float(ms)], device=device, dtype=torch.float64)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput_gbs(bytes_per_rank, steps, max_ms, world):
+    """Whole-job GB/s: every rank codes its own field (weak scaling), so the
+    job moves world * bytes_per_rank per step in the slowest rank's time."""
+    return world * bytes_per_rank * steps / (max_ms * 1e-3) / 1e9
+
+
 def kernel_sources_sha256():
     """Hash of the CUDA sources (names and bytes, sorted by path)."""
     import glob
@@ -530,13 +547,9 @@ def main():
     r = res.cpu().tolist()
     if r[1] != 0 or int(status.item()) != 0 or r[0] != nbytes:
         raise RuntimeError(f"device status: compress {r}, decompress {int(status.item())}")
-    if world > 1:
-        t = torch.tensor([total_ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
-
+    total_ms = max_over_ranks(total_ms, world, "cuda")
     in_bytes = n * 4
-    value = world * in_bytes * args.steps / (total_ms * 1e-3) / 1e9
+    value = job_throughput_gbs(in_bytes, args.steps, total_ms, world)
     comp_gbs = in_bytes / (statistics.median(comp_ms) * 1e-3) / 1e9
     deco_gbs = in_bytes / (statistics.median(deco_ms) * 1e-3) / 1e9
     alg_bytes = in_bytes + nbytes  # read the field + write the stream (and the reverse)
