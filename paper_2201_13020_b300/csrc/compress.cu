@@ -306,9 +306,13 @@ __device__ __forceinline__ void encode_lane(typename Fmt<T>::U (&x)[VPL], uint32
                 }
             }
         } else {
+            // the bytes below the top q are left in place: lead codes stop at
+            // min(q, 3) bytes and the packing takes bytes 0..q-1 only, so they
+            // never matter (only a decoded value, as in the check above, needs
+            // the masked word)
 #pragma unroll
             for (int m = 0; m < VPL; ++m)
-                if (FULL || m < nvalid) x[m] = (F::bits(F::sub(F::from(x[m]), mu)) >> s) & mask;
+                if (FULL || m < nvalid) x[m] = F::bits(F::sub(F::from(x[m]), mu)) >> s;
         }
     }
     const uint32_t segmask = (LPB == 32 ? kFull : ((1u << LPB) - 1u)) << (lane & ~(LPB - 1));
@@ -566,7 +570,7 @@ __global__ void __launch_bounds__(kCThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
                             timed_out = true;
                             break;
                         }
-                        __nanosleep(32);
+                        __nanosleep(256);  // a predecessor is still encoding
                         continue;
                     }
                     uint64_t v = lane <= first_p ? (wv & kValueMask) : 0ull;
