@@ -107,7 +107,7 @@ constexpr PlaneLut make_plane_lut() {
                 ++cnt;
             }
         }
-        t.v[i] = sel | (cnt << 16);
+        t.v[i] = sel | ((cnt * 8) << 16);
     }
     return t;
 }
@@ -141,13 +141,14 @@ __device__ __forceinline__ float max3_nan(float a, float b, float c) {
 
 __device__ __forceinline__ uint32_t prmt(uint32_t a, uint32_t b, uint32_t s) { return __byte_perm(a, b, s); }
 
-// OR a run of cnt <= 4 bytes (little-endian in `run`) into the zero-initialised
-// byte buffer at byte offset p.
-__device__ __forceinline__ void or_bytes(uint32_t *words, uint32_t p, uint32_t run, uint32_t cnt) {
-    const uint32_t sh = (p & 3u) * 8u;
-    uint32_t *wp = words + (p >> 2);
-    atomicOr(wp, run << sh);
-    if ((p & 3u) + cnt > 4u) atomicOr(wp + 1, __funnelshift_l(run, 0u, sh));
+// OR a run of up to 4 bytes (little-endian in `run`, zero above its length)
+// into the zero-initialised byte buffer at bit offset pb (a multiple of 8).
+__device__ __forceinline__ void or_bytes(uint32_t *words, uint32_t pb, uint32_t run) {
+    const uint64_t v = (uint64_t)run << (pb & 31u);
+    uint32_t *wp = words + (pb >> 5);
+    atomicOr(wp, (uint32_t)v);
+    const uint32_t hi = (uint32_t)(v >> 32);
+    if (hi) atomicOr(wp + 1, hi);  // OR-ing zeros would change nothing
 }
 
 // Record a failed self-check (first tile and check id).
@@ -778,19 +779,13 @@ __global__ void __launch_bounds__(kCThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
         }
 
         // ---- 2. tile totals, the aggregate for the look-back, state bits ----
-        uint32_t nn_before = 0, mid_before = 0, nn_t = 0, mid_t = 0, raw_t = 0, esc_t = 0;
-#pragma unroll
-        for (int i = 0; i < kConsumerWarps; ++i) {
-            const uint4 v = sm_w[i];
-            if (i < warp) {
-                nn_before += v.x;
-                mid_before += v.y;
-            }
-            nn_t += v.x;
-            mid_t += v.y;
-            raw_t += v.z;
-            esc_t += v.w;
-        }
+        // lane i holds warp i's totals; warp reductions give the tile's totals
+        // and the sums over the warps before this one
+        const uint4 wt = lane < kConsumerWarps ? sm_w[lane] : make_uint4(0, 0, 0, 0);
+        const uint32_t nn_t = __reduce_add_sync(kFull, wt.x), mid_t = __reduce_add_sync(kFull, wt.y);
+        const uint32_t raw_t = __reduce_add_sync(kFull, wt.z), esc_t = __reduce_add_sync(kFull, wt.w);
+        const uint32_t nn_before = __reduce_add_sync(kFull, lane < warp ? wt.x : 0u);
+        const uint32_t mid_before = __reduce_add_sync(kFull, lane < warp ? wt.y : 0u);
         const uint32_t rec_bytes = (uint32_t)pad16((uint64_t)nn_t * (b / 4 + 1) + mid_t);
         if (warp == 0) {
             if (lane == 0) {
@@ -845,14 +840,14 @@ __global__ void __launch_bounds__(kCThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
 
         // ---- 3. the record --------------------------------------------------
         uint32_t *words = reinterpret_cast<uint32_t *>(buf);
-        // every record write goes through put(): a self-checked build verifies
-        // that it lands inside the record
-        auto put = [&](uint32_t p, uint32_t run, uint32_t c) {
-            if (SZX_CHECKS && (p + 8 > L.buf_bytes || p + c > rec_bytes)) {
+        // every record write goes through put() (positions in bits, c8 = 8 x
+        // bytes): a self-checked build verifies that it lands inside the record
+        auto put = [&](uint32_t pb, uint32_t run, uint32_t c8) {
+            if (SZX_CHECKS && ((pb >> 3) + 8 > L.buf_bytes || ((pb + c8) >> 3) > rec_bytes)) {
                 report_bad(Fd->ws, tile, 1);
                 return;
             }
-            or_bytes(words, p, run, c);
+            or_bytes(words, pb, run);
         };
         if (exists && kind != kConst) {
             const uint32_t mbase = nn_t * (b / 4 + 1) + mid_before + mk_blk_excl;
@@ -868,7 +863,7 @@ __global__ void __launch_bounds__(kCThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
                     const U v = src[m];
                     const uint32_t p = mbase + (uint32_t)(sub * VPL + m) * w;
 #pragma unroll
-                    for (int h = 0; h < w / 4; ++h) put(p + 4 * h, (uint32_t)(v >> (32 * h)), 4);
+                    for (int h = 0; h < w / 4; ++h) put(8 * (p + 4 * h), (uint32_t)(v >> (32 * h)), 32);
                 }
             } else {
                 // lead codes: this lane's values are bytes [sub*VPL/4, (sub+1)*VPL/4)
@@ -883,9 +878,10 @@ __global__ void __launch_bounds__(kCThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
                 const int q = (req + s) >> 3;
                 const uint32_t n0 = (uint32_t)(tot & FM), n1 = (uint32_t)((tot >> FB) & FM),
                                n2 = (uint32_t)((tot >> (2 * FB)) & FM);
-                uint32_t pos0 = mbase + (uint32_t)(off & FM);
-                uint32_t pos1 = mbase + n0 + (uint32_t)((off >> FB) & FM);
-                uint32_t pos2 = mbase + n0 + n1 + (uint32_t)((off >> (2 * FB)) & FM);
+                // plane positions in bits
+                uint32_t pos0 = 8 * (mbase + (uint32_t)(off & FM));
+                uint32_t pos1 = 8 * (mbase + n0 + (uint32_t)((off >> FB) & FM));
+                uint32_t pos2 = 8 * (mbase + n0 + n1 + (uint32_t)((off >> (2 * FB)) & FM));
                 const uint32_t dense0 = mbase + n0 + n1 + n2 + (uint32_t)sub * VPL;
 #pragma unroll
                 for (int gq = 0; gq < VPL / 4; ++gq) {
@@ -931,11 +927,11 @@ __global__ void __launch_bounds__(kCThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
                         pos2 += e2 >> 16;
                     }
                     if (q >= 4) {
-                        const uint32_t sel = full_lane ? 0x43210u : lut[512 + dense8];
+                        const uint32_t sel = full_lane ? (0x3210u | (32u << 16)) : lut[512 + dense8];
 #pragma unroll
                         for (int j = 3; j < W / 8; ++j) {
                             if (j < q)
-                                put(dense0 + (uint32_t)(j - 3) * len + 4 * gq, prmt(Wd[j], 0, sel), sel >> 16);
+                                put(8 * (dense0 + (uint32_t)(j - 3) * len + 4 * gq), prmt(Wd[j], 0, sel), sel >> 16);
                         }
                     }
                 }
