@@ -337,6 +337,22 @@ szx_status szx_server_release(szx_server *server, uint64_t offset,
 /* Wait for the server's streams and free its resources (not the pool). */
 void szx_server_destroy(szx_server *server);
 
+/*
+ * Random access: decompress only blocks [first_block, first_block + nblocks)
+ * of the stream whose header is *h.  Every block is coded from its own values
+ * alone (Algorithm 1), and the tile index gives each tile record's offset, so
+ * only the tiles holding those blocks are read.  d_out receives
+ * min(n, (first_block + nblocks) * b) - first_block * b values, the same
+ * bits a full decompression puts at that position.  Errors as for
+ * szx_decompress_async, plus SZX_ERR_INVALID for an empty or out-of-range
+ * block range.  Asynchronous.
+ */
+szx_status szx_decompress_range_async(const void *d_in, size_t in_bytes,
+                                      const szx_header *h, size_t first_block,
+                                      size_t nblocks, void *d_out,
+                                      size_t out_capacity, uint32_t *d_status,
+                                      szx_stream_t stream);
+
 /* Human-readable name of a status code. */
 const char *szx_status_string(szx_status s);
 

@@ -11,7 +11,7 @@ import ctypes
 
 from ._lib import SZX_F32, SZX_F64, STATUS, SzxField, SzxHeader, SzxStreamField, lib
 
-__all__ = ["compress", "decompress", "compress_async", "decompress_async", "compress_bound",
+__all__ = ["compress", "decompress", "compress_async", "decompress_async", "decompress_range", "compress_bound",
            "stream_max_bytes", "header", "Batch", "batch_compress", "batch_decompress", "SzxError", "SZX_F32",
            "SZX_F64"]
 
@@ -120,6 +120,25 @@ def decompress_async(buf, h, out, status=None, stream=None):
                                       ctypes.c_void_p(out.data_ptr()), out.numel() * out.element_size(),
                                       ctypes.c_void_p(status.data_ptr() if status is not None else 0),
                                       _stream_handle(stream)), "szx_decompress_async")
+
+
+def decompress_range(buf, first_block, nblocks, h=None, out=None, status=None, stream=None):
+    """Decompress blocks [first_block, first_block + nblocks) of a stream (a
+    CUDA uint8 tensor); h: its header (read from the device if None).  Returns
+    the values of those blocks."""
+    torch = _torch()
+    if h is None:
+        h = header(buf, stream)
+    nvals = min(h.n, (first_block + nblocks) * h.block) - first_block * h.block
+    if out is None:
+        dt = torch.float32 if h.dtype == SZX_F32 else torch.float64
+        out = torch.empty(max(nvals, 0), dtype=dt, device=buf.device)
+    _check(lib().szx_decompress_range_async(ctypes.c_void_p(buf.data_ptr()), buf.numel(), ctypes.byref(h),
+                                            first_block, nblocks, ctypes.c_void_p(out.data_ptr()),
+                                            out.numel() * out.element_size(),
+                                            ctypes.c_void_p(status.data_ptr() if status is not None else 0),
+                                            _stream_handle(stream)), "szx_decompress_range_async")
+    return out
 
 
 class Batch:

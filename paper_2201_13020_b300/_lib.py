@@ -59,6 +59,8 @@ def lib():
     L.szx_header_read.argtypes = [vp, sz, ctypes.POINTER(SzxHeader), vp]
     L.szx_decompress.restype = i
     L.szx_decompress.argtypes = [vp, sz, vp, sz, ctypes.POINTER(sz), ctypes.POINTER(i), vp]
+    L.szx_decompress_range_async.restype = i
+    L.szx_decompress_range_async.argtypes = [vp, sz, ctypes.POINTER(SzxHeader), sz, sz, vp, sz, vp, vp]
     L.szx_decompress_async.restype = i
     L.szx_decompress_async.argtypes = [vp, sz, ctypes.POINTER(SzxHeader), vp, sz, vp, vp]
     pp = ctypes.POINTER(ctypes.c_void_p)
@@ -87,7 +89,7 @@ def lib():
 
 
 EXPORTED = ["szx_compress_bound", "szx_stream_max_bytes", "szx_compress", "szx_compress_async",
-            "szx_compress_static_async", "szx_batch_compress_plan", "szx_batch_decompress_plan",
+            "szx_compress_static_async", "szx_decompress_range_async", "szx_batch_compress_plan", "szx_batch_decompress_plan",
             "szx_batch_workspace_bytes", "szx_batch_upload", "szx_batch_run", "szx_batch_autotune", "szx_batch_groups",
             "szx_batch_destroy", "szx_server_create", "szx_server_pool", "szx_server_free_bytes", "szx_server_run",
             "szx_server_release", "szx_server_destroy", "szx_header_read", "szx_decompress", "szx_decompress_async", "szx_status_string", "szx_version"]

@@ -233,6 +233,25 @@ szx_status szx_decompress_async(const void *d_in, size_t in_bytes, const szx_hea
                                        d_status, true, s));
 }
 
+szx_status szx_decompress_range_async(const void *d_in, size_t in_bytes, const szx_header *h, size_t first_block,
+                                      size_t nblocks, void *d_out, size_t out_capacity, uint32_t *d_status,
+                                      szx_stream_t stream) {
+    if (!d_in || !h || !d_out) return SZX_ERR_INVALID;
+    if (!aligned16(d_in) || !aligned16(d_out)) return SZX_ERR_INVALID;
+    if (!dtype_ok(h->dtype) || !block_ok(h->block) || h->n == 0 || h->n > kMaxValues) return SZX_ERR_INVALID;
+    if (h->tile_blocks != tile_blocks(h->block, width(h->dtype))) return SZX_ERR_INVALID;
+    const Geometry g = make_geometry(h->n, h->block, width(h->dtype));
+    if (h->total_bytes > in_bytes || h->total_bytes < g.off_rec) return SZX_ERR_CORRUPT;
+    if (nblocks == 0 || first_block >= g.nb || nblocks > g.nb - first_block) return SZX_ERR_INVALID;
+    const uint64_t last = first_block + nblocks;
+    const uint64_t vals = min_u64(h->n, last * h->block) - (uint64_t)first_block * h->block;
+    if (out_capacity < vals * width(h->dtype)) return SZX_ERR_TOO_SMALL;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (d_status && cudaMemsetAsync(d_status, 0, sizeof(uint32_t), s) != cudaSuccess) return SZX_ERR_CUDA;
+    return from_cuda(launch_decompress(d_in, in_bytes, h->total_bytes, h->n, (int)h->dtype, h->block, d_out,
+                                       d_status, true, s, first_block, last));
+}
+
 szx_status szx_decompress(const void *d_in, size_t in_bytes, void *d_out, size_t out_capacity, size_t *n_out,
                           szx_dtype *dtype_out, szx_stream_t stream) {
     szx_header h;

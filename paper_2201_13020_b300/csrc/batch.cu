@@ -203,7 +203,7 @@ szx_status szx_batch_upload(szx_batch_plan *p, void *d_ws, size_t ws_bytes, uint
                 DField *d = reinterpret_cast<DField *>(host.data()) + s;
                 fill_decompress_field(d, sf.d_in, sf.header.total_bytes, sf.header.n, (int)sf.header.dtype,
                                       sf.header.block, sf.d_out, sf.d_status, true, tile0);
-                tile0 += d->g.ntiles;
+                tile0 += decompress_field_tiles(d);
             }
         }
     }

@@ -230,7 +230,7 @@ __global__ void __launch_bounds__(kDThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
             if (t >= lc.total_tiles) return;
             nf = dfield_of<BATCH>(lc, t);
             const DField *F = dfield_ptr<BATCH>(one, lc, nf);
-            ntile = (uint32_t)(t - F->tile0);
+            ntile = (uint32_t)(t - F->tile0 + F->tile_lo);
             const uint64_t *idx = reinterpret_cast<const uint64_t *>(F->in + F->g.off_index);
             n0 = idx[ntile];
             n1 = idx[ntile + 1];
@@ -560,21 +560,25 @@ __global__ void __launch_bounds__(kDThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
 
         // ---- output: full rows through the warp's buffer and a tensor store,
         // the ragged last row with plain stores ------------------------------
+        // rows of the output count from the range's first row; a warp whose
+        // rows all lie at or after it stores through the tensor map (rows past
+        // the end are clipped), one that straddles the start stores plainly
         const uint64_t wrow0 = (uint64_t)tile * 256 * RPL + (uint64_t)warp * 32 * RPL;  // warp's first row
-        const bool tma_rows = Fd->use_tma && wrow0 < Fd->rows_full;
+        const bool tma_rows = Fd->use_tma && wrow0 >= Fd->row_lo && wrow0 - Fd->row_lo < Fd->rows_full;
+        const bool wanted = kg >= Fd->blk_lo && kg < Fd->blk_hi;
         if (tma_rows) {
             // the buffer is free once the previous tile's store has read it
             if (lane == 0) bulk_wait_read_all();
             __syncwarp();
         }
-        if (exists && nvalid > 0) {
+        if (exists && wanted && nvalid > 0) {
 #pragma unroll
             for (int rr = 0; rr < RPL; ++rr) {
                 constexpr int VPR = 128 / w;  // values per row
                 const int nv = nvalid - rr * VPR;
                 if (nv <= 0) continue;
                 const uint32_t rowi = lane_row0 + rr;
-                if (Fd->use_tma && wrow0 + rowi < Fd->rows_full) {
+                if (tma_rows && wrow0 + rowi - Fd->row_lo < Fd->rows_full) {
                     uint8_t *row = wbuf + (rowi << 7);
 #pragma unroll
                     for (int c = 0; c < 8; ++c) {
@@ -585,7 +589,7 @@ __global__ void __launch_bounds__(kDThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
                         *reinterpret_cast<uint4 *>(row + ((c ^ (rowi & 7u)) << 4)) = v;
                     }
                 } else {
-                    U *dst = reinterpret_cast<U *>(Fd->out) + kg * b + sub * VPL + rr * VPR;
+                    U *dst = reinterpret_cast<U *>(Fd->out) + (kg - Fd->blk_lo) * b + sub * VPL + rr * VPR;
                     if (nv >= VPR) {
 #pragma unroll
                         for (int c = 0; c < 8; ++c) {
@@ -609,7 +613,7 @@ __global__ void __launch_bounds__(kDThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
             if (lane == 0) {
                 asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(
                                  reinterpret_cast<uint64_t>(&Fd->tmap)),
-                             "r"(0), "r"((int)wrow0), "r"(smem_addr(wbuf))
+                             "r"(0), "r"((int)(wrow0 - Fd->row_lo)), "r"(smem_addr(wbuf))
                              : "memory");
                 bulk_commit();
             }
@@ -668,7 +672,8 @@ uint64_t copy_limit_ns() { return 1000ull * wait_limit_from_env("SZX_COPY_US", 1
 }  // namespace
 
 void fill_decompress_field(DField *f, const void *in, uint64_t total_bytes, uint64_t n, int dtype, uint32_t block,
-                           void *out, uint32_t *d_status, bool check_header, uint64_t tile0) {
+                           void *out, uint32_t *d_status, bool check_header, uint64_t tile0, uint64_t blk_lo,
+                           uint64_t blk_hi) {
     DField &a = *f;
     std::memset(&a, 0, sizeof(a));
     const uint32_t w = dtype == 0 ? 4 : 8;
@@ -678,7 +683,13 @@ void fill_decompress_field(DField *f, const void *in, uint64_t total_bytes, uint
     a.g = make_geometry(n, block, w);
     a.rec_total = total_bytes - a.g.off_rec;
     a.total_bytes = total_bytes;
-    a.rows_full = n * w / 128;
+    if (blk_hi > a.g.nb) blk_hi = a.g.nb;
+    a.blk_lo = blk_lo;
+    a.blk_hi = blk_hi;
+    a.tile_lo = blk_lo / a.g.G;
+    a.row_lo = blk_lo * block * w / 128;  // b * w is a multiple of 128
+    const uint64_t range_vals = min_u64(n, blk_hi * block) - blk_lo * block;
+    a.rows_full = range_vals * w / 128;
     a.tile0 = tile0;
     a.dtype = (uint32_t)dtype;
     a.check_header = check_header ? 1u : 0u;
@@ -687,16 +698,21 @@ void fill_decompress_field(DField *f, const void *in, uint64_t total_bytes, uint
     a.use_tma = encode_row_map(&a.tmap, out, a.rows_full, box_rows) ? 1u : 0u;
 }
 
+uint64_t decompress_field_tiles(const DField *f) {
+    return f->blk_hi > f->blk_lo ? (f->blk_hi - 1) / f->g.G - f->tile_lo + 1 : 0;
+}
+
 cudaError_t launch_decompress(const void *in, uint64_t in_bytes, uint64_t total_bytes, uint64_t n, int dtype,
                               uint32_t block, void *out, uint32_t *d_status, bool check_header,
-                              cudaStream_t stream) {
+                              cudaStream_t stream, uint64_t blk_lo, uint64_t blk_hi) {
     (void)in_bytes;
     DField one;
-    fill_decompress_field(&one, in, total_bytes, n, dtype, block, out, d_status, check_header, 0);
+    fill_decompress_field(&one, in, total_bytes, n, dtype, block, out, d_status, check_header, 0, blk_lo, blk_hi);
     DecompressLaunch lc;
     lc.fields = nullptr;
     lc.nfields = 1;
-    lc.total_tiles = one.g.ntiles;
+    lc.total_tiles = decompress_field_tiles(&one);
+    if (!lc.total_tiles) return cudaSuccess;
     lc.copy_ns = copy_limit_ns();
     return ddispatch(dtype, block, one, lc, 0, stream);
 }

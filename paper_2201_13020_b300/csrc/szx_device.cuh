@@ -339,6 +339,9 @@ struct alignas(64) DField {
     uint64_t total_bytes;  // stream size (the header's)
     uint64_t rows_full;    // 128-byte output rows fully inside the output
     uint64_t tile0;        // the field's first tile in the launch's global list
+    uint64_t tile_lo;      // the first tile decoded (a block range starts there)
+    uint64_t blk_lo, blk_hi;  // blocks written: out holds values from block blk_lo on
+    uint64_t row_lo;       // blk_lo's first 128-byte row (rows of out count from it)
     uint32_t dtype;
     uint32_t check_header;  // re-check the stream header on the device
     uint32_t use_tma;

@@ -55,8 +55,14 @@ struct DField;
 
 // Fill the descriptor of one stream for a batched decompression launch (host
 // memory; the output tensor map is encoded here).
+// blk_lo, blk_hi: the blocks written (out holds values from block blk_lo on);
+// 0 and UINT64_MAX for the whole stream.
 void fill_decompress_field(DField *f, const void *in, uint64_t total_bytes, uint64_t n, int dtype, uint32_t block,
-                           void *out, uint32_t *d_status, bool check_header, uint64_t tile0);
+                           void *out, uint32_t *d_status, bool check_header, uint64_t tile0, uint64_t blk_lo = 0,
+                           uint64_t blk_hi = ~0ull);
+
+// Tiles a filled descriptor decodes.
+uint64_t decompress_field_tiles(const DField *f);
 
 // Enqueue one persistent decompression launch over nfields descriptors at
 // d_fields (device memory, 64-byte aligned; all of dtype and block).
@@ -68,6 +74,6 @@ cudaError_t launch_decompress_batch(const void *d_fields, uint32_t nfields, uint
 // szx_status codes (d_status may be null).
 cudaError_t launch_decompress(const void *in, uint64_t in_bytes, uint64_t total_bytes, uint64_t n, int dtype,
                               uint32_t block, void *out, uint32_t *d_status, bool check_header,
-                              cudaStream_t stream);
+                              cudaStream_t stream, uint64_t blk_lo = 0, uint64_t blk_hi = ~0ull);
 
 }  // namespace szx
