@@ -448,6 +448,71 @@ def run_serve(args, world, rank, local):
     return 0
 
 
+def run_dump(args, world, rank, local):
+    """Compressed dump to a host file and load back (the 512^3 f32 field, rel
+    1e-3), against a raw dump / load of the same values through the same path
+    (device-to-host copy into pinned memory, file write; and the reverse)."""
+    import tempfile
+
+    import torch
+
+    from paper_2201_13020_b300 import dump, inputs
+    torch.cuda.set_device(local)
+    x = make_field("cuda", seed=2 + rank)
+    eb = inputs.rel_to_abs(x, REL)
+    in_bytes = x.numel() * 4
+    d = args.dump_dir or tempfile.gettempdir()
+    path = os.path.join(d, f"szx_dump_{os.getpid()}.bin")
+    raw_path = path + ".raw"
+    chunk = 1 << 24  # 64 MiB of f32 per chunk
+
+    def raw_dump():
+        host = torch.empty(x.numel(), dtype=torch.float32, pin_memory=True)
+        host.copy_(x)
+        with open(raw_path, "wb") as f:
+            f.write(memoryview(host.numpy()))
+
+    def raw_load():
+        host = torch.empty(x.numel(), dtype=torch.float32, pin_memory=True)
+        with open(raw_path, "rb") as f:
+            f.readinto(memoryview(host.numpy()))
+        return host.cuda()
+
+    res = {}
+    try:
+        for name, fn in (("szx_dump", lambda: dump.dump(x, eb, path, chunk_values=chunk)),
+                         ("szx_load", lambda: dump.load(path)), ("raw_dump", raw_dump), ("raw_load", raw_load)):
+            times = []
+            for i in range(args.warmup + args.steps):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                fn()
+                torch.cuda.synchronize()
+                if i >= args.warmup:
+                    times.append(time.perf_counter() - t0)
+            res[name] = {"gbs": in_bytes / statistics.median(times) / 1e9, "ms": 1e3 * statistics.median(times)}
+        y = dump.load(path)
+        e = float((y.double() - x.double()).abs().max())
+        file_bytes = os.path.getsize(path)
+    finally:
+        for p_ in (path, raw_path):
+            if os.path.exists(p_):
+                os.remove(p_)
+    if e > eb:
+        raise RuntimeError(f"loaded values exceed the bound: {e} > {eb}")
+    if rank == 0:
+        line = {"metric": METRIC, "value": res["szx_dump"]["gbs"], "unit": "GB/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": res["szx_dump"]["ms"],
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "data": "synthetic",
+                "config": {"workload": "dump_grf512_f32_rel1e-3_chunk64MiB", "file_bytes": file_bytes,
+                           "input_bytes": in_bytes, "cr": in_bytes / file_bytes, "dir": d,
+                           "parallelism": f"replicas{world}"},
+                "arms": res, "max_abs_error": e, "eb": eb, "gpu": torch.cuda.get_device_name(local)}
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def config_block(world):
     edge = SHAPE_RUN[0]
     return {"workload": f"grf{edge}_f32_k-5/3_zero-slabs25_rel1e-3_block128", "shape": list(SHAPE_RUN),
@@ -466,9 +531,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--size", type=int, default=512, help="cube edge (default 512; smaller only for captures)")
-    ap.add_argument("--workload", default="grf512", choices=["grf512", "batch96", "serve"],
+    ap.add_argument("--workload", default="grf512", choices=["grf512", "batch96", "serve", "dump"],
                     help="grf512: the 512^3 f32 field (default); batch96: 96 mixed fields, batched vs plain; "
-                         "serve: Poisson request mix through the serving loop")
+                         "serve: Poisson request mix through the serving loop; dump: compressed dump to a file")
+    ap.add_argument("--dump-dir", default=None, help="dump: directory of the dump file (default: the temp dir)")
     ap.add_argument("--requests", type=int, default=600, help="serve: number of requests")
     ap.add_argument("--rate", type=float, default=30000.0, help="serve: mean arrivals per second")
     args = ap.parse_args()
@@ -482,6 +548,8 @@ def main():
         return run_batch96(args, world, rank, local)
     if args.workload == "serve":
         return run_serve(args, world, rank, local)
+    if args.workload == "dump":
+        return run_dump(args, world, rank, local)
 
     import numpy as np
     import torch
