@@ -513,6 +513,65 @@ def run_dump(args, world, rank, local):
     return 0
 
 
+def run_blocksweep(args, world, rank, local):
+    """Block length sweep on the 512^3 f32 field at rel 1e-3 (Sec. V-A.2's
+    study, Fig. 7, on synthetic data): per b, compress and decompress rates,
+    compression ratio, Eq. 7 PSNR and the constant-block fraction; and the
+    block length that block=0 picks."""
+    import torch
+
+    import paper_2201_13020_b300 as szx
+    from paper_2201_13020_b300 import inputs, metrics
+    torch.cuda.set_device(local)
+    x = make_field("cuda", seed=2 + rank)
+    eb = inputs.rel_to_abs(x, REL)
+    n = x.numel()
+    stream = torch.cuda.current_stream()
+    rows = {}
+    for b in (32, 64, 128, 256, 512, 1024):
+        out = torch.empty(szx.compress_bound(n, szx.SZX_F32, b), dtype=torch.uint8, device="cuda")
+        res = torch.zeros(2, dtype=torch.int64, device="cuda")
+        s0 = szx.compress(x, eb, b, out=out)
+        nbytes = s0.numel()
+        h = szx.header(out[:nbytes])
+        y = torch.empty_like(x)
+        st = torch.zeros(1, dtype=torch.int32, device="cuda")
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        tc, td = [], []
+        for i in range(args.warmup + args.steps):
+            ev[0].record(stream)
+            szx.compress_async(x, eb, b, out, res)
+            ev[1].record(stream)
+            szx.decompress_async(out[:nbytes], h, y, st)
+            ev[2].record(stream)
+            torch.cuda.synchronize()
+            if i >= args.warmup:
+                tc.append(ev[0].elapsed_time(ev[1]))
+                td.append(ev[1].elapsed_time(ev[2]))
+        if int(st.item()) or int(res[1].item()):
+            raise RuntimeError(f"block {b}: status {int(res[1].item())}/{int(st.item())}")
+        err = float((y.double() - x.double()).abs().max())
+        if err > eb:
+            raise RuntimeError(f"block {b}: error {err} > {eb}")
+        nb = -(-n // b)
+        rows[b] = {"compress_gbs": n * 4 / (statistics.median(tc) * 1e-3) / 1e9,
+                   "decompress_gbs": n * 4 / (statistics.median(td) * 1e-3) / 1e9,
+                   "cr": n * 4 / nbytes, "psnr_db": metrics.psnr(x, y),
+                   "constant_fraction": 1.0 - h.nonconst / nb, "raw_blocks": h.raw,
+                   "escalated_blocks": h.escalated}
+        del out, y
+    pick, sample_cr = metrics.choose_block(x, eb)
+    if rank == 0:
+        line = {"metric": METRIC, "value": rows[128]["compress_gbs"], "unit": "GB/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": "blocksweep_grf512_f32_rel1e-3", "parallelism": f"replicas{world}"},
+                "blocks": rows, "block0_choice": pick, "block0_sample_cr": sample_cr,
+                "gpu": torch.cuda.get_device_name(local)}
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def config_block(world):
     edge = SHAPE_RUN[0]
     return {"workload": f"grf{edge}_f32_k-5/3_zero-slabs25_rel1e-3_block128", "shape": list(SHAPE_RUN),
@@ -531,7 +590,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--size", type=int, default=512, help="cube edge (default 512; smaller only for captures)")
-    ap.add_argument("--workload", default="grf512", choices=["grf512", "batch96", "serve", "dump"],
+    ap.add_argument("--workload", default="grf512", choices=["grf512", "batch96", "serve", "dump", "blocksweep"],
                     help="grf512: the 512^3 f32 field (default); batch96: 96 mixed fields, batched vs plain; "
                          "serve: Poisson request mix through the serving loop; dump: compressed dump to a file")
     ap.add_argument("--dump-dir", default=None, help="dump: directory of the dump file (default: the temp dir)")
@@ -550,6 +609,8 @@ def main():
         return run_serve(args, world, rank, local)
     if args.workload == "dump":
         return run_dump(args, world, rank, local)
+    if args.workload == "blocksweep":
+        return run_blocksweep(args, world, rank, local)
 
     import numpy as np
     import torch

@@ -58,11 +58,16 @@ def stream_max_bytes(n, dtype=SZX_F32, block=128):
 
 
 def compress(x, eb, block=128, out=None, stream=None):
-    """Compress a contiguous CUDA tensor; returns a uint8 view of the stream."""
+    """Compress a contiguous CUDA tensor; returns a uint8 view of the stream.
+    block=0 picks the block length with metrics.choose_block (a sample of x
+    compressed with b = 64, 128 and 256)."""
     torch = _torch()
     if not x.is_cuda or not x.is_contiguous():
         raise ValueError("x must be a contiguous CUDA tensor")
     code = _dtype_code(x)
+    if block == 0:
+        from .metrics import choose_block
+        block, _ = choose_block(x, eb)
     n = x.numel()
     cap = compress_bound(n, code, block)
     if cap == 0:

@@ -144,3 +144,16 @@ def test_batch_plan_argument_checks_on_host():
     groups = (ctypes.c_int * 4)()
     assert L.szx_batch_groups(plan, groups, 4) == 2
     L.szx_batch_destroy(plan)
+
+
+@pytest.mark.gpu
+def test_block_zero_picks_a_candidate_and_round_trips():
+    from paper_2201_13020_b300 import metrics
+    x = torch.from_numpy(inputs.sinusoid_1d(1 << 20, seed=5)).cuda()
+    eb = inputs.rel_to_abs(x, 1e-3)
+    pick, ratios = metrics.choose_block(x, eb)
+    assert pick in (64, 128, 256) and ratios[pick] == max(ratios.values())
+    s = szx.compress(x, eb, 0)
+    h = szx.header(s)
+    assert h.block == pick
+    assert np.array_equal(s.cpu().numpy(), oracle.compress(x.cpu().numpy(), eb, pick))
