@@ -198,8 +198,11 @@ def run_reference(args, world, rank):
     del x
     per_step = []
     samples = []
+    # each step times the oracle on a bounded slice (about 2 s of CPU work), so
+    # that the whole run ends within a few minutes at the default step counts
+    step_s = min(args.ref_seconds, 2.0)
     for i in range(args.warmup + args.steps):
-        r = time_oracle(xh, eb, max_seconds=args.ref_seconds)
+        r = time_oracle(xh, eb, max_seconds=step_s)
         if i >= args.warmup:
             per_step.append(r)
             samples.append(r["value"])
@@ -572,6 +575,68 @@ def run_blocksweep(args, world, rank, local):
     return 0
 
 
+def run_grf384f64(args, world, rank, local):
+    """The f64 field: 384^3, spectrum |k|^-11/3 plus 1e-6 white noise; REL
+    1e-4 and 1e-6, block 128 and 256: compress and decompress rates, CR and
+    the HBM fraction of the algorithmic bytes."""
+    import torch
+
+    import paper_2201_13020_b300 as szx
+    from paper_2201_13020_b300 import inputs
+    torch.cuda.set_device(local)
+    g = inputs.grf_3d((384, 384, 384), -11.0 / 3.0, seed=3 + rank, device="cuda", dtype=torch.float64)
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(33 + rank)
+    x = (g + 1e-6 * torch.randn(g.shape, generator=gen, device="cuda", dtype=torch.float64)).reshape(-1)
+    del g
+    n = x.numel()
+    in_bytes = n * 8
+    stream = torch.cuda.current_stream()
+    peak, peak_kind = peaks()
+    rows = {}
+    for rel in (1e-4, 1e-6):
+        eb = inputs.rel_to_abs(x, rel)
+        for b in (128, 256):
+            out = torch.empty(szx.compress_bound(n, szx.SZX_F64, b), dtype=torch.uint8, device="cuda")
+            res = torch.zeros(2, dtype=torch.int64, device="cuda")
+            nbytes = szx.compress(x, eb, b, out=out).numel()
+            h = szx.header(out[:nbytes])
+            y = torch.empty_like(x)
+            st = torch.zeros(1, dtype=torch.int32, device="cuda")
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            tc, td = [], []
+            for i in range(args.warmup + args.steps):
+                ev[0].record(stream)
+                szx.compress_async(x, eb, b, out, res)
+                ev[1].record(stream)
+                szx.decompress_async(out[:nbytes], h, y, st)
+                ev[2].record(stream)
+                torch.cuda.synchronize()
+                if i >= args.warmup:
+                    tc.append(ev[0].elapsed_time(ev[1]))
+                    td.append(ev[1].elapsed_time(ev[2]))
+            if int(st.item()) or int(res[1].item()) or float((x - y).abs().max()) > eb:
+                raise RuntimeError(f"rel {rel} block {b}: failed")
+            mc, md = statistics.median(tc), statistics.median(td)
+            alg = in_bytes + nbytes
+            rows[f"rel{rel:g}_b{b}"] = {"compress_gbs": in_bytes / (mc * 1e-3) / 1e9,
+                                         "decompress_gbs": in_bytes / (md * 1e-3) / 1e9,
+                                         "cr": in_bytes / nbytes,
+                                         "hbm_frac_compress": alg / (mc * 1e-3) / 1e9 / peak,
+                                         "hbm_frac_decompress": alg / (md * 1e-3) / 1e9 / peak,
+                                         "escalated_blocks": h.escalated, "raw_blocks": h.raw}
+            del out, y
+    if rank == 0:
+        line = {"metric": METRIC, "value": rows["rel0.0001_b128"]["compress_gbs"], "unit": "GB/s",
+                "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": "grf384_f64_k-11/3_noise1e-6", "peak": f"hbm_gbs {peak} of {peak_kind}",
+                           "parallelism": f"replicas{world}"},
+                "rows": rows, "gpu": torch.cuda.get_device_name(local)}
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def config_block(world):
     edge = SHAPE_RUN[0]
     return {"workload": f"grf{edge}_f32_k-5/3_zero-slabs25_rel1e-3_block128", "shape": list(SHAPE_RUN),
@@ -590,7 +655,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--size", type=int, default=512, help="cube edge (default 512; smaller only for captures)")
-    ap.add_argument("--workload", default="grf512", choices=["grf512", "batch96", "serve", "dump", "blocksweep"],
+    ap.add_argument("--workload", default="grf512", choices=["grf512", "batch96", "serve", "dump", "blocksweep", "grf384f64"],
                     help="grf512: the 512^3 f32 field (default); batch96: 96 mixed fields, batched vs plain; "
                          "serve: Poisson request mix through the serving loop; dump: compressed dump to a file")
     ap.add_argument("--dump-dir", default=None, help="dump: directory of the dump file (default: the temp dir)")
@@ -611,6 +676,8 @@ def main():
         return run_dump(args, world, rank, local)
     if args.workload == "blocksweep":
         return run_blocksweep(args, world, rank, local)
+    if args.workload == "grf384f64":
+        return run_grf384f64(args, world, rank, local)
 
     import numpy as np
     import torch

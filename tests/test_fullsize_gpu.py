@@ -82,3 +82,40 @@ def test_512cubed_f32_sampled_tiles(variant, rel):
     assert int(h[7]) == stream.size
     del g, x, y, s, d
     torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("rel,block", [(1e-4, 128), (1e-6, 128), (1e-4, 256), (1e-6, 256)])
+def test_384cubed_f64_sampled_tiles(rel, block):
+    """The f64 field: 384^3, spectrum |k|^-11/3 plus 1e-6 white noise."""
+    torch.cuda.empty_cache()
+    g = inputs.grf_3d((384, 384, 384), -11.0 / 3.0, seed=3, device="cuda", dtype=torch.float64)
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(33)
+    x = (g + 1e-6 * torch.randn(g.shape, generator=gen, device="cuda", dtype=torch.float64)).reshape(-1)
+    del g
+    eb = inputs.rel_to_abs(x, rel)
+    s = szx.compress(x, eb, block)
+    y = szx.decompress(s)
+    e = oracle.error_bound(eb, oracle.F64)
+    d = (x - y).abs()
+    assert float(d.max()) <= e * (1 + 2 ** -40)
+    near = torch.nonzero(d > e * (1 - 2 ** -40)).flatten()
+    if near.numel():
+        assert exact_abs_diff_le(x[near].cpu().numpy(), y[near].cpu().numpy(), e).all()
+    stream = s.cpu().numpy()
+    x_host = x.cpu().numpy()
+    n = x_host.size
+    G = max(8, 32768 // (block * 8))
+    ntiles = -(-(-(-n // block)) // G)
+    rng = np.random.default_rng(1)
+    tiles = sorted(set([0, ntiles - 1] + rng.choice(ntiles, size=12, replace=False).tolist()))
+    y_host = y.cpu().numpy()
+    for t in tiles:
+        ref = tile_slice_parity(x_host, stream, t, block, 8, eb)
+        yr = oracle.decompress(ref)
+        v0 = t * G * block
+        assert np.array_equal(yr.view(np.uint64), y_host[v0:v0 + yr.size].view(np.uint64))
+    h = np.frombuffer(stream[:64].tobytes(), dtype=np.uint64)
+    assert int(h[7]) == stream.size
+    del x, y, s, d
+    torch.cuda.empty_cache()
