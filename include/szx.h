@@ -20,9 +20,11 @@
  * Conventions for every call below:
  *   - Pointers named d_* are CUDA device pointers on the current device and
  *     must be 16-byte aligned; the caller allocates and owns all of them.
- *     Nothing in this library allocates device memory in the compress or
- *     decompress calls; their scratch space is the tail of the caller's
- *     output buffer (see szx_compress_bound).
+ *     The compress calls keep their scratch in the tail of the caller's
+ *     output buffer (see szx_compress_bound) and allocate nothing; the only
+ *     device allocation of the codec calls is the small array of status
+ *     words that the synchronous szx_decompress takes once per device, on its
+ *     first call there (szx_compress_static_async allocates nothing at all).
  *   - `stream` is a cudaStream_t (0 = the legacy default stream).  All device
  *     work is enqueued on it in order.
  *   - Values are IEEE 754 binary32 (SZX_F32) or binary64 (SZX_F64), little
@@ -172,8 +174,9 @@ szx_status szx_header_read(const void *d_in, size_t in_bytes, szx_header *h,
  * *dtype_out receive the header's values (either may be NULL).  Every read
  * of the stream is bounds-checked on the device; a malformed stream returns
  * SZX_ERR_CORRUPT.  Synchronous.  The device status word it uses is one of a
- * fixed set inside the library (no allocation); concurrent calls from up to
- * 256 host threads get distinct words.
+ * set of 256 that the library allocates on its first call on each device and
+ * keeps until exit; concurrent calls from up to 256 host threads get distinct
+ * words.
  */
 szx_status szx_decompress(const void *d_in, size_t in_bytes, void *d_out,
                           size_t out_capacity, size_t *n_out,
