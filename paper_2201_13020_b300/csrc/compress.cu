@@ -12,34 +12,38 @@
 // lanes for f32, b = 128).  The serial previous-value dependency stays inside
 // a lane except at lane boundaries.
 //
-// Per CTA: a ring of three tile buffers and three roles.  A producer warp
+// Per CTA: a ring of three tile buffers and three roles.  A producer thread
 // takes tickets and copies tiles in with the TMA unit (2-D tensor copy, rows
 // of 128 B, 128-byte swizzle, so that each lane reads its row without bank
 // conflicts); eight consumer warps encode a tile and build its record in
 // place; a storer warp places and stores records.  The roles hand stages to
-// each other through mbarriers (full / ready / empty), so encoding never waits
-// for a look-back or a store.  Per tile:
-//   1. block statistics (Algorithm 1): NaN-propagating min/max per lane,
-//      reduced over the block's lanes with shuffles; mu, r, the exact constant
-//      test, reqBits (Eq. 4), the Eq. 5 shift and truncation.  The per-value
-//      bound check is skipped when a block-level bound proves it passes
-//      (see bound_check_needed); otherwise a fast test runs and an exact slow
-//      path re-checks a block that fails it, raising reqBits while a value
-//      exceeds e.  Then the identical-leading-byte codes against the previous
-//      value and the block's mid-byte count; the truncated words stay in
-//      registers;
-//   2. warp 0 scans the tile's blocks (non-constant rank, mid-byte offset)
-//      and publishes the tile's record size; the tile buffer is cleared and
-//      reused for the record;
+// each other through mbarriers (full / encoded / ready / empty), so encoding
+// never waits for a look-back or a store, and every wait is bounded.  The
+// same kernel serves one field (its descriptor is a kernel parameter) and
+// batches (a table of descriptors in device memory, BATCH).  Per tile:
+//   1. each consumer warp loads its rows and clears them (the buffer becomes
+//      the record), then encodes in registers -- block statistics
+//      (Algorithm 1): NaN-propagating min/max per lane, reduced over the
+//      block's lanes with shuffles; mu, r, the exact constant test, reqBits
+//      (Eq. 4), the Eq. 5 shift and truncation.  The per-value bound check is
+//      skipped when a block-level bound proves it passes (see
+//      bound_check_needed); otherwise a fast test runs and an exact slow path
+//      re-checks a block that fails it, raising reqBits while a value exceeds
+//      e.  Then the identical-leading-byte codes against the previous value
+//      and the lanes' mid-byte counts.  The warp writes its blocks' mu values
+//      and publishes its totals;
+//   2. the warps meet once (an mbarrier); warp reductions of the warps'
+//      totals give every block its rank and mid-byte offset; warp 0 publishes
+//      the tile's record size for the look-back and writes the state bits;
 //   3. lanes write lead codes, reqBits bytes and the mid-byte planes (plane j
 //      = byte j of every value whose code is <= j, ascending index): a 4x4
 //      byte transpose of four values gives their byte-j word, a 256-entry
 //      table compacts the selected bytes, and shared-memory OR writes place the
-//      run at its byte offset;
-//   4. the storer finishes the look-back, writes the tile index entry, the
-//      tile's state bits and mu values, and bulk-stores the record (TMA,
-//      cp.async.bulk) to its offset; once the store has read the buffer, the
-//      producer refills it with the CTA's next tile.
+//      run at its bit offset;
+//   4. the storer finishes the look-back, writes the tile index entry and
+//      bulk-stores the record (cp.async.bulk) to its offset; once the store
+//      has read the buffer, the producer refills it.  The last CTA to finish
+//      writes each field's header.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 

@@ -3,18 +3,21 @@
 // Persistent CTAs decode tiles of G blocks.  The tile index written by the
 // compressor gives each record's offset, so tiles decode independently: no
 // device-wide scan is left for decompression (the paper's GPU decoder, Sec.
-// V-B, runs a prefix scan of the mid-byte counts first).  Per CTA, three warp
-// roles share a ring of three stage buffers through mbarriers:
+// V-B, runs a prefix scan of the mid-byte counts first).  Per CTA, a producer
+// thread and eight decoding warps share two stage buffers through mbarriers
+// (full / consumed):
 //   producer (one thread): per tile, bulk-copies (cp.async.bulk) the record,
 //     the tile's mu values and a 16-byte-aligned window of its state bits into
 //     a stage; the tile index entries are loaded one tile ahead, so no global
 //     latency sits between two copies;
-//   eight decoding warps: decode the stage's record into registers, then
-//     write the values back into the same stage buffer as the output tile, in
-//     the 128-byte-swizzled row layout of the TMA tensor store;
-//   storer (one thread): stores the tile with a 2-D TMA tensor store (rows of
-//     128 bytes), then frees the stage for the producer.
-// The decoders therefore touch global memory only for the ragged last row.
+//   eight decoding warps: decode the stage's record into registers, release
+//     the stage, then write their rows into a buffer of their own in the
+//     128-byte-swizzled layout of the TMA tensor store and issue that store
+//     (one 2-D box of 32 rows per warp).  The ragged last row goes out with
+//     plain stores.
+// The same kernel serves a single stream (its descriptor is a kernel
+// parameter) and batches (a table of descriptors in device memory, BATCH),
+// and decodes a block range for random access.
 //
 // Work layout as in the compressor: every lane owns 128 contiguous output
 // bytes (32 f32 or 16 f64 values); a block of b values spans LPB = b / VPL
@@ -22,21 +25,20 @@
 //   1. every lane ranks its block among the tile's non-constant blocks (a
 //      popcount of the tile's state bits), reads its reqBits byte and lead
 //      codes, checks them, and counts its mid bytes;
-//   2. after one barrier every warp scans the blocks' counts into mid-byte
-//      offsets and checks the total against the record size, so that every
-//      later read is inside the record;
+//   2. each warp scans its lanes' counts; after one barrier, the warps' totals
+//      give every block its mid-byte offset, and the total is checked against
+//      the record size, so that every later read is inside the record;
 //   3. every lane rebuilds its values: for each group of four values and each
 //      byte plane, the lane's run of own bytes is read with two aligned word
-//      loads and a funnel shift and spread to the owning values with a
-//      table-driven byte permute.  A leading byte (identical to the previous
-//      value's) is resolved per plane: inside a lane a byte permute copies the
-//      nearest earlier owner forward, and the carry into a lane is the last
-//      own byte of the nearest lower lane of the block that owns one (a ballot
-//      and a shuffle) -- the paper's index propagation (Sec. V-B) in one step
-//      per plane.  A byte transpose turns planes back into words; then
-//      v' = t << s and d' = RN(v' + mu);
-//   4. after a second barrier (the record is no longer read) the values go to
-//      the stage buffer and the storer takes over.
+//      loads and a funnel shift, and one table-driven byte permute both
+//      spreads it to the owning values and copies a leading byte (identical
+//      to the previous value's) forward from the nearest earlier owner, or
+//      from the carry into the lane -- the last own byte of the nearest lower
+//      lane of the block that owns one (a ballot and a shuffle).  This is the
+//      paper's index propagation (Sec. V-B) in one step per plane.  A byte
+//      transpose turns planes back into words; then v' = t << s and
+//      d' = RN(v' + mu);
+//   4. the warp stores its rows (step above).
 #include <cstring>
 #include <type_traits>
 

@@ -108,25 +108,6 @@ __device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
 
 __host__ __device__ __forceinline__ uint64_t min_u64(uint64_t a, uint64_t b) { return a < b ? a : b; }
 
-__device__ __forceinline__ int32_t warp_min(int32_t v) { return __reduce_min_sync(kFull, v); }
-__device__ __forceinline__ int32_t warp_max(int32_t v) { return __reduce_max_sync(kFull, v); }
-__device__ __forceinline__ int64_t warp_min(int64_t v) {
-#pragma unroll
-    for (int d = 16; d > 0; d >>= 1) {
-        int64_t o = __shfl_xor_sync(kFull, v, d);
-        v = o < v ? o : v;
-    }
-    return v;
-}
-__device__ __forceinline__ int64_t warp_max(int64_t v) {
-#pragma unroll
-    for (int d = 16; d > 0; d >>= 1) {
-        int64_t o = __shfl_xor_sync(kFull, v, d);
-        v = o > v ? o : v;
-    }
-    return v;
-}
-
 // Exclusive prefix sum over the warp; *total receives the warp's sum.
 template <typename V>
 __device__ __forceinline__ V warp_exclusive_scan(V v, V *total) {
@@ -162,18 +143,6 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t by
         "mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(smem_addr(bar)),
         "r"(bytes)
         : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(smem_addr(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
 }
 
 __device__ __forceinline__ uint64_t globaltimer_ns() {
