@@ -200,7 +200,8 @@ def _upload(plan, device, results, stream):
 
 
 def batch_compress(xs, ebs, blocks=128, outs=None, stream=None):
-    """Plan and upload the compression of CUDA tensors xs (one bound each).
+    """Plan and upload the compression of CUDA tensors xs (one bound each;
+    a block of 0 is chosen per field by metrics.choose_block).
 
     Returns (batch, outs, results): outs are uint8 buffers of
     stream_max_bytes each; after batch.run() and a synchronisation, field i's
@@ -210,6 +211,10 @@ def batch_compress(xs, ebs, blocks=128, outs=None, stream=None):
     k = len(xs)
     if isinstance(blocks, int):
         blocks = [blocks] * k
+    if any(b == 0 for b in blocks):
+        # block=0: each such field's block length from a compressed sample
+        from .metrics import choose_block
+        blocks = [choose_block(x, eb)[0] if b == 0 else b for x, eb, b in zip(xs, ebs, blocks)]
     if outs is None:
         outs = [torch.empty(stream_max_bytes(x.numel(), _dtype_code(x), bk), dtype=torch.uint8, device=x.device)
                 for x, bk in zip(xs, blocks)]

@@ -157,3 +157,18 @@ def test_block_zero_picks_a_candidate_and_round_trips():
     h = szx.header(s)
     assert h.block == pick
     assert np.array_equal(s.cpu().numpy(), oracle.compress(x.cpu().numpy(), eb, pick))
+
+
+@pytest.mark.gpu
+def test_batch_block_zero_resolves_per_field():
+    from paper_2201_13020_b300 import metrics
+    fields = _fields()[:3]
+    xs = [torch.from_numpy(np.ascontiguousarray(x)).cuda() for x, _, _ in fields]
+    ebs = [eb for _, eb, _ in fields]
+    batch, outs, results = szx.batch_compress(xs, ebs, 0)
+    batch.run()
+    torch.cuda.synchronize()
+    for i, (x, eb, _) in enumerate(fields):
+        pick, _ = metrics.choose_block(xs[i], eb)
+        n = int(results[2 * i].item())
+        assert np.array_equal(outs[i][:n].cpu().numpy(), oracle.compress(x, eb, pick))
