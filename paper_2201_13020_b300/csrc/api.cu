@@ -6,6 +6,7 @@
 // CPU fallback: if the kernels cannot run, the call returns SZX_ERR_CUDA.
 #include "szx.h"
 #include "szx_device.cuh"
+#include "szx_host.h"
 #include "szx_launch.h"
 
 #include <atomic>
@@ -21,25 +22,9 @@ namespace {
 
 constexpr uint64_t kMaxValues = 1ull << 40;
 
-bool block_ok(uint32_t b) { return b >= 32 && b <= 1024 && (b & (b - 1)) == 0; }
 bool dtype_ok(szx_dtype d) { return d == SZX_F32 || d == SZX_F64; }
 uint32_t width(szx_dtype d) { return d == SZX_F32 ? 4u : 8u; }
-bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
-uint64_t align256(uint64_t x) { return (x + 255) & ~uint64_t(255); }
-
-// The bound actually used: f32 takes the largest float <= eb.
-uint64_t bound_bits(double eb, szx_dtype d) {
-    if (d == SZX_F64) {
-        uint64_t u;
-        std::memcpy(&u, &eb, 8);
-        return u;
-    }
-    float f = static_cast<float>(eb);
-    if (static_cast<double>(f) > eb) f = std::nextafterf(f, 0.0f);
-    uint32_t u;
-    std::memcpy(&u, &f, 4);
-    return u;
-}
+uint64_t align256(uint64_t x) { return align_up(x, 256); }
 
 uint64_t stream_max(uint64_t n, uint32_t b, uint32_t w) {
     const Geometry g = make_geometry(n, b, w);

@@ -16,6 +16,7 @@
 // streams it writes are the same either way.
 #include "szx.h"
 #include "szx_device.cuh"
+#include "szx_host.h"
 #include "szx_launch.h"
 
 #include <algorithm>
@@ -27,23 +28,6 @@
 using namespace szx;
 
 namespace {
-
-uint64_t align_up(uint64_t x, uint64_t a) { return (x + a - 1) / a * a; }
-bool block_ok(uint32_t b) { return b >= 32 && b <= 1024 && (b & (b - 1)) == 0; }
-bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
-
-uint64_t bound_bits(double eb, szx_dtype d) {
-    if (d == SZX_F64) {
-        uint64_t u;
-        std::memcpy(&u, &eb, 8);
-        return u;
-    }
-    float f = static_cast<float>(eb);
-    if (static_cast<double>(f) > eb) f = std::nextafterf(f, 0.0f);
-    uint32_t u;
-    std::memcpy(&u, &f, 4);
-    return u;
-}
 
 struct Group {
     int dtype;

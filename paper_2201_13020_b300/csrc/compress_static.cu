@@ -22,6 +22,7 @@
 // threads) race on it; callers must order them.
 #include "szx.h"
 #include "szx_device.cuh"
+#include "szx_host.h"
 #include "szx_launch.h"
 
 #include <cmath>
@@ -56,29 +57,14 @@ szx_status static_ws(void **out) {
     return SZX_OK;
 }
 
-uint64_t bound_bits_of(double eb, szx_dtype d) {
-    if (d == SZX_F64) {
-        uint64_t u;
-        std::memcpy(&u, &eb, 8);
-        return u;
-    }
-    float f = static_cast<float>(eb);
-    if (static_cast<double>(f) > eb) f = std::nextafterf(f, 0.0f);
-    uint32_t u;
-    std::memcpy(&u, &f, 4);
-    return u;
-}
-
 }  // namespace
 
 extern "C" szx_status szx_compress_static_async(const void *d_in, size_t n, szx_dtype dtype, double eb,
                                                 uint32_t block, void *d_out, size_t out_capacity,
                                                 uint64_t *d_result, szx_stream_t stream) {
-    if (!d_in || !d_out || (dtype != SZX_F32 && dtype != SZX_F64)) return SZX_ERR_INVALID;
-    if (block < 32 || block > 1024 || (block & (block - 1)) != 0) return SZX_ERR_INVALID;
+    if (!d_in || !d_out || (dtype != SZX_F32 && dtype != SZX_F64) || !block_ok(block)) return SZX_ERR_INVALID;
     if (!(eb > 0.0) || !std::isfinite(eb)) return SZX_ERR_INVALID;
-    if ((reinterpret_cast<uintptr_t>(d_in) & 15u) || (reinterpret_cast<uintptr_t>(d_out) & 15u))
-        return SZX_ERR_INVALID;
+    if (!aligned16(d_in) || !aligned16(d_out)) return SZX_ERR_INVALID;
     const size_t smax = szx_stream_max_bytes(n, dtype, block);
     if (!smax) return SZX_ERR_INVALID;  // n == 0 or n above the library's limit
     const uint32_t w = dtype == SZX_F32 ? 4u : 8u;
@@ -88,7 +74,7 @@ extern "C" szx_status szx_compress_static_async(const void *d_in, size_t n, szx_
     void *ws = nullptr;
     const szx_status st = static_ws(&ws);
     if (st != SZX_OK) return st;
-    const cudaError_t e = launch_compress_ws(d_in, n, (int)dtype, bound_bits_of(eb, dtype), block, d_out, ws,
+    const cudaError_t e = launch_compress_ws(d_in, n, (int)dtype, bound_bits(eb, dtype), block, d_out, ws,
                                              d_result, (cudaStream_t)stream);
     return e == cudaSuccess ? SZX_OK : SZX_ERR_CUDA;
 }
