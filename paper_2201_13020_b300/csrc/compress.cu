@@ -456,7 +456,7 @@ __global__ void __launch_bounds__(kCThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
     __shared__ __align__(8) uint64_t full[kStages], encoded[kStages], ready[kStages], empty[kStages];
     // per stage: the field and its local tile (0xFFFFFFFF: no more tiles)
     __shared__ uint32_t st_field[kStages], st_tile[kStages], st_nn[kStages], st_nraw[kStages], st_nesc[kStages],
-        st_rec[kStages], st_fail[kStages];
+        st_rec[kStages];
 
     // the 128-byte swizzle of the tensor copy needs 1024-byte aligned buffers
     uint8_t *smem = smem_raw + ((1024u - (smem_addr(smem_raw) & 1023u)) & 1023u);
@@ -482,7 +482,7 @@ __global__ void __launch_bounds__(kCThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
         for (int i = 0; i < kStages; ++i) {
             st_tile[i] = 0xFFFFFFFFu;
             st_field[i] = 0;
-            st_nn[i] = st_nraw[i] = st_nesc[i] = st_rec[i] = st_fail[i] = 0;
+            st_nn[i] = st_nraw[i] = st_nesc[i] = st_rec[i] = 0;
         }
     }
     __syncthreads();
@@ -508,7 +508,6 @@ __global__ void __launch_bounds__(kCThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
             const uint32_t tile = more ? (uint32_t)(t - F->tile0) : 0xFFFFFFFFu;
             st_field[st] = f;
             st_tile[st] = tile;
-            st_fail[st] = 0;
             st_nesc[st] = 0;
             const uint64_t row0 = (uint64_t)tile * 256 * RPL;
             if (more && F->use_tma && row0 < F->rows_full) {
@@ -589,11 +588,6 @@ __global__ void __launch_bounds__(kCThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
             if (lane == 0) {
                 st_relaxed_u64(&lookback[tile], kFlagPrefix | (excl + rec_bytes));
                 Workspace *ws = F->ws;
-                if (st_fail[st]) {
-                    atomicOr(&ws->err, kErrTmaTimeout);
-                    atomicAdd(&ws->tma_timeouts, 1u);
-                    atomicCAS(&ws->first_tma_tile, 0u, tile + 1);
-                }
                 if (timed_out) {
                     atomicOr(&ws->err, kErrTimeout);
                     atomicAdd(&ws->lookback_timeouts, 1ull);

@@ -255,11 +255,11 @@ struct Workspace {
     uint32_t ticket;  // next tile ticket (tiles are processed in ticket order)
     uint32_t done;    // tiles finished
     uint32_t err;     // kErr* bits
-    uint32_t tma_timeouts;  // tiles whose input copy did not complete
+    uint32_t reserved0;     // zero (a copy that does not complete sets kErrTmaTimeout in err)
     unsigned long long nn, nraw, nesc;
     unsigned long long result[2];  // stream bytes, status (written by the last tile)
     unsigned long long lookback_timeouts;  // tiles whose look-back gave up
-    uint32_t first_tma_tile;  // 1 + the first tile whose copy timed out (0: none)
+    uint32_t reserved1;       // zero
     uint32_t first_lb_tile;   // 1 + the first tile whose look-back timed out
     uint32_t first_bad_tile;  // 1 + the first tile that failed a self-check
     uint32_t bad_code;        // which self-check failed

@@ -119,3 +119,44 @@ def test_384cubed_f64_sampled_tiles(rel, block):
     assert int(h[7]) == stream.size
     del x, y, s, d
     torch.cuda.empty_cache()
+
+
+def test_record_sizes_change_tile_to_tile():
+    """Each tile of 8192 values gets its own noise level (1e-6 to 1 against a bound of
+    1e-5), so nearly constant tiles and nearly incompressible ones follow each other in
+    random order: every CTA handles dozens of tiles whose records, of very different
+    sizes, pass through its shared-memory record buffer and wrap around its end."""
+    torch.cuda.empty_cache()
+    n, per_tile = 1 << 26, 64 * 128
+    ntiles = n // per_tile
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(41)
+    level = 10.0 ** (-6.0 * torch.rand(ntiles, generator=gen, device="cuda"))
+    x = torch.linspace(0.0, 1.0, n, device="cuda") + \
+        level.repeat_interleave(per_tile) * torch.randn(n, generator=gen, device="cuda")
+    eb = 1e-5
+    s = szx.compress(x, eb)
+    y = szx.decompress(s)
+    e = oracle.error_bound(eb, oracle.F32)
+    d = (x.double() - y.double()).abs()
+    assert float(d.max()) <= e * (1 + 2 ** -20)
+    near = torch.nonzero(d > e * (1 - 2 ** -20)).flatten()
+    if near.numel():
+        assert exact_abs_diff_le(x[near].cpu().numpy(), y[near].cpu().numpy(), e).all()
+    stream = s.cpu().numpy()
+    nb = n // 128
+    off_index = 64 + ss.pad16(-(-nb // 8)) + ss.pad16(nb * 4)
+    idx = stream[off_index:off_index + 8 * (ntiles + 1)].view(np.uint64).astype(np.int64)
+    sizes = np.diff(idx)
+    assert sizes.min() < 2048 and sizes.max() > 24576, (sizes.min(), sizes.max())
+    x_host, y_host = x.cpu().numpy(), y.cpu().numpy()
+    rng = np.random.default_rng(5)
+    tiles = sorted(set([0, ntiles - 1, int(sizes.argmax()), int(sizes.argmin())] +
+                       rng.choice(ntiles, size=20, replace=False).tolist()))
+    for t in tiles:
+        ref = tile_slice_parity(x_host, stream, t, 128, 4, eb)
+        yr = oracle.decompress(ref)
+        v0 = t * per_tile
+        assert np.array_equal(yr.view(np.uint32), y_host[v0:v0 + yr.size].view(np.uint32))
+    del x, y, s, d
+    torch.cuda.empty_cache()
