@@ -148,10 +148,11 @@ __device__ __forceinline__ uint32_t prmt(uint32_t a, uint32_t b, uint32_t s) { r
 // OR a run of up to 4 bytes (little-endian in `run`, zero above its length)
 // into the zero-initialised byte buffer at bit offset pb (a multiple of 8).
 __device__ __forceinline__ void or_bytes(uint32_t *words, uint32_t pb, uint32_t run) {
-    const uint64_t v = (uint64_t)run << (pb & 31u);
+    // the two words of (uint64_t)run << (pb mod 32), by funnel shifts (which
+    // take the shift modulo 32 themselves)
     uint32_t *wp = words + (pb >> 5);
-    atomicOr(wp, (uint32_t)v);
-    const uint32_t hi = (uint32_t)(v >> 32);
+    atomicOr(wp, __funnelshift_l(0u, run, pb));
+    const uint32_t hi = __funnelshift_l(run, 0u, pb);
     if (hi) atomicOr(wp + 1, hi);  // OR-ing zeros would change nothing
 }
 
