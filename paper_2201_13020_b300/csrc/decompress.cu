@@ -4,12 +4,19 @@
 // compressor gives each record's offset, so tiles decode independently: no
 // device-wide scan is left for decompression (the paper's GPU decoder, Sec.
 // V-B, runs a prefix scan of the mid-byte counts first).  Per CTA, a producer
-// thread and eight decoding warps share two stage buffers through mbarriers
-// (full / consumed):
+// thread, an indexing warp and eight decoding warps share two stage buffers
+// through mbarriers (full / indexed / consumed):
 //   producer (one thread): per tile, bulk-copies (cp.async.bulk) the record,
 //     the tile's mu values and a 16-byte-aligned window of its state bits into
 //     a stage; the tile index entries are loaded one tile ahead, so no global
 //     latency sits between two copies;
+//   indexing warp: per stage, ranks every block among the tile's non-constant
+//     blocks (a popcount of the state bits), reads its reqBits byte and lead
+//     codes, checks them, counts its mid bytes, and scans the counts into
+//     each block's mid-byte offset; the total is checked against the record
+//     size (and the pad bytes against zero), so that every later read is
+//     inside the record.  It writes a block table (offset, rank, reqBits)
+//     and the stage's verdict, one stage ahead of the decoders;
 //   eight decoding warps: decode the stage's record into registers, release
 //     the stage, then write their rows into a buffer of their own in the
 //     128-byte-swizzled layout of the TMA tensor store and issue that store
@@ -21,24 +28,16 @@
 //
 // Work layout as in the compressor: every lane owns 128 contiguous output
 // bytes (32 f32 or 16 f64 values); a block of b values spans LPB = b / VPL
-// adjacent lanes.  Per tile:
-//   1. every lane ranks its block among the tile's non-constant blocks (a
-//      popcount of the tile's state bits), reads its reqBits byte and lead
-//      codes, checks them, and counts its mid bytes;
-//   2. each warp scans its lanes' counts; after one barrier, the warps' totals
-//      give every block its mid-byte offset, and the total is checked against
-//      the record size, so that every later read is inside the record;
-//   3. every lane rebuilds its values: for each group of four values and each
-//      byte plane, the lane's run of own bytes is read with two aligned word
-//      loads and a funnel shift, and one table-driven byte permute both
-//      spreads it to the owning values and copies a leading byte (identical
-//      to the previous value's) forward from the nearest earlier owner, or
-//      from the carry into the lane -- the last own byte of the nearest lower
-//      lane of the block that owns one (a ballot and a shuffle).  This is the
-//      paper's index propagation (Sec. V-B) in one step per plane.  A byte
-//      transpose turns planes back into words; then v' = t << s and
-//      d' = RN(v' + mu);
-//   4. the warp stores its rows (step above).
+// adjacent lanes.  Every lane reads its block's table entry and its own lead
+// codes and rebuilds its values: for each group of four values and each byte
+// plane, the lane's run of own bytes is read with two aligned word loads and
+// a funnel shift, and one table-driven byte permute both spreads it to the
+// owning values and copies a leading byte (identical to the previous
+// value's) forward from the nearest earlier owner, or from the carry into
+// the lane -- the last own byte of the nearest lower lane of the block that
+// owns one (a ballot and a shuffle).  This is the paper's index propagation
+// (Sec. V-B) in one step per plane.  A byte transpose turns planes back into
+// words; then v' = t << s and d' = RN(v' + mu).
 #include <cstring>
 #include <type_traits>
 
@@ -132,16 +131,17 @@ constexpr int kDStages = 2;
 constexpr int kDConsumers = kThreads;             // 8 decoding warps
 constexpr int kDWarps = kDConsumers / 32;
 constexpr int kDProducerWarp = kDWarps;           // warp 8
-constexpr int kDThreads = kDConsumers + 32;
+constexpr int kDIndexerWarp = kDWarps + 1;        // warp 9
+constexpr int kDThreads = kDConsumers + 64;
 constexpr uint32_t kBitsWindow = 64;  // 16-byte-aligned window holding a tile's state bits
 
 // Shared memory: kDStages stages (each: the record buffer, the tile's mu
-// values, its state-bit window and its blocks' mid-byte counts), one output
+// values, its state-bit window and its block table), one output
 // buffer per decoding warp (its 32 * RPL rows of 128 bytes, 1024-byte aligned
 // for the swizzled tensor store), and the decode table.
 struct DSmem {
     uint32_t stage;         // stage st starts at st * stage
-    uint32_t mu, bits, mk;  // offsets inside a stage (the record buffer is at 0)
+    uint32_t mu, bits, info;  // offsets inside a stage (the record buffer is at 0)
     uint32_t wbuf, wbuf_bytes;  // warp w's output buffer at wbuf + w * wbuf_bytes
     uint32_t lut, total;
 };
@@ -150,18 +150,16 @@ __host__ __device__ inline DSmem decompress_smem(uint32_t G, uint32_t b, uint32_
     const uint32_t rec = record_max_bytes(G, b, w) + 16;  // + slack for the 8-byte run reads
     const uint32_t body = (rec + 15) & ~15u;
     const uint32_t mub = (G * w + 15) & ~15u;
-    s.stage = (body + mub + kBitsWindow + 4 * G + 1023) & ~1023u;
+    s.stage = (body + mub + kBitsWindow + 8 * G + 1023) & ~1023u;  // + the block table
     s.mu = body;
     s.bits = s.mu + mub;
-    s.mk = s.bits + kBitsWindow;
+    s.info = s.bits + kBitsWindow;
     s.wbuf = kDStages * s.stage;
     s.wbuf_bytes = (G * b * w) / kDWarps;  // 4 KiB per 128-byte row per lane
     s.lut = s.wbuf + kDWarps * s.wbuf_bytes;
     s.total = s.lut + (uint32_t)sizeof(DecodeLut) + 1024;  // + slack to realign the dynamic base
     return s;
 }
-
-__device__ __forceinline__ void decoder_sync() { asm volatile("bar.sync 1, %0;" ::"n"(kDConsumers) : "memory"); }
 
 __device__ __forceinline__ void dmbar_arrive(uint64_t *bar) {
     asm volatile(
@@ -187,14 +185,14 @@ __global__ void __launch_bounds__(kDThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
     static_assert(RPL >= 1 && G * b * w == 32768u * RPL, "lane geometry");
 
     extern __shared__ __align__(16) uint8_t smem_raw[];  // realigned to 1024 below
-    // full: record, mu and state bits copied in; consumed: every decoding warp
-    // is done reading the stage
-    __shared__ __align__(8) uint64_t full[kDStages], consumed[kDStages];
-    // st_bad: set by the producer (index or header fault); st_dbad: set by a
-    // decoder (bad codes), read only after the barrier
-    __shared__ uint32_t st_size[kDStages], st_bad[kDStages], st_dbad[kDStages], st_boff[kDStages];
+    // full: record, mu and state bits copied in; indexed: the indexing warp
+    // has written the stage's block table and verdict; consumed: every
+    // decoding warp is done reading the stage
+    __shared__ __align__(8) uint64_t full[kDStages], indexed[kDStages], consumed[kDStages];
+    // st_bad: set by the producer (index or header fault); st_verdict: set by
+    // the indexing warp (0: decode, 3: corrupt record, 6: a wait ran out)
+    __shared__ uint32_t st_size[kDStages], st_bad[kDStages], st_verdict[kDStages], st_boff[kDStages];
     __shared__ uint32_t st_field[kDStages], st_tile[kDStages];  // the stage's field and its local tile
-    __shared__ uint32_t s_abort;  // a decoder's wait ran out: the CTA stops after the barrier
 
     uint8_t *smem = smem_raw + ((1024u - (smem_addr(smem_raw) & 1023u)) & 1023u);
     const DSmem L = decompress_smem(G, b, w);
@@ -209,10 +207,10 @@ __global__ void __launch_bounds__(kDThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
     if (tid == 0) {
         for (int i = 0; i < kDStages; ++i) {
             mbar_init(&full[i], 1);
+            mbar_init(&indexed[i], 1);
             mbar_init(&consumed[i], kDWarps);
-            st_size[i] = st_bad[i] = st_dbad[i] = st_boff[i] = st_field[i] = st_tile[i] = 0;
+            st_size[i] = st_bad[i] = st_verdict[i] = st_boff[i] = st_field[i] = st_tile[i] = 0;
         }
-        s_abort = 0;
         fence_mbar_init();
     }
     __syncthreads();
@@ -267,7 +265,6 @@ __global__ void __launch_bounds__(kDThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
             st_tile[st] = tile;
             st_size[st] = size;
             st_bad[st] = bad;
-            st_dbad[st] = 0;
             if (!bad) {
                 const uint64_t k0 = (uint64_t)tile * G;
                 const uint32_t Gt = (uint32_t)min_u64(G, g.nb - k0);
@@ -297,6 +294,126 @@ __global__ void __launch_bounds__(kDThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
         return;
     }
 
+    if (warp == kDIndexerWarp) {
+        // ---- indexing warp: per stage, every block's rank among the tile's
+        // non-constant blocks, its reqBits byte and the offset of its mid
+        // bytes, and the record's checks; one stage ahead of the decoders.
+        // Lane l takes blocks BPL*l .. BPL*l + BPL - 1 (consecutive, inside
+        // one 32-bit word of state bits), so a scan over lanes orders them.
+        constexpr uint32_t BPL = (G + 31) / 32;
+        constexpr uint32_t NSW = (G + 31) / 32;  // 32-bit words of state bits
+        static_assert(32 % BPL == 0, "a lane's blocks share one state word");
+        for (uint32_t it = 0;; ++it) {
+            const uint64_t tile64 = (uint64_t)blockIdx.x + (uint64_t)it * gridDim.x;
+            if (tile64 >= lc.total_tiles) break;
+            const int st = (int)(it % kDStages);
+            const uint32_t k = it / kDStages;
+            const bool waited = mbar_wait_bounded(&full[st], k & 1u, lc.copy_ns);
+            const DField *Fd = dfield_ptr<BATCH>(one, lc, st_field[st]);
+            const Geometry &g = Fd->g;
+            const uint32_t tile = st_tile[st];
+            const uint32_t size = st_size[st];
+            const bool pbad = !waited || st_bad[st] != 0;
+            const uint8_t *rec = smem + st * L.stage;
+            uint2 *info = reinterpret_cast<uint2 *>(smem + st * L.stage + L.info);
+            const uint64_t k0 = (uint64_t)tile * G;
+            const uint32_t Gt = pbad ? 0u : (uint32_t)min_u64(G, g.nb - k0);
+
+            // the tile's state bits (bits at or past Gt cleared)
+            uint32_t sw[NSW];
+            {
+                const uint8_t *stb = rec + L.bits + st_boff[st];
+                if constexpr (G >= 32) {
+                    // the tile's bits start at a multiple of 4 bytes
+#pragma unroll
+                    for (uint32_t i = 0; i < NSW; ++i) sw[i] = reinterpret_cast<const uint32_t *>(stb)[i];
+                } else {
+                    sw[0] = stb[0];
+                    if (G > 8) sw[0] |= (uint32_t)stb[1] << 8;
+                }
+#pragma unroll
+                for (uint32_t i = 0; i < NSW; ++i) {
+                    const uint32_t lo = 32 * i;
+                    sw[i] &= Gt >= lo + 32 ? kFull : (Gt <= lo ? 0u : (1u << (Gt - lo)) - 1u);
+                }
+            }
+            const uint32_t j0 = (uint32_t)lane * BPL;
+            uint32_t nn_t = 0, rank0 = 0, mybits = 0;
+#pragma unroll
+            for (uint32_t i = 0; i < NSW; ++i) {
+                nn_t += __popc(sw[i]);
+                if (j0 >= 32 * i + 32) {
+                    rank0 += __popc(sw[i]);
+                } else if (j0 >= 32 * i) {
+                    const uint32_t sh = j0 - 32 * i;
+                    rank0 += __popc(sw[i] & ((1u << sh) - 1u));
+                    mybits = (sw[i] >> sh) & ((BPL >= 32 ? 0u : (1u << BPL)) - 1u);
+                }
+            }
+            bool ok = (uint64_t)nn_t * (b / 4 + 1) <= size;
+            uint32_t rq_b[BPL], rank_b[BPL], mk_b[BPL];
+            uint32_t lane_total = 0;
+#pragma unroll
+            for (uint32_t i = 0; i < BPL; ++i) {
+                const uint32_t j = j0 + i;
+                const uint32_t rank = rank0 + __popc(mybits & ((1u << i) - 1u));
+                const bool ex = j < Gt;
+                const uint32_t len = ex ? (uint32_t)min_u64(b, g.n - (k0 + j) * b) : 0u;
+                const bool nc = ex && ((mybits >> i) & 1u) && ok;
+                const uint32_t rq = nc ? rec[nn_t * (b / 4) + rank] : 0u;
+                const bool raw = nc && rq == 0xFFu;
+                const bool coded = nc && !raw;
+                if (nc && rq == 0u) ok = false;  // 0 marks a constant block in the table
+                if (coded && !(rq >= 1u + F::E && rq <= (uint32_t)W)) ok = false;
+                const uint32_t s = (8u - (rq & 7u)) & 7u;
+                const uint32_t q = coded ? (rq + s) >> 3 : 2u;
+                uint32_t suml = 0;
+                if (coded) {
+                    // codes past the block's end are 0; none exceeds min(3, q)
+                    const uint32_t *lw = reinterpret_cast<const uint32_t *>(rec + rank * (b / 4));
+#pragma unroll 8
+                    for (uint32_t wd = 0; wd < b / 16; ++wd) {
+                        const uint32_t c = lw[wd];
+                        const int nv = (int)len - 16 * (int)wd;
+                        const uint32_t vm = nv >= 16 ? kFull : (nv <= 0 ? 0u : (kFull >> (2 * (16 - nv))));
+                        if (c & ~vm) ok = false;
+                        if (q == 2u && (c & (c >> 1) & 0x55555555u)) ok = false;
+                        suml += __popc(c & 0x55555555u) + 2 * __popc(c & 0xAAAAAAAAu);
+                    }
+                }
+                const uint32_t mk = coded ? len * q - suml : (raw ? len * w : 0u);
+                rq_b[i] = rq;
+                rank_b[i] = rank;
+                mk_b[i] = mk;
+                lane_total += mk;
+            }
+            uint32_t total;
+            const uint32_t excl = warp_exclusive_scan(lane_total, &total);
+            const uint32_t used = nn_t * (b / 4 + 1) + total;
+            ok = __all_sync(kFull, ok) && !pbad && pad16(used) == size;
+            if (ok) {
+                uint32_t run = nn_t * (b / 4 + 1) + excl;
+#pragma unroll
+                for (uint32_t i = 0; i < BPL; ++i) {
+                    if (j0 + i < G) info[j0 + i] = make_uint2(run, rank_b[i] | (rq_b[i] << 16));
+                    run += mk_b[i];
+                }
+                // strictness: the record's pad bytes must be zero
+                const bool pad_ok = lane >= (int)(size - used) || rec[used + lane] == 0;
+                ok = __all_sync(kFull, pad_ok);
+            }
+            if (lane == 0) {
+                const uint32_t verdict = ok ? 0u : (!waited ? 6u : 3u);
+                st_verdict[st] = verdict;
+                if (verdict) flag_status(Fd->status, verdict);
+                dmbar_arrive(&indexed[st]);
+            }
+            __syncwarp();
+            if (!waited) break;
+        }
+        return;
+    }
+
     // ---- decoders (warps 0..7) ---------------------------------------------
     uint8_t *wbuf = smem + L.wbuf + warp * L.wbuf_bytes;
     const uint32_t lane_row0 = (uint32_t)(lane * RPL);  // inside the warp's rows
@@ -305,130 +422,56 @@ __global__ void __launch_bounds__(kDThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
         if (tile64 >= lc.total_tiles) break;
         const int st = (int)(it % kDStages);
         const uint32_t k = it / kDStages;
-        // a wait that ran out still joins the barrier below (every decoding
-        // warp must), then the whole CTA stops
-        const bool waited = mbar_wait_bounded(&full[st], k & 1u, lc.copy_ns);
-        if (!waited) s_abort = 1;
+        // the stage's bytes, then its block table (the indexing warp waited
+        // for the same copy); a wait that runs out stops this warp
+        if (!mbar_wait_bounded(&full[st], k & 1u, lc.copy_ns) ||
+            !mbar_wait_bounded(&indexed[st], k & 1u, 2 * lc.copy_ns)) {
+            if (lane == 0) flag_status(dfield_ptr<BATCH>(one, lc, st_field[st])->status, 6u);
+            break;
+        }
         const DField *Fd = dfield_ptr<BATCH>(one, lc, st_field[st]);
         const Geometry &g = Fd->g;
         const uint32_t tile = st_tile[st];
-        const uint32_t size = st_size[st];
-        const bool pbad = st_bad[st] != 0 || !waited;
-        uint8_t *rec = smem + st * L.stage;
-        uint32_t *sm_mk = reinterpret_cast<uint32_t *>(rec + L.mk);
+        const bool bad = st_verdict[st] != 0;
+        const uint8_t *rec = smem + st * L.stage;
         const uint64_t k0 = (uint64_t)tile * G;
         const uint32_t Gt = (uint32_t)min_u64(G, g.nb - k0);
 
-        // ---- ranks, codes, mid-byte counts --------------------------------
         const int sub = lane % LPB;
         const uint32_t blk = (uint32_t)(warp * BPW + lane / LPB);
-        const bool exists = blk < Gt && !pbad;
+        const bool exists = blk < Gt && !bad;
         const uint64_t kg = k0 + blk;
         const int len = exists ? (int)min_u64(b, g.n - kg * b) : 0;
         int nvalid = len - sub * VPL;
         nvalid = nvalid < 0 ? 0 : (nvalid > VPL ? VPL : nvalid);
         const bool full_lane = nvalid == VPL;
-        // rank of the block among the tile's non-constant blocks: a popcount
-        // of the tile's state bits below it
-        uint32_t rank = 0, nn_t = 0;
-        bool nonconst = false;
-        if (!pbad) {
-            const uint8_t *stb = rec + L.bits + st_boff[st];
-            if constexpr (G >= 32) {
-                // the tile's bits start at a multiple of 4 bytes
-                const uint32_t *sw = reinterpret_cast<const uint32_t *>(stb);
-#pragma unroll
-                for (uint32_t i = 0; i < G / 32; ++i) {
-                    if (32 * i < Gt) {
-                        uint32_t wv = sw[i];
-                        if (Gt - 32 * i < 32) wv &= (1u << (Gt - 32 * i)) - 1u;
-                        nn_t += __popc(wv);
-                        if (blk >= 32 * i + 32) {
-                            rank += __popc(wv);
-                        } else if (blk >= 32 * i) {
-                            rank += __popc(wv & ((1u << (blk - 32 * i)) - 1u));
-                            nonconst = (wv >> (blk - 32 * i)) & 1u;
-                        }
-                    }
-                }
-            } else {
-                uint32_t wv = stb[0];
-                if (G > 8) wv |= (uint32_t)stb[1] << 8;
-                wv &= (1u << Gt) - 1u;
-                nn_t = __popc(wv);
-                rank = __popc(wv & ((1u << blk) - 1u));
-                nonconst = (wv >> blk) & 1u;
-            }
-        }
-        nonconst = nonconst && exists;
-        bool ok = (uint64_t)nn_t * (b / 4 + 1) <= size;
-        nonconst = nonconst && ok;
-        const int rq = nonconst ? (int)rec[nn_t * (b / 4) + rank] : 0;
-        const bool raw = nonconst && rq == 0xFF;
-        const bool coded = nonconst && !raw;
-        if (coded && !(rq >= 1 + F::E && rq <= W)) ok = false;
-        const int s = (8 - (rq & 7)) & 7;
-        const int q = coded && ok ? (rq + s) >> 3 : 2;
-        const int lmax = q < 3 ? q : 3;
-        uint32_t codes[NCODE];
-#pragma unroll
-        for (int i = 0; i < NCODE; ++i) codes[i] = 0;
-        if (coded && ok) {
-            const uint8_t *lead = rec + rank * (b / 4) + sub * (VPL / 4);
-            if constexpr (NCODE == 2) {
-                const uint2 v = *reinterpret_cast<const uint2 *>(lead);
-                codes[0] = v.x;
-                codes[1] = v.y;
-            } else {
-                codes[0] = *reinterpret_cast<const uint32_t *>(lead);
-            }
-            // codes past the end are 0; no code exceeds min(3, q)
-#pragma unroll
-            for (int i = 0; i < NCODE; ++i) {
-                const int nv = nvalid - 16 * i;
-                const uint32_t vm = nv >= 16 ? 0xFFFFFFFFu : (nv <= 0 ? 0u : (0xFFFFFFFFu >> (2 * (16 - nv))));
-                if (codes[i] & ~vm) ok = false;
-                if (lmax == 2 && (codes[i] & (codes[i] >> 1) & 0x55555555u)) ok = false;
-            }
-        }
-        uint32_t suml = 0;
-#pragma unroll
-        for (int i = 0; i < NCODE; ++i) suml += __popc(codes[i] & 0x55555555u) + 2 * __popc(codes[i] & 0xAAAAAAAAu);
-        const uint32_t mk_lane = coded ? (uint32_t)(nvalid * q) - suml : (raw ? (uint32_t)nvalid * w : 0u);
         const uint32_t segmask = (LPB == 32 ? kFull : ((1u << LPB) - 1u)) << (lane & ~(LPB - 1));
-        {
-            const uint32_t bal = __ballot_sync(kFull, ok);
-            ok = (bal & segmask) == segmask;
-        }
-        // the warp's blocks in order: an exclusive scan over lanes gives each
-        // block's mid-byte offset inside the warp's share of the record
-        uint32_t wtotal;
-        const uint32_t lane_excl = warp_exclusive_scan(mk_lane, &wtotal);
-        const uint32_t blk_excl = __shfl_sync(kFull, lane_excl, lane & ~(LPB - 1));
-        if (lane == 0) sm_mk[warp] = wtotal;
-        if (!ok && exists) st_dbad[st] = 1;
-        decoder_sync();
-
-        // ---- mid-byte offsets: warps before this one -----------------------
-        uint32_t before = 0, total = 0;
-#pragma unroll
-        for (int i = 0; i < kDWarps; ++i) {
-            const uint32_t m = sm_mk[i];
-            total += m;
-            if (i < warp) before += m;
-        }
-        const uint32_t used = nn_t * (b / 4 + 1) + total;
-        // uniform over the CTA: the flags and the counts were fixed before the barrier
-        const bool abort = s_abort != 0;
-        const bool bad = abort || st_bad[st] || st_dbad[st] || pad16(used) != size;
         U x[VPL];
-        if (bad) {
-            if (tid == 0) flag_status(Fd->status, abort ? 6u : 3u);
-        } else {
-            // ---- decode --------------------------------------------------
-            const uint32_t mbase = nn_t * (b / 4 + 1) + before + blk_excl;
+        if (!bad) {
+            // ---- the block's entry: mid-byte offset, rank, reqBits ----------
+            const uint2 bi = exists ? reinterpret_cast<const uint2 *>(rec + L.info)[blk] : make_uint2(0, 0);
+            const uint32_t mbase = bi.x, rank = bi.y & 0xFFFFu, rq = bi.y >> 16;
+            const bool raw = rq == 0xFFu;
+            const bool coded = rq != 0u && !raw;
+            const int s = (8 - (int)(rq & 7u)) & 7;
+            const int q = coded ? ((int)rq + s) >> 3 : 2;
+            const int lmax = q < 3 ? q : 3;
+            uint32_t codes[NCODE];
+#pragma unroll
+            for (int i = 0; i < NCODE; ++i) codes[i] = 0;
+            if (coded) {
+                const uint8_t *lead = rec + rank * (b / 4) + sub * (VPL / 4);
+                if constexpr (NCODE == 2) {
+                    const uint2 v = *reinterpret_cast<const uint2 *>(lead);
+                    codes[0] = v.x;
+                    codes[1] = v.y;
+                } else {
+                    codes[0] = *reinterpret_cast<const uint32_t *>(lead);
+                }
+            }
             const U mu_bits = exists ? reinterpret_cast<const U *>(rec + L.mu)[blk] : U(0);
 
+            // ---- decode --------------------------------------------------
             using CntT = std::conditional_t<(LPB * VPL > 1023), unsigned long long, uint32_t>;
             constexpr int FB = LPB * VPL > 1023 ? 16 : 10;
             constexpr CntT FM = (CntT(1) << FB) - 1;
@@ -549,15 +592,10 @@ __global__ void __launch_bounds__(kDThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
 #pragma unroll
                 for (int m = 0; m < VPL; ++m) x[m] = mu_bits;
             }
-            // strictness: the record's pad bytes must be zero
-            if (warp == 0)
-                for (uint32_t i = used + lane; i < size; i += 32)
-                    if (rec[i]) flag_status(Fd->status, 3u);
         }
         // this warp no longer reads the stage
         __syncwarp();
         if (lane == 0) dmbar_arrive(&consumed[st]);
-        if (abort) break;
         if (bad) continue;
 
         // ---- output: full rows through the warp's buffer and a tensor store,
