@@ -5,23 +5,26 @@
 // device-wide scan is left for decompression (the paper's GPU decoder, Sec.
 // V-B, runs a prefix scan of the mid-byte counts first).  Per CTA, a producer
 // thread, an indexing warp and eight decoding warps share two stage buffers
-// through mbarriers (full / indexed / consumed):
+// through mbarriers (head / full / indexed / consumed):
 //   producer (one thread): per tile, bulk-copies (cp.async.bulk) the record,
 //     the tile's mu values and a 16-byte-aligned window of its state bits into
-//     a stage; the tile index entries are loaded one tile ahead, so no global
+//     a stage.  The record's head (reqBits bytes and lead codes), the mu
+//     values and the state bits complete one mbarrier and the rest of the
+//     record another, so that indexing starts before the mid bytes have
+//     landed.  The tile index entries are loaded one tile ahead, so no global
 //     latency sits between two copies;
 //   indexing warp: per stage, ranks every block among the tile's non-constant
 //     blocks (a popcount of the state bits), reads its reqBits byte and lead
 //     codes, checks them, counts its mid bytes, and scans the counts into
 //     each block's mid-byte offset; the total is checked against the record
-//     size (and the pad bytes against zero), so that every later read is
-//     inside the record.  It writes a block table (offset, rank, reqBits)
-//     and the stage's verdict, one stage ahead of the decoders;
+//     size, so that every later read is inside the record.  It writes a
+//     block table (offset, rank, reqBits) and the stage's verdict, one stage
+//     ahead of the decoders;
 //   eight decoding warps: decode the stage's record into registers, release
 //     the stage, then write their rows into a buffer of their own in the
 //     128-byte-swizzled layout of the TMA tensor store and issue that store
 //     (one 2-D box of 32 rows per warp).  The ragged last row goes out with
-//     plain stores.
+//     plain stores.  Warp 0 also checks that the record's padding is zero.
 // The same kernel serves a single stream (its descriptor is a kernel
 // parameter) and batches (a table of descriptors in device memory, BATCH),
 // and decodes a block range for random access.
@@ -183,15 +186,18 @@ __global__ void __launch_bounds__(kDThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
     constexpr uint32_t b = (uint32_t)(LPB * VPL);
     constexpr uint32_t G = tile_blocks(b, (uint32_t)w);
     static_assert(RPL >= 1 && G * b * w == 32768u * RPL, "lane geometry");
+    constexpr uint32_t kHeadBytes = (G * (b / 4 + 1) + 15) & ~15u;  // reqBits bytes and lead codes, at most
 
     extern __shared__ __align__(16) uint8_t smem_raw[];  // realigned to 1024 below
-    // full: record, mu and state bits copied in; indexed: the indexing warp
-    // has written the stage's block table and verdict; consumed: every
-    // decoding warp is done reading the stage
-    __shared__ __align__(8) uint64_t full[kDStages], indexed[kDStages], consumed[kDStages];
+    // head: the record's head (reqBits bytes and lead codes), mu values and
+    // state bits copied in; full: the rest of the record; indexed: the
+    // indexing warp has written the stage's block table and verdict;
+    // consumed: every decoding warp is done reading the stage
+    __shared__ __align__(8) uint64_t head[kDStages], full[kDStages], indexed[kDStages], consumed[kDStages];
     // st_bad: set by the producer (index or header fault); st_verdict: set by
     // the indexing warp (0: decode, 3: corrupt record, 6: a wait ran out)
     __shared__ uint32_t st_size[kDStages], st_bad[kDStages], st_verdict[kDStages], st_boff[kDStages];
+    __shared__ uint32_t st_used[kDStages];  // the record's bytes before its zero padding (when the verdict is 0)
     __shared__ uint32_t st_field[kDStages], st_tile[kDStages];  // the stage's field and its local tile
 
     uint8_t *smem = smem_raw + ((1024u - (smem_addr(smem_raw) & 1023u)) & 1023u);
@@ -206,10 +212,11 @@ __global__ void __launch_bounds__(kDThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
     }
     if (tid == 0) {
         for (int i = 0; i < kDStages; ++i) {
+            mbar_init(&head[i], 1);
             mbar_init(&full[i], 1);
             mbar_init(&indexed[i], 1);
             mbar_init(&consumed[i], kDWarps);
-            st_size[i] = st_bad[i] = st_verdict[i] = st_boff[i] = st_field[i] = st_tile[i] = 0;
+            st_size[i] = st_bad[i] = st_verdict[i] = st_boff[i] = st_used[i] = st_field[i] = st_tile[i] = 0;
         }
         fence_mbar_init();
     }
@@ -277,20 +284,29 @@ __global__ void __launch_bounds__(kDThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
                 const uint64_t sbE = pad16(g.off_state + (k0 + Gt + 7) / 8);
                 st_boff[st] = (uint32_t)(sb0 - sbA);
                 uint8_t *stage = smem + st * L.stage;
-                mbar_arrive_expect_tx(&full[st], size + mu_bytes + (uint32_t)(sbE - sbA));
-                if (size) bulk_g2s(stage, F->in + g.off_rec + r0, size, &full[st]);
-                bulk_g2s(stage + L.mu, F->in + g.off_mu + k0 * w, mu_bytes, &full[st]);
-                bulk_g2s(stage + L.bits, F->in + sbA, (uint32_t)(sbE - sbA), &full[st]);
+                // the head first (what the indexing warp reads: at most
+                // G * (b/4 + 1) bytes, rounded up to 16), then the rest
+                const uint32_t hb = size < kHeadBytes ? size : kHeadBytes;
+                mbar_arrive_expect_tx(&head[st], hb + mu_bytes + (uint32_t)(sbE - sbA));
+                bulk_g2s(stage + L.bits, F->in + sbA, (uint32_t)(sbE - sbA), &head[st]);
+                if (hb) bulk_g2s(stage, F->in + g.off_rec + r0, hb, &head[st]);
+                bulk_g2s(stage + L.mu, F->in + g.off_mu + k0 * w, mu_bytes, &head[st]);
+                mbar_arrive_expect_tx(&full[st], size - hb);
+                if (size > hb) bulk_g2s(stage + hb, F->in + g.off_rec + r0 + hb, size - hb, &full[st]);
                 copy_last |= 1u << st;
                 copy_par = (copy_par & ~(1u << st)) | ((k & 1u) << st);
             } else {
+                dmbar_arrive(&head[st]);
                 dmbar_arrive(&full[st]);
                 copy_last &= ~(1u << st);
             }
         }
         // do not leave while a copy may still be writing into shared memory
         for (int st = 0; st < kDStages; ++st)
-            if ((copy_last >> st) & 1u) mbar_wait_bounded(&full[st], (copy_par >> st) & 1u, lc.copy_ns);
+            if ((copy_last >> st) & 1u) {
+                mbar_wait_bounded(&head[st], (copy_par >> st) & 1u, lc.copy_ns);
+                mbar_wait_bounded(&full[st], (copy_par >> st) & 1u, lc.copy_ns);
+            }
         return;
     }
 
@@ -308,7 +324,7 @@ __global__ void __launch_bounds__(kDThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
             if (tile64 >= lc.total_tiles) break;
             const int st = (int)(it % kDStages);
             const uint32_t k = it / kDStages;
-            const bool waited = mbar_wait_bounded(&full[st], k & 1u, lc.copy_ns);
+            const bool waited = mbar_wait_bounded(&head[st], k & 1u, lc.copy_ns);
             const DField *Fd = dfield_ptr<BATCH>(one, lc, st_field[st]);
             const Geometry &g = Fd->g;
             const uint32_t tile = st_tile[st];
@@ -369,17 +385,34 @@ __global__ void __launch_bounds__(kDThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
                 const uint32_t q = coded ? (rq + s) >> 3 : 2u;
                 uint32_t suml = 0;
                 if (coded) {
+                    // the block's codes, b/16 words (16-byte aligned for b >= 64);
                     // codes past the block's end are 0; none exceeds min(3, q)
-                    const uint32_t *lw = reinterpret_cast<const uint32_t *>(rec + rank * (b / 4));
-#pragma unroll 8
-                    for (uint32_t wd = 0; wd < b / 16; ++wd) {
-                        const uint32_t c = lw[wd];
-                        const int nv = (int)len - 16 * (int)wd;
-                        const uint32_t vm = nv >= 16 ? kFull : (nv <= 0 ? 0u : (kFull >> (2 * (16 - nv))));
-                        if (c & ~vm) ok = false;
-                        if (q == 2u && (c & (c >> 1) & 0x55555555u)) ok = false;
-                        suml += __popc(c & 0x55555555u) + 2 * __popc(c & 0xAAAAAAAAu);
+                    constexpr uint32_t NW = b / 16;
+                    constexpr uint32_t VW = NW % 4 == 0 ? 4 : 2;  // words per load
+                    const uint8_t *lb = rec + rank * (b / 4);
+                    uint32_t any3 = 0, past = 0;
+#pragma unroll 2
+                    for (uint32_t v4 = 0; v4 < NW / VW; ++v4) {
+                        uint32_t c[VW];
+                        if constexpr (VW == 4) {
+                            const uint4 u = reinterpret_cast<const uint4 *>(lb)[v4];
+                            c[0] = u.x, c[1] = u.y, c[2] = u.z, c[3] = u.w;
+                        } else {
+                            const uint2 u = reinterpret_cast<const uint2 *>(lb)[v4];
+                            c[0] = u.x, c[1] = u.y;
+                        }
+#pragma unroll
+                        for (uint32_t e = 0; e < VW; ++e) {
+                            any3 |= c[e] & (c[e] >> 1);
+                            suml += __popc(c[e]) + __popc(c[e] & 0xAAAAAAAAu);  // lo + 2 hi
+                            if (len < b) {
+                                const int nv = (int)len - 16 * (int)(v4 * VW + e);
+                                const uint32_t vm = nv >= 16 ? kFull : (nv <= 0 ? 0u : (kFull >> (2 * (16 - nv))));
+                                past |= c[e] & ~vm;
+                            }
+                        }
                     }
+                    if (past || (q == 2u && (any3 & 0x55555555u))) ok = false;
                 }
                 const uint32_t mk = coded ? len * q - suml : (raw ? len * w : 0u);
                 rq_b[i] = rq;
@@ -398,13 +431,11 @@ __global__ void __launch_bounds__(kDThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
                     if (j0 + i < G) info[j0 + i] = make_uint2(run, rank_b[i] | (rq_b[i] << 16));
                     run += mk_b[i];
                 }
-                // strictness: the record's pad bytes must be zero
-                const bool pad_ok = lane >= (int)(size - used) || rec[used + lane] == 0;
-                ok = __all_sync(kFull, pad_ok);
             }
             if (lane == 0) {
                 const uint32_t verdict = ok ? 0u : (!waited ? 6u : 3u);
                 st_verdict[st] = verdict;
+                st_used[st] = used;
                 if (verdict) flag_status(Fd->status, verdict);
                 dmbar_arrive(&indexed[st]);
             }
@@ -422,9 +453,9 @@ __global__ void __launch_bounds__(kDThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
         if (tile64 >= lc.total_tiles) break;
         const int st = (int)(it % kDStages);
         const uint32_t k = it / kDStages;
-        // the stage's bytes, then its block table (the indexing warp waited
-        // for the same copy); a wait that runs out stops this warp
-        if (!mbar_wait_bounded(&full[st], k & 1u, lc.copy_ns) ||
+        // the stage's bytes and its block table; a wait that runs out stops
+        // this warp
+        if (!mbar_wait_bounded(&head[st], k & 1u, lc.copy_ns) || !mbar_wait_bounded(&full[st], k & 1u, lc.copy_ns) ||
             !mbar_wait_bounded(&indexed[st], k & 1u, 2 * lc.copy_ns)) {
             if (lane == 0) flag_status(dfield_ptr<BATCH>(one, lc, st_field[st])->status, 6u);
             break;
@@ -591,6 +622,11 @@ __global__ void __launch_bounds__(kDThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
             } else {
 #pragma unroll
                 for (int m = 0; m < VPL; ++m) x[m] = mu_bits;
+            }
+            // strictness: the record's pad bytes (fewer than 16) must be zero
+            if (warp == 0) {
+                const uint32_t used = st_used[st];
+                if (used + lane < st_size[st] && rec[used + lane]) flag_status(Fd->status, 3u);
             }
         }
         // this warp no longer reads the stage
