@@ -456,8 +456,7 @@ __global__ void __launch_bounds__(kCThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
     // totals in place; ready: record written; empty: record stored
     __shared__ __align__(8) uint64_t full[kStages], encoded[kStages], ready[kStages], empty[kStages];
     // per stage: the field and its local tile (0xFFFFFFFF: no more tiles)
-    __shared__ uint32_t st_field[kStages], st_tile[kStages], st_nn[kStages], st_nraw[kStages], st_nesc[kStages],
-        st_rec[kStages];
+    __shared__ uint32_t st_field[kStages], st_tile[kStages], st_rec[kStages];
 
     // the 128-byte swizzle of the tensor copy needs 1024-byte aligned buffers
     uint8_t *smem = smem_raw + ((1024u - (smem_addr(smem_raw) & 1023u)) & 1023u);
@@ -483,7 +482,7 @@ __global__ void __launch_bounds__(kCThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
         for (int i = 0; i < kStages; ++i) {
             st_tile[i] = 0xFFFFFFFFu;
             st_field[i] = 0;
-            st_nn[i] = st_nraw[i] = st_nesc[i] = st_rec[i] = 0;
+            st_rec[i] = 0;
         }
     }
     __syncthreads();
@@ -509,7 +508,6 @@ __global__ void __launch_bounds__(kCThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
             const uint32_t tile = more ? (uint32_t)(t - F->tile0) : 0xFFFFFFFFu;
             st_field[st] = f;
             st_tile[st] = tile;
-            st_nesc[st] = 0;
             const uint64_t row0 = (uint64_t)tile * 256 * RPL;
             if (more && F->use_tma && row0 < F->rows_full) {
                 mbar_arrive_expect_tx(&full[st], 256u * 128u * RPL);
@@ -586,6 +584,7 @@ __global__ void __launch_bounds__(kCThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
                     base -= 32;
                 }
             }
+            uint8_t *out = F->out;
             if (lane == 0) {
                 st_relaxed_u64(&lookback[tile], kFlagPrefix | (excl + rec_bytes));
                 Workspace *ws = F->ws;
@@ -594,7 +593,6 @@ __global__ void __launch_bounds__(kCThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
                     atomicAdd(&ws->lookback_timeouts, 1ull);
                     atomicCAS(&ws->first_lb_tile, 0u, tile + 1);
                 }
-                uint8_t *out = F->out;
                 uint64_t *idx = reinterpret_cast<uint64_t *>(out + g.off_index);
                 idx[tile] = excl;
                 if (tile == g.ntiles - 1) {
@@ -609,10 +607,38 @@ __global__ void __launch_bounds__(kCThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
                     bulk_s2g(out + g.off_rec + excl, smem + st * L.buf_stride, rec_bytes);
                     bulk_commit();
                 }
-                // the field's counts (the header is written once every CTA is done)
-                if (st_nn[st]) atomicAdd(&ws->nn, (unsigned long long)st_nn[st]);
-                if (st_nraw[st]) atomicAdd(&ws->nraw, (unsigned long long)st_nraw[st]);
-                if (st_nesc[st]) atomicAdd(&ws->nesc, (unsigned long long)st_nesc[st]);
+            }
+            {
+                // while the store reads the record: the field's counts (the
+                // header is written once every CTA is done) and the state
+                // bits, from the warps' totals and the block kinds
+                const uint8_t *meta = smem + (L.meta0 + st * L.meta_stride);
+                const uint4 wt = lane < kConsumerWarps ? reinterpret_cast<const uint4 *>(meta + L.m_w)[lane]
+                                                       : make_uint4(0, 0, 0, 0);
+                const uint32_t nn_t = __reduce_add_sync(kFull, wt.x) >> 20;
+                const uint32_t raw_t = __reduce_add_sync(kFull, wt.y), esc_t = __reduce_add_sync(kFull, wt.z);
+                if (lane == 0) {
+                    Workspace *ws = F->ws;
+                    if (nn_t) atomicAdd(&ws->nn, (unsigned long long)nn_t);
+                    if (raw_t) atomicAdd(&ws->nraw, (unsigned long long)raw_t);
+                    if (esc_t) atomicAdd(&ws->nesc, (unsigned long long)esc_t);
+                }
+                // bit i of byte j is set when block 8j + i is not constant
+                const uint8_t *sm_kind = meta + L.m_kind;
+                const uint64_t k0 = (uint64_t)tile * G;
+                const uint32_t Gt = (uint32_t)min_u64(G, g.nb - k0);
+                uint8_t *state = out + g.off_state + (size_t)k0 / 8;
+                for (uint32_t j = lane; j < (Gt + 7) / 8; j += 32) {
+                    uint32_t byte = 0;
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) {
+                        const uint32_t kk = j * 8 + i;
+                        if (kk < Gt && sm_kind[kk] != kConst) byte |= 1u << i;
+                    }
+                    state[j] = (uint8_t)byte;
+                }
+            }
+            if (lane == 0) {
                 // the buffer is free once the store has read it
                 if (rec_bytes) bulk_wait_read_all();
                 mbar_arrive(&empty[st]);
@@ -764,56 +790,18 @@ __global__ void __launch_bounds__(kCThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
         const uint32_t nonc_bal = __ballot_sync(kFull, lead && kind != kConst);
         const uint32_t raw_bal = __ballot_sync(kFull, lead && kind == kRaw);
         const uint32_t esc_bal = __ballot_sync(kFull, lead && kind == kNonConst && req > req0);
-        if (lane == 0) sm_w[warp] = make_uint4(__popc(nonc_bal), mid_w, __popc(raw_bal), __popc(esc_bal));
+        // per warp: (non-constant blocks << 20 | mid bytes), raw blocks, escalated blocks
+        if (lane == 0) sm_w[warp] = make_uint4((uint32_t)__popc(nonc_bal) << 20 | mid_w, __popc(raw_bal), __popc(esc_bal), 0);
         __syncwarp();
         if (lane == 0) mbar_arrive(&encoded[st]);
-        if (!mbar_wait_bounded(&encoded[st], k & 1u, lc.lookback_ns + lc.copy_ns)) {
-            // a warp of this CTA never finished the tile: give up
-            if (lane == 0) {
-                atomicOr(lc.err, kErrTimeout);
-                st_tile[st] = 0xFFFFFFFFu;
-                mbar_arrive(&ready[st]);
-            }
-            break;
-        }
-
-        // ---- 2. tile totals, the aggregate for the look-back, state bits ----
-        // lane i holds warp i's totals; warp reductions give the tile's totals
-        // and the sums over the warps before this one
-        const uint4 wt = lane < kConsumerWarps ? sm_w[lane] : make_uint4(0, 0, 0, 0);
-        const uint32_t nn_t = __reduce_add_sync(kFull, wt.x), mid_t = __reduce_add_sync(kFull, wt.y);
-        const uint32_t raw_t = __reduce_add_sync(kFull, wt.z), esc_t = __reduce_add_sync(kFull, wt.w);
-        const uint32_t nn_before = __reduce_add_sync(kFull, lane < warp ? wt.x : 0u);
-        const uint32_t mid_before = __reduce_add_sync(kFull, lane < warp ? wt.y : 0u);
-        const uint32_t rec_bytes = (uint32_t)pad16((uint64_t)nn_t * (b / 4 + 1) + mid_t);
-        if (warp == 0) {
-            if (lane == 0) {
-                st_nn[st] = nn_t;
-                st_nraw[st] = raw_t;
-                st_nesc[st] = esc_t;
-                st_rec[st] = rec_bytes;
-                st_relaxed_u64(&Fd->lookback[tile], kFlagAgg | rec_bytes);
-            }
-            // state bits: bit i of byte j is set when block 8j + i is not constant
-            uint8_t *state = Fd->out + g.off_state + (size_t)k0 / 8;
-            for (uint32_t j = lane; j < (Gt + 7) / 8; j += 32) {
-                uint32_t byte = 0;
-#pragma unroll
-                for (int i = 0; i < 8; ++i) {
-                    const uint32_t kk = j * 8 + i;
-                    if (kk < Gt && sm_kind[kk] != kConst) byte |= 1u << i;
-                }
-                state[j] = (uint8_t)byte;
-            }
-        }
-        if (SZX_CHECKS && rec_bytes > record_max_bytes(G, b, w) && tid == 0) report_bad(Fd->ws, tile, 2);
-        const uint32_t rank = nn_before + __popc(nonc_bal & ((1u << (lane & ~(LPB - 1))) - 1u));
-        const uint32_t mk_blk_excl = __shfl_sync(kFull, lane_excl, lane & ~(LPB - 1));
 
         // per-lane counts of values with code <= j (j = 0, 1, 2), packed in
-        // FB-bit fields, and their exclusive scan over the block's lanes.
+        // FB-bit fields, and their exclusive scan over the block's lanes;
+        // nothing here depends on the other warps, so it runs before the wait.
         // Every lane runs this (the shuffles need the whole warp); lanes of
         // constant or raw blocks contribute nothing.
+        const uint32_t mk_blk_excl = __shfl_sync(kFull, lane_excl, lane & ~(LPB - 1));
+        const uint32_t rank_in_warp = __popc(nonc_bal & ((1u << (lane & ~(LPB - 1))) - 1u));
         using CntT = std::conditional_t<(LPB * VPL > 1023), unsigned long long, uint32_t>;
         constexpr int FB = LPB * VPL > 1023 ? 16 : 10;
         constexpr CntT FM = (CntT(1) << FB) - 1;
@@ -836,6 +824,32 @@ __global__ void __launch_bounds__(kCThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
         }
         const CntT tot = __shfl_sync(kFull, incl, (lane & ~(LPB - 1)) + LPB - 1);
         const CntT off = incl - cnt;
+
+        if (!mbar_wait_bounded(&encoded[st], k & 1u, lc.lookback_ns + lc.copy_ns)) {
+            // a warp of this CTA never finished the tile: give up
+            if (lane == 0) {
+                atomicOr(lc.err, kErrTimeout);
+                st_tile[st] = 0xFFFFFFFFu;
+                mbar_arrive(&ready[st]);
+            }
+            break;
+        }
+
+        // ---- 2. tile totals and the aggregate for the look-back --------------
+        // lane i holds warp i's (nn << 20 | mid); warp reductions give the
+        // tile's totals and the sums over the warps before this one
+        const uint32_t wt = lane < kConsumerWarps ? sm_w[lane].x : 0u;
+        const uint32_t nm_t = __reduce_add_sync(kFull, wt);
+        const uint32_t nm_before = __reduce_add_sync(kFull, lane < warp ? wt : 0u);
+        const uint32_t nn_t = nm_t >> 20, mid_t = nm_t & 0xFFFFFu;
+        const uint32_t nn_before = nm_before >> 20, mid_before = nm_before & 0xFFFFFu;
+        const uint32_t rec_bytes = (uint32_t)pad16((uint64_t)nn_t * (b / 4 + 1) + mid_t);
+        if (warp == 0 && lane == 0) {
+            st_rec[st] = rec_bytes;
+            st_relaxed_u64(&Fd->lookback[tile], kFlagAgg | rec_bytes);
+        }
+        if (SZX_CHECKS && rec_bytes > record_max_bytes(G, b, w) && tid == 0) report_bad(Fd->ws, tile, 2);
+        const uint32_t rank = nn_before + rank_in_warp;
 
         // ---- 3. the record --------------------------------------------------
         uint32_t *words = reinterpret_cast<uint32_t *>(buf);
