@@ -500,6 +500,19 @@ __global__ void __launch_bounds__(kCThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
                 atomicOr(lc.err, kErrTimeout);
                 break;
             }
+            // Take tile it's ticket only once the warps have finished tile
+            // it - 2 (they are on tile it - 1 now): a ticket taken earlier
+            // would wait in the ring longer, the tiles before it in ticket
+            // order would be encoded later, and so the look-back -- which
+            // holds a stage until every earlier tile has its aggregate --
+            // would wait longer.  The copy still has a tile's time to land.
+            if (it >= 2) {
+                const uint32_t j = it - 2;
+                if (!mbar_wait_bounded(&ready[j % kStages], (j / kStages) & 1u, lc.lookback_ns + lc.copy_ns)) {
+                    atomicOr(lc.err, kErrTimeout);
+                    break;
+                }
+            }
             // a ticket is a tile of the launch's global list; find its field
             const uint64_t t = atomicAdd(lc.ticket, 1u);
             const bool more = t < lc.total_tiles;
