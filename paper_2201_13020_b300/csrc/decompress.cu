@@ -4,24 +4,26 @@
 // compressor gives each record's offset, so tiles decode independently: no
 // device-wide scan is left for decompression (the paper's GPU decoder, Sec.
 // V-B, runs a prefix scan of the mid-byte counts first).  Per CTA, a producer
-// thread, an indexing warp and eight decoding warps share two stage buffers
-// through mbarriers (head / full / indexed / consumed):
-//   producer (one thread): per tile, bulk-copies (cp.async.bulk) the record,
-//     the tile's mu values and a 16-byte-aligned window of its state bits into
-//     a stage.  The record's head (reqBits bytes and lead codes), the mu
+// thread, an indexing warp and eight decoding warps share up to six tiles in
+// flight through mbarriers per tile slot (head / full / indexed / consumed):
+//   producer (one thread): per tile, bulk-copies (cp.async.bulk) the record
+//     into a shared-memory ring, where it takes its own size, and the tile's
+//     mu values and a 16-byte-aligned window of its state bits into the
+//     tile's slot; it frees ring space in tile order as the decoders release
+//     tiles.  The record's head (reqBits bytes and lead codes), the mu
 //     values and the state bits complete one mbarrier and the rest of the
 //     record another, so that indexing starts before the mid bytes have
 //     landed.  The tile index entries are loaded one tile ahead, so no global
 //     latency sits between two copies;
-//   indexing warp: per stage, ranks every block among the tile's non-constant
+//   indexing warp: per tile, ranks every block among the tile's non-constant
 //     blocks (a popcount of the state bits), reads its reqBits byte and lead
 //     codes, checks them, counts its mid bytes, and scans the counts into
 //     each block's mid-byte offset; the total is checked against the record
 //     size, so that every later read is inside the record.  It writes a
-//     block table (offset, rank, reqBits) and the stage's verdict, one stage
-//     ahead of the decoders;
-//   eight decoding warps: decode the stage's record into registers, release
-//     the stage, then write their rows into a buffer of their own in the
+//     block table (offset, rank, reqBits) and the tile's verdict, ahead of
+//     the decoders;
+//   eight decoding warps: decode the tile's record into registers, release
+//     the tile, then write their rows into a buffer of their own in the
 //     128-byte-swizzled layout of the TMA tensor store and issue that store
 //     (one 2-D box of 32 rows per warp).  The ragged last row goes out with
 //     plain stores.  Warp 0 also checks that the record's padding is zero.
@@ -130,7 +132,7 @@ __device__ __forceinline__ uint32_t load_run(const uint8_t *buf, uint32_t p) {
     return __funnelshift_r(wp[0], wp[1], (p & 3u) * 8u);
 }
 
-constexpr int kDStages = 2;
+constexpr int kDSlots = 6;  // tiles in flight per CTA, at most (their records share one ring)
 constexpr int kDConsumers = kThreads;             // 8 decoding warps
 constexpr int kDWarps = kDConsumers / 32;
 constexpr int kDProducerWarp = kDWarps;           // warp 8
@@ -138,29 +140,38 @@ constexpr int kDIndexerWarp = kDWarps + 1;        // warp 9
 constexpr int kDThreads = kDConsumers + 64;
 constexpr uint32_t kBitsWindow = 64;  // 16-byte-aligned window holding a tile's state bits
 
-// Shared memory: kDStages stages (each: the record buffer, the tile's mu
-// values, its state-bit window and its block table), one output
-// buffer per decoding warp (its 32 * RPL rows of 128 bytes, 1024-byte aligned
-// for the swizzled tensor store), and the decode table.
+// Shared memory: one output buffer per decoding warp (its 32 * RPL rows of
+// 128 bytes, 1024-byte aligned for the swizzled tensor store), the decode
+// table, kDSlots tile slots (each: the tile's mu values, its state-bit window
+// and its block table), and the record ring, which takes the rest of the
+// CTA's share of the SM (two CTAs per SM for 32 KiB tiles, one for 64 KiB).
+// Records sit in the ring at their own size, so that at a typical ratio four
+// or five tiles are in flight, and at worst (every block raw) two.
 struct DSmem {
-    uint32_t stage;         // stage st starts at st * stage
-    uint32_t mu, bits, info;  // offsets inside a stage (the record buffer is at 0)
     uint32_t wbuf, wbuf_bytes;  // warp w's output buffer at wbuf + w * wbuf_bytes
-    uint32_t lut, total;
+    uint32_t lut;
+    uint32_t slots, slot;       // slot i at slots + i * slot
+    uint32_t mu, bits, info;    // offsets inside a slot
+    uint32_t ring, ring_bytes;  // the record ring (128-aligned, a multiple of 1024 bytes)
+    uint32_t total;
 };
 __host__ __device__ inline DSmem decompress_smem(uint32_t G, uint32_t b, uint32_t w) {
     DSmem s;
-    const uint32_t rec = record_max_bytes(G, b, w) + 16;  // + slack for the 8-byte run reads
-    const uint32_t body = (rec + 15) & ~15u;
-    const uint32_t mub = (G * w + 15) & ~15u;
-    s.stage = (body + mub + kBitsWindow + 8 * G + 1023) & ~1023u;  // + the block table
-    s.mu = body;
-    s.bits = s.mu + mub;
+    const uint32_t tile = G * b * w;  // 32 KiB, or 64 KiB for f64 with b = 1024
+    // (the per-CTA limit includes the static barriers and slot words)
+    const uint32_t budget = tile > 32768u ? 226u * 1024u : 112u * 1024u;
+    constexpr uint32_t kRealign = 1024;  // slack to realign the dynamic base to 1024
+    s.wbuf = 0;
+    s.wbuf_bytes = tile / kDWarps;  // 4 KiB per 128-byte row per lane
+    s.lut = s.wbuf + tile;
+    s.slots = s.lut + (uint32_t)sizeof(DecodeLut);
+    s.mu = 0;
+    s.bits = (G * w + 15) & ~15u;
     s.info = s.bits + kBitsWindow;
-    s.wbuf = kDStages * s.stage;
-    s.wbuf_bytes = (G * b * w) / kDWarps;  // 4 KiB per 128-byte row per lane
-    s.lut = s.wbuf + kDWarps * s.wbuf_bytes;
-    s.total = s.lut + (uint32_t)sizeof(DecodeLut) + 1024;  // + slack to realign the dynamic base
+    s.slot = s.info + ((8 * G + 15) & ~15u);
+    s.ring = (s.slots + kDSlots * s.slot + 127) & ~127u;
+    s.ring_bytes = (budget - kRealign - s.ring) & ~1023u;
+    s.total = s.ring + s.ring_bytes + kRealign;
     return s;
 }
 
@@ -191,14 +202,16 @@ __global__ void __launch_bounds__(kDThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
     extern __shared__ __align__(16) uint8_t smem_raw[];  // realigned to 1024 below
     // head: the record's head (reqBits bytes and lead codes), mu values and
     // state bits copied in; full: the rest of the record; indexed: the
-    // indexing warp has written the stage's block table and verdict;
-    // consumed: every decoding warp is done reading the stage
-    __shared__ __align__(8) uint64_t head[kDStages], full[kDStages], indexed[kDStages], consumed[kDStages];
+    // indexing warp has written the tile's block table and verdict;
+    // consumed: every decoding warp is done with the tile (record and slot)
+    __shared__ __align__(8) uint64_t head[kDSlots], full[kDSlots], indexed[kDSlots], consumed[kDSlots];
     // st_bad: set by the producer (index or header fault); st_verdict: set by
     // the indexing warp (0: decode, 3: corrupt record, 6: a wait ran out)
-    __shared__ uint32_t st_size[kDStages], st_bad[kDStages], st_verdict[kDStages], st_boff[kDStages];
-    __shared__ uint32_t st_used[kDStages];  // the record's bytes before its zero padding (when the verdict is 0)
-    __shared__ uint32_t st_field[kDStages], st_tile[kDStages];  // the stage's field and its local tile
+    __shared__ uint32_t st_size[kDSlots], st_bad[kDSlots], st_verdict[kDSlots], st_boff[kDSlots];
+    __shared__ uint32_t st_used[kDSlots];  // the record's bytes before its zero padding (when the verdict is 0)
+    __shared__ uint32_t st_field[kDSlots], st_tile[kDSlots];  // the slot's field and its local tile
+    __shared__ uint32_t st_off[kDSlots];                       // the slot's record: offset in the ring
+    __shared__ __align__(8) unsigned long long st_end[kDSlots];  // its end, as a position of the ring's sequence
 
     uint8_t *smem = smem_raw + ((1024u - (smem_addr(smem_raw) & 1023u)) & 1023u);
     const DSmem L = decompress_smem(G, b, w);
@@ -211,24 +224,45 @@ __global__ void __launch_bounds__(kDThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
         for (uint32_t i = tid; i < sizeof(DecodeLut) / 16; i += kDThreads) dst[i] = src[i];
     }
     if (tid == 0) {
-        for (int i = 0; i < kDStages; ++i) {
+        for (int i = 0; i < kDSlots; ++i) {
             mbar_init(&head[i], 1);
             mbar_init(&full[i], 1);
             mbar_init(&indexed[i], 1);
             mbar_init(&consumed[i], kDWarps);
-            st_size[i] = st_bad[i] = st_verdict[i] = st_boff[i] = st_used[i] = st_field[i] = st_tile[i] = 0;
+            st_size[i] = st_bad[i] = st_verdict[i] = st_boff[i] = st_used[i] = st_field[i] = st_tile[i] = st_off[i] = 0;
+            st_end[i] = 0;
         }
         fence_mbar_init();
     }
     __syncthreads();
 
     if (warp == kDProducerWarp) {
-        // ---- producer: record, mu and state-bit copies into the stages ------
+        // ---- producer: record copies into the ring, mu and state bits into the slots
         if (lane != 0) return;
         const uint32_t rec_max = record_max_bytes(G, b, w);
-        // per stage (bit st): is its last phase a copy (then it may still be in
+        // per slot (bit st): is its last phase a copy (then it may still be in
         // flight when the producer is done), and that phase's parity
         uint32_t copy_last = 0, copy_par = 0;
+        // The record ring, allocated here and released in tile order: a
+        // record takes [pos, pos + size + 16) of a sequence of positions that
+        // maps onto the ring modulo its size (the 16 bytes of slack serve the
+        // decoders' 8-byte run reads); it does not wrap around the ring's end
+        // but skips the bytes left there.  `freed` is the end of the last
+        // released record, `rel` the next tile to be released.
+        const uint32_t A = L.ring_bytes;
+        unsigned long long a_pos = 0, freed = 0;
+        uint32_t a_off = 0, rel = 0;
+        bool stop = false;
+        // wait until the decoders are done with tile `rel`, and release it
+        auto release_one = [&]() {
+            const int s2 = (int)(rel % kDSlots);
+            if (!mbar_wait_bounded(&consumed[s2], (rel / kDSlots) & 1u, 8 * lc.copy_ns)) {
+                stop = true;
+                return;
+            }
+            freed = st_end[s2];
+            ++rel;
+        };
         // the next tile (its field, local index and index entries), loaded one
         // tile ahead so that its entries arrive while this iteration waits
         uint32_t nf = 0, ntile = 0;
@@ -249,11 +283,13 @@ __global__ void __launch_bounds__(kDThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
             const uint32_t f = nf, tile = ntile;
             const DField *F = dfield_ptr<BATCH>(one, lc, f);
             const Geometry &g = F->g;
-            const int st = (int)(it % kDStages);
-            const uint32_t k = it / kDStages;
+            const int st = (int)(it % kDSlots);
+            const uint32_t k = it / kDSlots;
             const uint64_t r0 = n0, r1 = n1;
             load_next(tile64 + gridDim.x);
-            if (it >= kDStages && !mbar_wait_bounded(&consumed[st], (k - 1) & 1u, 8 * lc.copy_ns)) {
+            // the slot's previous tile (it - kDSlots) must be released
+            while (!stop && rel + kDSlots <= it) release_one();
+            if (stop) {
                 flag_status(F->status, 6u);
                 break;
             }
@@ -283,26 +319,48 @@ __global__ void __launch_bounds__(kDThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
                 const uint64_t sbA = sb0 & ~uint64_t(15);
                 const uint64_t sbE = pad16(g.off_state + (k0 + Gt + 7) / 8);
                 st_boff[st] = (uint32_t)(sb0 - sbA);
-                uint8_t *stage = smem + st * L.stage;
+                // the record's place in the ring: fits once nothing is held
+                // (the skipped bytes are then free as well) or once it ends
+                // within one ring of `freed`
+                const uint32_t need = size + 16;
+                const unsigned long long prev_end = a_pos;
+                if (a_off + need > A) {
+                    a_pos += A - a_off;
+                    a_off = 0;
+                }
+                const uint32_t r_off = a_off;
+                const unsigned long long r_end = a_pos + need;
+                while (!stop && rel < it && freed < prev_end && freed + A < r_end) release_one();
+                if (stop) {
+                    flag_status(F->status, 6u);
+                    break;
+                }
+                a_pos = r_end;
+                a_off += need;
+                st_off[st] = r_off;
+                st_end[st] = r_end;
+                uint8_t *rec = smem + L.ring + r_off;
+                uint8_t *slot = smem + L.slots + st * L.slot;
                 // the head first (what the indexing warp reads: at most
                 // G * (b/4 + 1) bytes, rounded up to 16), then the rest
                 const uint32_t hb = size < kHeadBytes ? size : kHeadBytes;
                 mbar_arrive_expect_tx(&head[st], hb + mu_bytes + (uint32_t)(sbE - sbA));
-                bulk_g2s(stage + L.bits, F->in + sbA, (uint32_t)(sbE - sbA), &head[st]);
-                if (hb) bulk_g2s(stage, F->in + g.off_rec + r0, hb, &head[st]);
-                bulk_g2s(stage + L.mu, F->in + g.off_mu + k0 * w, mu_bytes, &head[st]);
+                bulk_g2s(slot + L.bits, F->in + sbA, (uint32_t)(sbE - sbA), &head[st]);
+                if (hb) bulk_g2s(rec, F->in + g.off_rec + r0, hb, &head[st]);
+                bulk_g2s(slot + L.mu, F->in + g.off_mu + k0 * w, mu_bytes, &head[st]);
                 mbar_arrive_expect_tx(&full[st], size - hb);
-                if (size > hb) bulk_g2s(stage + hb, F->in + g.off_rec + r0 + hb, size - hb, &full[st]);
+                if (size > hb) bulk_g2s(rec + hb, F->in + g.off_rec + r0 + hb, size - hb, &full[st]);
                 copy_last |= 1u << st;
                 copy_par = (copy_par & ~(1u << st)) | ((k & 1u) << st);
             } else {
+                st_end[st] = a_pos;  // no record: releasing the tile frees nothing more
                 dmbar_arrive(&head[st]);
                 dmbar_arrive(&full[st]);
                 copy_last &= ~(1u << st);
             }
         }
         // do not leave while a copy may still be writing into shared memory
-        for (int st = 0; st < kDStages; ++st)
+        for (int st = 0; st < kDSlots; ++st)
             if ((copy_last >> st) & 1u) {
                 mbar_wait_bounded(&head[st], (copy_par >> st) & 1u, lc.copy_ns);
                 mbar_wait_bounded(&full[st], (copy_par >> st) & 1u, lc.copy_ns);
@@ -311,9 +369,9 @@ __global__ void __launch_bounds__(kDThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
     }
 
     if (warp == kDIndexerWarp) {
-        // ---- indexing warp: per stage, every block's rank among the tile's
+        // ---- indexing warp: per tile, every block's rank among the tile's
         // non-constant blocks, its reqBits byte and the offset of its mid
-        // bytes, and the record's checks; one stage ahead of the decoders.
+        // bytes, and the record's checks; ahead of the decoders.
         // Lane l takes blocks BPL*l .. BPL*l + BPL - 1 (consecutive, inside
         // one 32-bit word of state bits), so a scan over lanes orders them.
         constexpr uint32_t BPL = (G + 31) / 32;
@@ -322,23 +380,24 @@ __global__ void __launch_bounds__(kDThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
         for (uint32_t it = 0;; ++it) {
             const uint64_t tile64 = (uint64_t)blockIdx.x + (uint64_t)it * gridDim.x;
             if (tile64 >= lc.total_tiles) break;
-            const int st = (int)(it % kDStages);
-            const uint32_t k = it / kDStages;
+            const int st = (int)(it % kDSlots);
+            const uint32_t k = it / kDSlots;
             const bool waited = mbar_wait_bounded(&head[st], k & 1u, lc.copy_ns);
             const DField *Fd = dfield_ptr<BATCH>(one, lc, st_field[st]);
             const Geometry &g = Fd->g;
             const uint32_t tile = st_tile[st];
             const uint32_t size = st_size[st];
             const bool pbad = !waited || st_bad[st] != 0;
-            const uint8_t *rec = smem + st * L.stage;
-            uint2 *info = reinterpret_cast<uint2 *>(smem + st * L.stage + L.info);
+            const uint8_t *rec = smem + L.ring + st_off[st];
+            const uint8_t *slot = smem + L.slots + st * L.slot;
+            uint2 *info = reinterpret_cast<uint2 *>(smem + L.slots + st * L.slot + L.info);
             const uint64_t k0 = (uint64_t)tile * G;
             const uint32_t Gt = pbad ? 0u : (uint32_t)min_u64(G, g.nb - k0);
 
             // the tile's state bits (bits at or past Gt cleared)
             uint32_t sw[NSW];
             {
-                const uint8_t *stb = rec + L.bits + st_boff[st];
+                const uint8_t *stb = slot + L.bits + st_boff[st];
                 if constexpr (G >= 32) {
                     // the tile's bits start at a multiple of 4 bytes
 #pragma unroll
@@ -451,9 +510,9 @@ __global__ void __launch_bounds__(kDThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
     for (uint32_t it = 0;; ++it) {
         const uint64_t tile64 = (uint64_t)blockIdx.x + (uint64_t)it * gridDim.x;
         if (tile64 >= lc.total_tiles) break;
-        const int st = (int)(it % kDStages);
-        const uint32_t k = it / kDStages;
-        // the stage's bytes and its block table; a wait that runs out stops
+        const int st = (int)(it % kDSlots);
+        const uint32_t k = it / kDSlots;
+        // the tile's bytes and its block table; a wait that runs out stops
         // this warp
         if (!mbar_wait_bounded(&head[st], k & 1u, lc.copy_ns) || !mbar_wait_bounded(&full[st], k & 1u, lc.copy_ns) ||
             !mbar_wait_bounded(&indexed[st], k & 1u, 2 * lc.copy_ns)) {
@@ -464,7 +523,8 @@ __global__ void __launch_bounds__(kDThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
         const Geometry &g = Fd->g;
         const uint32_t tile = st_tile[st];
         const bool bad = st_verdict[st] != 0;
-        const uint8_t *rec = smem + st * L.stage;
+        const uint8_t *rec = smem + L.ring + st_off[st];
+        const uint8_t *slot = smem + L.slots + st * L.slot;
         const uint64_t k0 = (uint64_t)tile * G;
         const uint32_t Gt = (uint32_t)min_u64(G, g.nb - k0);
 
@@ -480,7 +540,7 @@ __global__ void __launch_bounds__(kDThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
         U x[VPL];
         if (!bad) {
             // ---- the block's entry: mid-byte offset, rank, reqBits ----------
-            const uint2 bi = exists ? reinterpret_cast<const uint2 *>(rec + L.info)[blk] : make_uint2(0, 0);
+            const uint2 bi = exists ? reinterpret_cast<const uint2 *>(slot + L.info)[blk] : make_uint2(0, 0);
             const uint32_t mbase = bi.x, rank = bi.y & 0xFFFFu, rq = bi.y >> 16;
             const bool raw = rq == 0xFFu;
             const bool coded = rq != 0u && !raw;
@@ -500,7 +560,7 @@ __global__ void __launch_bounds__(kDThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
                     codes[0] = *reinterpret_cast<const uint32_t *>(lead);
                 }
             }
-            const U mu_bits = exists ? reinterpret_cast<const U *>(rec + L.mu)[blk] : U(0);
+            const U mu_bits = exists ? reinterpret_cast<const U *>(slot + L.mu)[blk] : U(0);
 
             // ---- decode --------------------------------------------------
             using CntT = std::conditional_t<(LPB * VPL > 1023), unsigned long long, uint32_t>;
@@ -629,7 +689,7 @@ __global__ void __launch_bounds__(kDThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
                 if (used + lane < st_size[st] && rec[used + lane]) flag_status(Fd->status, 3u);
             }
         }
-        // this warp no longer reads the stage
+        // this warp no longer reads the tile's record or slot
         __syncwarp();
         if (lane == 0) dmbar_arrive(&consumed[st]);
         if (bad) continue;
@@ -707,6 +767,7 @@ template <typename T, int LPB, int VPL>
 cudaError_t launch_t(const DField &one, const DecompressLaunch &lc, int ctas_per_sm, cudaStream_t stream) {
     constexpr uint32_t b = (uint32_t)(LPB * VPL), w = (uint32_t)Fmt<T>::w;
     const DSmem L = decompress_smem(tile_blocks(b, w), b, w);
+    if (L.ring_bytes < record_max_bytes(tile_blocks(b, w), b, w) + 16) return cudaErrorInvalidValue;
     auto kern = lc.fields ? decompress_kernel<T, LPB, VPL, true> : decompress_kernel<T, LPB, VPL, false>;
     // per device and kernel: the shared-memory attribute and the occupancy,
     // set up on first use (a launch then only reads them)
