@@ -371,16 +371,20 @@ __device__ __forceinline__ void encode_lane(typename Fmt<T>::U (&x)[VPL], uint32
 #pragma unroll
     for (int i = 0; i < NCODE; ++i) codes[i] = 0;
     {
-        U prev = __shfl_up_sync(kFull, x[VPL - 1], 1);
+        // Only the top lmax <= 3 bytes decide a code, and they lie in the
+        // word's top 32 bits: the count runs on those (one 32-bit xor and
+        // clz per value, also for f64)
+        uint32_t prev = (uint32_t)(__shfl_up_sync(kFull, x[VPL - 1], 1) >> (W - 32));
         if (sub == 0) prev = 0;
         // a set bit in byte lmax (counted from the top) caps the count at lmax
-        const U cap = U(1) << (W - 1 - 8 * lmax);
+        const uint32_t cap = 1u << (31 - 8 * lmax);
 #pragma unroll
         for (int m = 0; m < VPL; ++m) {
-            int l = F::clz((x[m] ^ prev) | cap) >> 3;
+            const uint32_t top = (uint32_t)(x[m] >> (W - 32));
+            int l = __clz((top ^ prev) | cap) >> 3;
             if (!FULL && m >= nvalid) l = 0;
             codes[m >> 4] += (uint32_t)l << (2 * (m & 15));
-            prev = x[m];
+            prev = top;
         }
     }
     uint32_t suml = 0;

@@ -88,10 +88,15 @@ __device__ __forceinline__ U top_bytes_mask(int q) {
 template <typename T>
 __device__ __forceinline__ bool within(T a, T b, T e) {
     using F = Fmt<T>;
+    using U = typename F::U;
     T s = F::sub(a, b);
-    T as = fabs(s);
-    if (as < e) return true;
-    if (!(as == e)) return false;  // > e, or an overflow to infinity
+    // |s| against e on the IEEE bit patterns, which order the non-negative
+    // values (and place NaNs above infinity); integer compares, not
+    // floating-point ones, which are slow for f64
+    const U as = F::bits(s) & ~(U(1) << (F::W - 1));
+    const U eb = F::bits(e);
+    if (as < eb) return true;
+    if (as != eb) return false;  // > e, NaN, or an overflow to infinity
     T y = -b;
     T bv = F::sub(s, a);
     T av = F::sub(s, bv);
