@@ -160,3 +160,48 @@ def test_record_sizes_change_tile_to_tile():
         assert np.array_equal(yr.view(np.uint32), y_host[v0:v0 + yr.size].view(np.uint32))
     del x, y, s, d
     torch.cuda.empty_cache()
+
+
+def test_raw_tiles_of_the_largest_record_size():
+    """Half the tiles, chosen at random, hold a NaN in every block: each of their blocks is
+    stored raw, so their records have the largest size a tile can have.  The decoder's
+    shared-memory record ring then holds only two of them, and wraps often.  The other tiles
+    are a smooth random walk.  2^24 values: every CTA handles several tiles of each kind."""
+    torch.cuda.empty_cache()
+    n, b, per_tile = 1 << 24, 128, 64 * 128
+    ntiles = n // per_tile
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(43)
+    x = torch.cumsum(torch.randn(n, generator=gen, device="cuda"), 0) * 1e-3
+    raw_tiles = torch.rand(ntiles, generator=gen, device="cuda") < 0.5
+    nan_blocks = raw_tiles[torch.arange(n // b, device="cuda") // 64]
+    xv = x.view(-1, b)
+    xv[nan_blocks, 5] = float("nan")
+    eb = 1e-3
+    s = szx.compress(x, eb)
+    y = szx.decompress(s)
+    yv = y.view(-1, b)
+    # raw blocks come back bit for bit; the others within the bound
+    assert torch.equal(xv[nan_blocks].view(torch.int32), yv[nan_blocks].view(torch.int32))
+    e = oracle.error_bound(eb, oracle.F32)
+    d = (xv[~nan_blocks].double() - yv[~nan_blocks].double()).abs()
+    assert float(d.max()) <= e * (1 + 2 ** -20)
+    stream = s.cpu().numpy()
+    nb = n // b
+    off_index = 64 + ss.pad16(-(-nb // 8)) + ss.pad16(nb * 4)
+    idx = stream[off_index:off_index + 8 * (ntiles + 1)].view(np.uint64).astype(np.int64)
+    sizes = np.diff(idx)
+    largest = ss.pad16(64 * (b // 4 + 1) + 64 * b * 4)
+    raw_host = raw_tiles.cpu().numpy()
+    assert (sizes[raw_host] == largest).all()
+    assert (sizes[~raw_host] < largest // 2).all()
+    x_host, y_host = x.cpu().numpy(), y.cpu().numpy()
+    rng = np.random.default_rng(6)
+    tiles = sorted(set([0, ntiles - 1] + rng.choice(ntiles, size=16, replace=False).tolist()))
+    for t in tiles:
+        ref = tile_slice_parity(x_host, stream, t, b, 4, eb)
+        yr = oracle.decompress(ref)
+        v0 = t * per_tile
+        assert np.array_equal(yr.view(np.uint32), y_host[v0:v0 + yr.size].view(np.uint32))
+    del x, y, s, d
+    torch.cuda.empty_cache()
