@@ -2,11 +2,12 @@
 //
 // A plan groups the fields by (dtype, block): each group is one persistent
 // launch of the same kernels as the single-field calls, over the global list
-// of all its fields' tiles (one ticket counter per group for compression, a
-// static split for decompression), with the per-field descriptors in a table
-// in device memory.  The caller's workspace holds, in order:
+// of all its fields' tiles, handed out by one ticket counter per group, with
+// the per-field descriptors in a table in device memory.  The caller's
+// workspace holds, in order:
 //   descriptor tables (one CField or DField per field, 64-byte aligned),
-//   per-group counters (ticket, done, error: 16 bytes each),
+//   per-group counters (ticket, done, error: 16 bytes each; decompression
+//   uses the ticket only),
 //   per-field compression workspaces (counters + look-back words, 256-byte
 //   aligned; compression only).
 // Running a plan is one cudaMemsetAsync (counters and workspaces) plus one
@@ -158,7 +159,9 @@ szx_status szx_batch_decompress_plan(const szx_stream_field *streams, int count,
         return st;
     }
     p->table_bytes = align_up((uint64_t)count * sizeof(DField), 256);
-    p->counters_off = p->zero_off = p->total_bytes = p->table_bytes;
+    // per group, a tile ticket (16 bytes, as for compression), zeroed per run
+    p->counters_off = p->zero_off = p->table_bytes;
+    p->total_bytes = p->counters_off + align_up(16 * p->groups.size(), 256);
     *plan = p;
     return SZX_OK;
 }
@@ -206,10 +209,9 @@ szx_status szx_batch_run(const szx_batch_plan *p, void *d_ws, szx_stream_t strea
     if (d_ws != p->uploaded_ws) return SZX_ERR_INVALID;  // the tables point into that workspace
     cudaStream_t s = (cudaStream_t)stream;
     uint8_t *base = static_cast<uint8_t *>(d_ws);
-    if (p->compress) {
-        if (cudaMemsetAsync(base + p->zero_off, 0, p->total_bytes - p->zero_off, s) != cudaSuccess)
-            return SZX_ERR_CUDA;
-    } else {
+    // counters (and, for compression, the fields' workspaces) start at zero
+    if (cudaMemsetAsync(base + p->zero_off, 0, p->total_bytes - p->zero_off, s) != cudaSuccess) return SZX_ERR_CUDA;
+    if (!p->compress) {
         // every stream's status word starts at SZX_OK
         for (const szx_stream_field &sf : p->streams)
             if (sf.d_status && cudaMemsetAsync(sf.d_status, 0, sizeof(uint32_t), s) != cudaSuccess)
@@ -224,7 +226,8 @@ szx_status szx_batch_run(const szx_batch_plan *p, void *d_ws, szx_stream_t strea
             e = launch_compress_batch(tbl, g.count, g.tiles, ctr, g.dtype, g.block, g.ctas_per_sm, s);
         } else {
             const DField *tbl = reinterpret_cast<const DField *>(base) + g.first;
-            e = launch_decompress_batch(tbl, g.count, g.tiles, g.dtype, g.block, g.ctas_per_sm, s);
+            uint32_t *ticket = reinterpret_cast<uint32_t *>(base + p->counters_off + 16 * gi);
+            e = launch_decompress_batch(tbl, g.count, g.tiles, ticket, g.dtype, g.block, g.ctas_per_sm, s);
         }
         if (e != cudaSuccess) return SZX_ERR_CUDA;
     }

@@ -56,6 +56,9 @@ struct DecompressLaunch {
     uint32_t nfields;
     uint64_t total_tiles;  // tiles of all fields, field after field
     uint64_t copy_ns;      // wall-time limit of a copy wait
+    // tile tickets (zeroed before the launch): CTAs take tiles as they go; or
+    // null: CTA c takes tiles c, c + gridDim.x, ...
+    uint32_t *ticket;
 };
 
 template <bool BATCH>
@@ -267,8 +270,14 @@ __global__ void __launch_bounds__(kDThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
         // tile ahead so that its entries arrive while this iteration waits
         uint32_t nf = 0, ntile = 0;
         uint64_t n0 = 0, n1 = 0;
+        bool nmore = false;
+        // the CTA's i-th tile: a ticket, or its share of the static split
+        auto take = [&](uint32_t i) -> uint64_t {
+            return lc.ticket ? (uint64_t)atomicAdd(lc.ticket, 1u) : (uint64_t)blockIdx.x + (uint64_t)i * gridDim.x;
+        };
         auto load_next = [&](uint64_t t) {
-            if (t >= lc.total_tiles) return;
+            nmore = t < lc.total_tiles;
+            if (!nmore) return;
             nf = dfield_of<BATCH>(lc, t);
             const DField *F = dfield_ptr<BATCH>(one, lc, nf);
             ntile = (uint32_t)(t - F->tile0 + F->tile_lo);
@@ -276,21 +285,28 @@ __global__ void __launch_bounds__(kDThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
             n0 = idx[ntile];
             n1 = idx[ntile + 1];
         };
-        load_next(blockIdx.x);
+        load_next(take(0));
         for (uint32_t it = 0;; ++it) {
-            const uint64_t tile64 = (uint64_t)blockIdx.x + (uint64_t)it * gridDim.x;
-            if (tile64 >= lc.total_tiles) break;
+            const bool more = nmore;
             const uint32_t f = nf, tile = ntile;
             const DField *F = dfield_ptr<BATCH>(one, lc, f);
             const Geometry &g = F->g;
             const int st = (int)(it % kDSlots);
             const uint32_t k = it / kDSlots;
             const uint64_t r0 = n0, r1 = n1;
-            load_next(tile64 + gridDim.x);
+            if (more) load_next(take(it + 1));
             // the slot's previous tile (it - kDSlots) must be released
             while (!stop && rel + kDSlots <= it) release_one();
             if (stop) {
                 flag_status(F->status, 6u);
+                break;
+            }
+            if (!more) {
+                // no more tiles: the slot carries the end to the other warps
+                st_tile[st] = 0xFFFFFFFFu;
+                dmbar_arrive(&head[st]);
+                dmbar_arrive(&full[st]);
+                copy_last &= ~(1u << st);
                 break;
             }
             uint32_t bad = 0;
@@ -378,11 +394,14 @@ __global__ void __launch_bounds__(kDThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
         constexpr uint32_t NSW = (G + 31) / 32;  // 32-bit words of state bits
         static_assert(32 % BPL == 0, "a lane's blocks share one state word");
         for (uint32_t it = 0;; ++it) {
-            const uint64_t tile64 = (uint64_t)blockIdx.x + (uint64_t)it * gridDim.x;
-            if (tile64 >= lc.total_tiles) break;
             const int st = (int)(it % kDSlots);
             const uint32_t k = it / kDSlots;
             const bool waited = mbar_wait_bounded(&head[st], k & 1u, lc.copy_ns);
+            if (waited && st_tile[st] == 0xFFFFFFFFu) {
+                // the end: pass it on to the decoders
+                if (lane == 0) dmbar_arrive(&indexed[st]);
+                break;
+            }
             const DField *Fd = dfield_ptr<BATCH>(one, lc, st_field[st]);
             const Geometry &g = Fd->g;
             const uint32_t tile = st_tile[st];
@@ -508,8 +527,6 @@ __global__ void __launch_bounds__(kDThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
     uint8_t *wbuf = smem + L.wbuf + warp * L.wbuf_bytes;
     const uint32_t lane_row0 = (uint32_t)(lane * RPL);  // inside the warp's rows
     for (uint32_t it = 0;; ++it) {
-        const uint64_t tile64 = (uint64_t)blockIdx.x + (uint64_t)it * gridDim.x;
-        if (tile64 >= lc.total_tiles) break;
         const int st = (int)(it % kDSlots);
         const uint32_t k = it / kDSlots;
         // the tile's bytes and its block table; a wait that runs out stops
@@ -519,6 +536,7 @@ __global__ void __launch_bounds__(kDThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
             if (lane == 0) flag_status(dfield_ptr<BATCH>(one, lc, st_field[st])->status, 6u);
             break;
         }
+        if (st_tile[st] == 0xFFFFFFFFu) break;  // no more tiles
         const DField *Fd = dfield_ptr<BATCH>(one, lc, st_field[st]);
         const Geometry &g = Fd->g;
         const uint32_t tile = st_tile[st];
@@ -851,11 +869,12 @@ cudaError_t launch_decompress(const void *in, uint64_t in_bytes, uint64_t total_
     lc.total_tiles = decompress_field_tiles(&one);
     if (!lc.total_tiles) return cudaSuccess;
     lc.copy_ns = copy_limit_ns();
+    lc.ticket = nullptr;  // no device workspace here: the static split
     return ddispatch(dtype, block, one, lc, 0, stream);
 }
 
-cudaError_t launch_decompress_batch(const void *d_fields, uint32_t nfields, uint64_t total_tiles, int dtype,
-                                    uint32_t block, int ctas_per_sm, cudaStream_t stream) {
+cudaError_t launch_decompress_batch(const void *d_fields, uint32_t nfields, uint64_t total_tiles, uint32_t *d_ticket,
+                                    int dtype, uint32_t block, int ctas_per_sm, cudaStream_t stream) {
     DField one;
     std::memset(&one, 0, sizeof(one));
     DecompressLaunch lc;
@@ -863,6 +882,7 @@ cudaError_t launch_decompress_batch(const void *d_fields, uint32_t nfields, uint
     lc.nfields = nfields;
     lc.total_tiles = total_tiles;
     lc.copy_ns = copy_limit_ns();
+    lc.ticket = d_ticket;
     return ddispatch(dtype, block, one, lc, ctas_per_sm, stream);
 }
 

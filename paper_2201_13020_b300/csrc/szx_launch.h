@@ -65,9 +65,11 @@ void fill_decompress_field(DField *f, const void *in, uint64_t total_bytes, uint
 uint64_t decompress_field_tiles(const DField *f);
 
 // Enqueue one persistent decompression launch over nfields descriptors at
-// d_fields (device memory, 64-byte aligned; all of dtype and block).
-cudaError_t launch_decompress_batch(const void *d_fields, uint32_t nfields, uint64_t total_tiles, int dtype,
-                                    uint32_t block, int ctas_per_sm, cudaStream_t stream);
+// d_fields (device memory, 64-byte aligned; all of dtype and block).  CTAs
+// take tiles by ticket from *d_ticket (device memory, zero before the launch),
+// or, if d_ticket is null, by a static split.
+cudaError_t launch_decompress_batch(const void *d_fields, uint32_t nfields, uint64_t total_tiles, uint32_t *d_ticket,
+                                    int dtype, uint32_t block, int ctas_per_sm, cudaStream_t stream);
 
 // Enqueue the decompression of a stream of total_bytes whose header says
 // (n, dtype, block).  Errors are folded into *d_status with atomicMax as
