@@ -56,8 +56,8 @@ struct DecompressLaunch {
     uint32_t nfields;
     uint64_t total_tiles;  // tiles of all fields, field after field
     uint64_t copy_ns;      // wall-time limit of a copy wait
-    // tile tickets (zeroed before the launch): CTAs take tiles as they go; or
-    // null: CTA c takes tiles c, c + gridDim.x, ...
+    // batches: tile tickets (zeroed before the launch), CTAs take tiles as
+    // they go; a single stream: null, CTA c takes tiles c, c + gridDim.x, ...
     uint32_t *ticket;
 };
 
@@ -271,9 +271,10 @@ __global__ void __launch_bounds__(kDThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
         uint32_t nf = 0, ntile = 0;
         uint64_t n0 = 0, n1 = 0;
         bool nmore = false;
-        // the CTA's i-th tile: a ticket, or its share of the static split
+        // the CTA's i-th tile: a ticket (batches), or its share of the static split
         auto take = [&](uint32_t i) -> uint64_t {
-            return lc.ticket ? (uint64_t)atomicAdd(lc.ticket, 1u) : (uint64_t)blockIdx.x + (uint64_t)i * gridDim.x;
+            if constexpr (BATCH) return (uint64_t)atomicAdd(lc.ticket, 1u);
+            else return (uint64_t)blockIdx.x + (uint64_t)i * gridDim.x;
         };
         auto load_next = [&](uint64_t t) {
             nmore = t < lc.total_tiles;
@@ -295,6 +296,8 @@ __global__ void __launch_bounds__(kDThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
             const uint32_t k = it / kDSlots;
             const uint64_t r0 = n0, r1 = n1;
             if (more) load_next(take(it + 1));
+            if constexpr (!BATCH)
+                if (!more) break;  // the static split: the other warps count tiles themselves
             // the slot's previous tile (it - kDSlots) must be released
             while (!stop && rel + kDSlots <= it) release_one();
             if (stop) {
@@ -302,7 +305,7 @@ __global__ void __launch_bounds__(kDThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
                 break;
             }
             if (!more) {
-                // no more tiles: the slot carries the end to the other warps
+                // no more tickets: the slot carries the end to the other warps
                 st_tile[st] = 0xFFFFFFFFu;
                 dmbar_arrive(&head[st]);
                 dmbar_arrive(&full[st]);
@@ -394,10 +397,12 @@ __global__ void __launch_bounds__(kDThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
         constexpr uint32_t NSW = (G + 31) / 32;  // 32-bit words of state bits
         static_assert(32 % BPL == 0, "a lane's blocks share one state word");
         for (uint32_t it = 0;; ++it) {
+            if constexpr (!BATCH)
+                if ((uint64_t)blockIdx.x + (uint64_t)it * gridDim.x >= lc.total_tiles) break;
             const int st = (int)(it % kDSlots);
             const uint32_t k = it / kDSlots;
             const bool waited = mbar_wait_bounded(&head[st], k & 1u, lc.copy_ns);
-            if (waited && st_tile[st] == 0xFFFFFFFFu) {
+            if (BATCH && waited && st_tile[st] == 0xFFFFFFFFu) {
                 // the end: pass it on to the decoders
                 if (lane == 0) dmbar_arrive(&indexed[st]);
                 break;
@@ -527,6 +532,8 @@ __global__ void __launch_bounds__(kDThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
     uint8_t *wbuf = smem + L.wbuf + warp * L.wbuf_bytes;
     const uint32_t lane_row0 = (uint32_t)(lane * RPL);  // inside the warp's rows
     for (uint32_t it = 0;; ++it) {
+        if constexpr (!BATCH)
+            if ((uint64_t)blockIdx.x + (uint64_t)it * gridDim.x >= lc.total_tiles) break;
         const int st = (int)(it % kDSlots);
         const uint32_t k = it / kDSlots;
         // the tile's bytes and its block table; a wait that runs out stops
@@ -536,7 +543,8 @@ __global__ void __launch_bounds__(kDThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
             if (lane == 0) flag_status(dfield_ptr<BATCH>(one, lc, st_field[st])->status, 6u);
             break;
         }
-        if (st_tile[st] == 0xFFFFFFFFu) break;  // no more tiles
+        if constexpr (BATCH)
+            if (st_tile[st] == 0xFFFFFFFFu) break;  // no more tickets
         const DField *Fd = dfield_ptr<BATCH>(one, lc, st_field[st]);
         const Geometry &g = Fd->g;
         const uint32_t tile = st_tile[st];
