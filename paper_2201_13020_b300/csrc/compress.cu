@@ -737,241 +737,253 @@ __global__ void __launch_bounds__(kCThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
         const uint64_t rows_full = Fd->rows_full;
         const bool tma = Fd->use_tma && row0 < rows_full;
 
-        // ---- 1. block statistics and encoding (registers) -------------------
-        const int sub = lane % LPB;
-        const uint32_t blk = (uint32_t)(warp * BPW + lane / LPB);
-        const bool exists = blk < Gt;
-        const uint64_t kg = k0 + blk;
-        const int len = exists ? (int)min_u64(b, g.n - kg * b) : 0;
-        int nvalid = len - sub * VPL;
-        nvalid = nvalid < 0 ? 0 : (nvalid > VPL ? VPL : nvalid);
-        const bool full_lane = nvalid == VPL;
-        const uint32_t lane_row0 = (uint32_t)((warp * 32 + lane) * RPL);
-        // the lane's values in global memory (read only below nvalid)
-        const U *src = reinterpret_cast<const U *>(Fd->in) + kg * b + sub * VPL;
-
-        // rows the tensor copy brought in come from shared memory; the
-        // input's ragged end (or every row without the tensor copy) from global
-        constexpr int VPR = 128 / w;  // values per row
-        U x[VPL];
-#pragma unroll
-        for (int rr = 0; rr < RPL; ++rr) {
-            const uint32_t rowi = lane_row0 + rr;
-            if (tma && row0 + rowi < rows_full) {
-#pragma unroll
-                for (int c = 0; c < 8; ++c) {
-                    const uint4 v = *reinterpret_cast<const uint4 *>(buf + (rowi << 7) + ((c ^ (rowi & 7u)) << 4));
-                    const U *u = reinterpret_cast<const U *>(&v);
-#pragma unroll
-                    for (int kk = 0; kk < 16 / w; ++kk) x[rr * VPR + c * (16 / w) + kk] = u[kk];
-                }
-            } else {
-#pragma unroll
-                for (int m = 0; m < VPR; ++m) x[rr * VPR + m] = rr * VPR + m < nvalid ? src[rr * VPR + m] : U(0);
+        // Tiles wholly inside the input (all but its ragged end) run a copy of
+        // the work below compiled with every block full and every row copied
+        // in: no checks of the input's end per block, row or group of values
+        const bool full_tile = tma && (k0 + G) * b <= g.n;
+        auto tile_body = [&](auto full_c) -> bool {
+            constexpr bool FT = decltype(full_c)::value;
+            // ---- 1. block statistics and encoding (registers) -------------------
+            const int sub = lane % LPB;
+            const uint32_t blk = (uint32_t)(warp * BPW + lane / LPB);
+            const bool exists = FT || blk < Gt;
+            const uint64_t kg = k0 + blk;
+            const int len = FT ? (int)b : (exists ? (int)min_u64(b, g.n - kg * b) : 0);
+            int nvalid = VPL;
+            if constexpr (!FT) {
+                nvalid = len - sub * VPL;
+                nvalid = nvalid < 0 ? 0 : (nvalid > VPL ? VPL : nvalid);
             }
-        }
-        // this lane's rows are read: clear them, the buffer becomes the record
-        // (the exact slow path below re-reads the input from global memory)
-        {
-            const uint4 z = make_uint4(0, 0, 0, 0);
-#pragma unroll
+            const bool full_lane = FT || nvalid == VPL;
+            const uint32_t lane_row0 = (uint32_t)((warp * 32 + lane) * RPL);
+            // the lane's values in global memory (read only below nvalid)
+            const U *src = reinterpret_cast<const U *>(Fd->in) + kg * b + sub * VPL;
+
+            // rows the tensor copy brought in come from shared memory; the
+            // input's ragged end (or every row without the tensor copy) from global
+            constexpr int VPR = 128 / w;  // values per row
+            U x[VPL];
+    #pragma unroll
             for (int rr = 0; rr < RPL; ++rr) {
                 const uint32_t rowi = lane_row0 + rr;
-#pragma unroll
-                for (int c = 0; c < 8; ++c) *reinterpret_cast<uint4 *>(buf + (rowi << 7) + ((c ^ (rowi & 7u)) << 4)) = z;
-            }
-            if (warp == kConsumerWarps - 1)
-                for (uint32_t i = 32768u * RPL + 16u * lane; i < L.buf_bytes; i += 16u * 32u)
-                    *reinterpret_cast<uint4 *>(buf + i) = z;
-        }
-        uint32_t codes[NCODE];
-        int kind, req, req0;
-        T mu;
-        uint32_t mk_lane;
-        if (__all_sync(kFull, full_lane)) {
-            encode_lane<T, LPB, VPL, true>(x, codes, kind, req, req0, mu, mk_lane, src, nvalid, exists, e,
-                                           Fd->e_bits, Fd->ws, tile);
-        } else {
-            encode_lane<T, LPB, VPL, false>(x, codes, kind, req, req0, mu, mk_lane, src, nvalid, exists, e,
-                                            Fd->e_bits, Fd->ws, tile);
-        }
-        const bool lead = exists && sub == 0;  // the block's first lane
-        if (lead) {
-            sm_kind[blk] = (uint8_t)kind;
-            reinterpret_cast<U *>(Fd->out + g.off_mu)[kg] = kind == kRaw ? U(0) : F::bits(mu);
-        }
-        // the warp's totals; its blocks are consecutive, so an exclusive scan
-        // over lanes gives each block's mid-byte offset inside the warp's share
-        uint32_t mid_w;
-        const uint32_t lane_excl = warp_exclusive_scan(mk_lane, &mid_w);
-        const uint32_t nonc_bal = __ballot_sync(kFull, lead && kind != kConst);
-        const uint32_t raw_bal = __ballot_sync(kFull, lead && kind == kRaw);
-        const uint32_t esc_bal = __ballot_sync(kFull, lead && kind == kNonConst && req > req0);
-        // per warp: (non-constant blocks << 20 | mid bytes), raw blocks, escalated blocks
-        if (lane == 0) sm_w[warp] = make_uint4((uint32_t)__popc(nonc_bal) << 20 | mid_w, __popc(raw_bal), __popc(esc_bal), 0);
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&encoded[st]);
-
-        // per-lane counts of values with code <= j (j = 0, 1, 2), packed in
-        // FB-bit fields, and their exclusive scan over the block's lanes;
-        // nothing here depends on the other warps, so it runs before the wait.
-        // Every lane runs this (the shuffles need the whole warp); lanes of
-        // constant or raw blocks contribute nothing.
-        const uint32_t mk_blk_excl = __shfl_sync(kFull, lane_excl, lane & ~(LPB - 1));
-        const uint32_t rank_in_warp = __popc(nonc_bal & ((1u << (lane & ~(LPB - 1))) - 1u));
-        using CntT = std::conditional_t<(LPB * VPL > 1023), unsigned long long, uint32_t>;
-        constexpr int FB = LPB * VPL > 1023 ? 16 : 10;
-        constexpr CntT FM = (CntT(1) << FB) - 1;
-        CntT cnt = 0;
-        if (exists && kind == kNonConst) {
-#pragma unroll
-            for (int i = 0; i < NCODE; ++i) {
-                const int nv = nvalid - 16 * i;
-                const uint32_t vm = nv >= 16 ? 0x55555555u : (nv <= 0 ? 0u : (0x55555555u >> (2 * (16 - nv))));
-                const uint32_t lo = codes[i] & 0x55555555u, hi = (codes[i] >> 1) & 0x55555555u;
-                cnt += (CntT)__popc(~(lo | hi) & vm) | ((CntT)__popc(~hi & vm) << FB) |
-                       ((CntT)__popc(~(lo & hi) & vm) << (2 * FB));
-            }
-        }
-        CntT incl = cnt;
-#pragma unroll
-        for (int d = 1; d < LPB; d <<= 1) {
-            const CntT y = __shfl_up_sync(kFull, incl, d);
-            if (sub >= d) incl += y;
-        }
-        const CntT tot = __shfl_sync(kFull, incl, (lane & ~(LPB - 1)) + LPB - 1);
-        const CntT off = incl - cnt;
-
-        if (!mbar_wait_bounded(&encoded[st], k & 1u, lc.lookback_ns + lc.copy_ns)) {
-            // a warp of this CTA never finished the tile: give up
-            if (lane == 0) {
-                atomicOr(lc.err, kErrTimeout);
-                st_tile[st] = 0xFFFFFFFFu;
-                mbar_arrive(&ready[st]);
-            }
-            break;
-        }
-
-        // ---- 2. tile totals and the aggregate for the look-back --------------
-        // lane i holds warp i's (nn << 20 | mid); warp reductions give the
-        // tile's totals and the sums over the warps before this one
-        const uint32_t wt = lane < kConsumerWarps ? sm_w[lane].x : 0u;
-        const uint32_t nm_t = __reduce_add_sync(kFull, wt);
-        const uint32_t nm_before = __reduce_add_sync(kFull, lane < warp ? wt : 0u);
-        const uint32_t nn_t = nm_t >> 20, mid_t = nm_t & 0xFFFFFu;
-        const uint32_t nn_before = nm_before >> 20, mid_before = nm_before & 0xFFFFFu;
-        const uint32_t rec_bytes = (uint32_t)pad16((uint64_t)nn_t * (b / 4 + 1) + mid_t);
-        if (warp == 0 && lane == 0) {
-            st_rec[st] = rec_bytes;
-            st_relaxed_u64(&Fd->lookback[tile], kFlagAgg | rec_bytes);
-        }
-        if (SZX_CHECKS && rec_bytes > record_max_bytes(G, b, w) && tid == 0) report_bad(Fd->ws, tile, 2);
-        const uint32_t rank = nn_before + rank_in_warp;
-
-        // ---- 3. the record --------------------------------------------------
-        uint32_t *words = reinterpret_cast<uint32_t *>(buf);
-        // every record write goes through put() (positions in bits, c8 = 8 x
-        // bytes): a self-checked build verifies that it lands inside the record
-        auto put = [&](uint32_t pb, uint32_t run, uint32_t c8) {
-            if (SZX_CHECKS && ((pb >> 3) + 8 > L.buf_bytes || ((pb + c8) >> 3) > rec_bytes)) {
-                report_bad(Fd->ws, tile, 1);
-                return;
-            }
-            or_bytes(words, pb, run);
-        };
-        if (exists && kind != kConst) {
-            const uint32_t mbase = nn_t * (b / 4 + 1) + mid_before + mk_blk_excl;
-            if (sub == 0) {
-                // the reqBits byte's word may also hold mid bytes: OR it in too
-                const uint32_t p = nn_t * (b / 4) + rank;
-                atomicOr(words + (p >> 2), (kind == kNonConst ? (uint32_t)req : 0xFFu) << (8 * (p & 3u)));
-            }
-            if (kind == kRaw) {
-                // verbatim input bytes, value-major
-                const U *src = reinterpret_cast<const U *>(Fd->in) + kg * b + sub * VPL;
-                for (int m = 0; m < nvalid; ++m) {
-                    const U v = src[m];
-                    const uint32_t p = mbase + (uint32_t)(sub * VPL + m) * w;
-#pragma unroll
-                    for (int h = 0; h < w / 4; ++h) put(8 * (p + 4 * h), (uint32_t)(v >> (32 * h)), 32);
-                }
-            } else {
-                // lead codes: this lane's values are bytes [sub*VPL/4, (sub+1)*VPL/4)
-                if (SZX_CHECKS && (rank + 1) * (b / 4) > nn_t * (b / 4)) report_bad(Fd->ws, tile, 6);
-                uint8_t *lead = buf + rank * (b / 4) + sub * (VPL / 4);
-                if constexpr (NCODE == 2) {
-                    *reinterpret_cast<uint2 *>(lead) = make_uint2(codes[0], codes[1]);
+                if (FT || (tma && row0 + rowi < rows_full)) {
+    #pragma unroll
+                    for (int c = 0; c < 8; ++c) {
+                        const uint4 v = *reinterpret_cast<const uint4 *>(buf + (rowi << 7) + ((c ^ (rowi & 7u)) << 4));
+                        const U *u = reinterpret_cast<const U *>(&v);
+    #pragma unroll
+                        for (int kk = 0; kk < 16 / w; ++kk) x[rr * VPR + c * (16 / w) + kk] = u[kk];
+                    }
                 } else {
-                    *reinterpret_cast<uint32_t *>(lead) = codes[0];
+    #pragma unroll
+                    for (int m = 0; m < VPR; ++m) x[rr * VPR + m] = rr * VPR + m < nvalid ? src[rr * VPR + m] : U(0);
                 }
-                const int s = (8 - (req & 7)) & 7;
-                const int q = (req + s) >> 3;
-                const uint32_t n0 = (uint32_t)(tot & FM), n1 = (uint32_t)((tot >> FB) & FM),
-                               n2 = (uint32_t)((tot >> (2 * FB)) & FM);
-                // plane positions in bits
-                uint32_t pos0 = 8 * (mbase + (uint32_t)(off & FM));
-                uint32_t pos1 = 8 * (mbase + n0 + (uint32_t)((off >> FB) & FM));
-                uint32_t pos2 = 8 * (mbase + n0 + n1 + (uint32_t)((off >> (2 * FB)) & FM));
-                const uint32_t dense0 = mbase + n0 + n1 + n2 + (uint32_t)sub * VPL;
-#pragma unroll
-                for (int gq = 0; gq < VPL / 4; ++gq) {
-                    // lookup codes: values past the end of a partial block never match
-                    uint32_t code8 = (codes[gq >> 2] >> (8 * (gq & 3))) & 0xFFu;
-                    uint32_t dense8 = 0;
-                    if (!full_lane) {
-                        const int nv = nvalid - 4 * gq;
-                        const uint32_t inval = nv >= 4 ? 0u : (nv <= 0 ? 0xFFu : (0xFFu << (2 * nv)) & 0xFFu);
-                        code8 |= inval;
-                        dense8 = inval;
+            }
+            // this lane's rows are read: clear them, the buffer becomes the record
+            // (the exact slow path below re-reads the input from global memory)
+            {
+                const uint4 z = make_uint4(0, 0, 0, 0);
+    #pragma unroll
+                for (int rr = 0; rr < RPL; ++rr) {
+                    const uint32_t rowi = lane_row0 + rr;
+    #pragma unroll
+                    for (int c = 0; c < 8; ++c) *reinterpret_cast<uint4 *>(buf + (rowi << 7) + ((c ^ (rowi & 7u)) << 4)) = z;
+                }
+                if (warp == kConsumerWarps - 1)
+                    for (uint32_t i = 32768u * RPL + 16u * lane; i < L.buf_bytes; i += 16u * 32u)
+                        *reinterpret_cast<uint4 *>(buf + i) = z;
+            }
+            uint32_t codes[NCODE];
+            int kind, req, req0;
+            T mu;
+            uint32_t mk_lane;
+            if (FT || __all_sync(kFull, full_lane)) {
+                encode_lane<T, LPB, VPL, true>(x, codes, kind, req, req0, mu, mk_lane, src, nvalid, exists, e,
+                                               Fd->e_bits, Fd->ws, tile);
+            } else {
+                encode_lane<T, LPB, VPL, false>(x, codes, kind, req, req0, mu, mk_lane, src, nvalid, exists, e,
+                                                Fd->e_bits, Fd->ws, tile);
+            }
+            const bool lead = exists && sub == 0;  // the block's first lane
+            if (lead) {
+                sm_kind[blk] = (uint8_t)kind;
+                reinterpret_cast<U *>(Fd->out + g.off_mu)[kg] = kind == kRaw ? U(0) : F::bits(mu);
+            }
+            // the warp's totals; its blocks are consecutive, so an exclusive scan
+            // over lanes gives each block's mid-byte offset inside the warp's share
+            uint32_t mid_w;
+            const uint32_t lane_excl = warp_exclusive_scan(mk_lane, &mid_w);
+            const uint32_t nonc_bal = __ballot_sync(kFull, lead && kind != kConst);
+            const uint32_t raw_bal = __ballot_sync(kFull, lead && kind == kRaw);
+            const uint32_t esc_bal = __ballot_sync(kFull, lead && kind == kNonConst && req > req0);
+            // per warp: (non-constant blocks << 20 | mid bytes), raw blocks, escalated blocks
+            if (lane == 0) sm_w[warp] = make_uint4((uint32_t)__popc(nonc_bal) << 20 | mid_w, __popc(raw_bal), __popc(esc_bal), 0);
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&encoded[st]);
+
+            // per-lane counts of values with code <= j (j = 0, 1, 2), packed in
+            // FB-bit fields, and their exclusive scan over the block's lanes;
+            // nothing here depends on the other warps, so it runs before the wait.
+            // Every lane runs this (the shuffles need the whole warp); lanes of
+            // constant or raw blocks contribute nothing.
+            const uint32_t mk_blk_excl = __shfl_sync(kFull, lane_excl, lane & ~(LPB - 1));
+            const uint32_t rank_in_warp = __popc(nonc_bal & ((1u << (lane & ~(LPB - 1))) - 1u));
+            using CntT = std::conditional_t<(LPB * VPL > 1023), unsigned long long, uint32_t>;
+            constexpr int FB = LPB * VPL > 1023 ? 16 : 10;
+            constexpr CntT FM = (CntT(1) << FB) - 1;
+            CntT cnt = 0;
+            if (exists && kind == kNonConst) {
+    #pragma unroll
+                for (int i = 0; i < NCODE; ++i) {
+                    const int nv = nvalid - 16 * i;
+                    const uint32_t vm = nv >= 16 ? 0x55555555u : (nv <= 0 ? 0u : (0x55555555u >> (2 * (16 - nv))));
+                    const uint32_t lo = codes[i] & 0x55555555u, hi = (codes[i] >> 1) & 0x55555555u;
+                    cnt += (CntT)__popc(~(lo | hi) & vm) | ((CntT)__popc(~hi & vm) << FB) |
+                           ((CntT)__popc(~(lo & hi) & vm) << (2 * FB));
+                }
+            }
+            CntT incl = cnt;
+    #pragma unroll
+            for (int d = 1; d < LPB; d <<= 1) {
+                const CntT y = __shfl_up_sync(kFull, incl, d);
+                if (sub >= d) incl += y;
+            }
+            const CntT tot = __shfl_sync(kFull, incl, (lane & ~(LPB - 1)) + LPB - 1);
+            const CntT off = incl - cnt;
+
+            if (!mbar_wait_bounded(&encoded[st], k & 1u, lc.lookback_ns + lc.copy_ns)) {
+                // a warp of this CTA never finished the tile: give up
+                if (lane == 0) {
+                    atomicOr(lc.err, kErrTimeout);
+                    st_tile[st] = 0xFFFFFFFFu;
+                    mbar_arrive(&ready[st]);
+                }
+                return false;
+            }
+
+            // ---- 2. tile totals and the aggregate for the look-back --------------
+            // lane i holds warp i's (nn << 20 | mid); warp reductions give the
+            // tile's totals and the sums over the warps before this one
+            const uint32_t wt = lane < kConsumerWarps ? sm_w[lane].x : 0u;
+            const uint32_t nm_t = __reduce_add_sync(kFull, wt);
+            const uint32_t nm_before = __reduce_add_sync(kFull, lane < warp ? wt : 0u);
+            const uint32_t nn_t = nm_t >> 20, mid_t = nm_t & 0xFFFFFu;
+            const uint32_t nn_before = nm_before >> 20, mid_before = nm_before & 0xFFFFFu;
+            const uint32_t rec_bytes = (uint32_t)pad16((uint64_t)nn_t * (b / 4 + 1) + mid_t);
+            if (warp == 0 && lane == 0) {
+                st_rec[st] = rec_bytes;
+                st_relaxed_u64(&Fd->lookback[tile], kFlagAgg | rec_bytes);
+            }
+            if (SZX_CHECKS && rec_bytes > record_max_bytes(G, b, w) && tid == 0) report_bad(Fd->ws, tile, 2);
+            const uint32_t rank = nn_before + rank_in_warp;
+
+            // ---- 3. the record --------------------------------------------------
+            uint32_t *words = reinterpret_cast<uint32_t *>(buf);
+            // every record write goes through put() (positions in bits, c8 = 8 x
+            // bytes): a self-checked build verifies that it lands inside the record
+            auto put = [&](uint32_t pb, uint32_t run, uint32_t c8) {
+                if (SZX_CHECKS && ((pb >> 3) + 8 > L.buf_bytes || ((pb + c8) >> 3) > rec_bytes)) {
+                    report_bad(Fd->ws, tile, 1);
+                    return;
+                }
+                or_bytes(words, pb, run);
+            };
+            if (exists && kind != kConst) {
+                const uint32_t mbase = nn_t * (b / 4 + 1) + mid_before + mk_blk_excl;
+                if (sub == 0) {
+                    // the reqBits byte's word may also hold mid bytes: OR it in too
+                    const uint32_t p = nn_t * (b / 4) + rank;
+                    atomicOr(words + (p >> 2), (kind == kNonConst ? (uint32_t)req : 0xFFu) << (8 * (p & 3u)));
+                }
+                if (kind == kRaw) {
+                    // verbatim input bytes, value-major
+                    const U *src = reinterpret_cast<const U *>(Fd->in) + kg * b + sub * VPL;
+                    for (int m = 0; m < nvalid; ++m) {
+                        const U v = src[m];
+                        const uint32_t p = mbase + (uint32_t)(sub * VPL + m) * w;
+    #pragma unroll
+                        for (int h = 0; h < w / 4; ++h) put(8 * (p + 4 * h), (uint32_t)(v >> (32 * h)), 32);
                     }
-                    uint32_t Wd[W / 8];
-                    if constexpr (sizeof(T) == 4) {
-                        uint32_t Wq[4];
-                        transpose4((uint32_t)x[4 * gq], (uint32_t)x[4 * gq + 1], (uint32_t)x[4 * gq + 2],
-                                   (uint32_t)x[4 * gq + 3], Wq);
-#pragma unroll
-                        for (int j = 0; j < 4; ++j) Wd[j] = Wq[j];
+                } else {
+                    // lead codes: this lane's values are bytes [sub*VPL/4, (sub+1)*VPL/4)
+                    if (SZX_CHECKS && (rank + 1) * (b / 4) > nn_t * (b / 4)) report_bad(Fd->ws, tile, 6);
+                    uint8_t *lead = buf + rank * (b / 4) + sub * (VPL / 4);
+                    if constexpr (NCODE == 2) {
+                        *reinterpret_cast<uint2 *>(lead) = make_uint2(codes[0], codes[1]);
                     } else {
-                        uint32_t Wh[4], Wl[4];
-                        transpose4((uint32_t)(x[4 * gq] >> 32), (uint32_t)(x[4 * gq + 1] >> 32),
-                                   (uint32_t)(x[4 * gq + 2] >> 32), (uint32_t)(x[4 * gq + 3] >> 32), Wh);
-                        transpose4((uint32_t)x[4 * gq], (uint32_t)x[4 * gq + 1], (uint32_t)x[4 * gq + 2],
-                                   (uint32_t)x[4 * gq + 3], Wl);
-#pragma unroll
-                        for (int j = 0; j < 4; ++j) {
-                            Wd[j] = Wh[j];
-                            Wd[4 + j] = Wl[j];
+                        *reinterpret_cast<uint32_t *>(lead) = codes[0];
+                    }
+                    const int s = (8 - (req & 7)) & 7;
+                    const int q = (req + s) >> 3;
+                    const uint32_t n0 = (uint32_t)(tot & FM), n1 = (uint32_t)((tot >> FB) & FM),
+                                   n2 = (uint32_t)((tot >> (2 * FB)) & FM);
+                    // plane positions in bits
+                    uint32_t pos0 = 8 * (mbase + (uint32_t)(off & FM));
+                    uint32_t pos1 = 8 * (mbase + n0 + (uint32_t)((off >> FB) & FM));
+                    uint32_t pos2 = 8 * (mbase + n0 + n1 + (uint32_t)((off >> (2 * FB)) & FM));
+                    const uint32_t dense0 = mbase + n0 + n1 + n2 + (uint32_t)sub * VPL;
+    #pragma unroll
+                    for (int gq = 0; gq < VPL / 4; ++gq) {
+                        // lookup codes: values past the end of a partial block never match
+                        uint32_t code8 = (codes[gq >> 2] >> (8 * (gq & 3))) & 0xFFu;
+                        uint32_t dense8 = 0;
+                        if (!full_lane) {
+                            const int nv = nvalid - 4 * gq;
+                            const uint32_t inval = nv >= 4 ? 0u : (nv <= 0 ? 0xFFu : (0xFFu << (2 * nv)) & 0xFFu);
+                            code8 |= inval;
+                            dense8 = inval;
                         }
-                    }
-                    {
-                        const uint32_t e0 = lut[code8];
-                        put(pos0, prmt(Wd[0], 0, e0), e0 >> 16);
-                        pos0 += e0 >> 16;
-                        const uint32_t e1 = lut[256 + code8];
-                        put(pos1, prmt(Wd[1], 0, e1), e1 >> 16);
-                        pos1 += e1 >> 16;
-                    }
-                    if (q >= 3) {
-                        const uint32_t e2 = lut[512 + code8];
-                        put(pos2, prmt(Wd[2], 0, e2), e2 >> 16);
-                        pos2 += e2 >> 16;
-                    }
-                    if (q >= 4) {
-                        const uint32_t sel = full_lane ? (0x3210u | (32u << 16)) : lut[512 + dense8];
-#pragma unroll
-                        for (int j = 3; j < W / 8; ++j) {
-                            if (j < q)
-                                put(8 * (dense0 + (uint32_t)(j - 3) * len + 4 * gq), prmt(Wd[j], 0, sel), sel >> 16);
+                        uint32_t Wd[W / 8];
+                        if constexpr (sizeof(T) == 4) {
+                            uint32_t Wq[4];
+                            transpose4((uint32_t)x[4 * gq], (uint32_t)x[4 * gq + 1], (uint32_t)x[4 * gq + 2],
+                                       (uint32_t)x[4 * gq + 3], Wq);
+    #pragma unroll
+                            for (int j = 0; j < 4; ++j) Wd[j] = Wq[j];
+                        } else {
+                            uint32_t Wh[4], Wl[4];
+                            transpose4((uint32_t)(x[4 * gq] >> 32), (uint32_t)(x[4 * gq + 1] >> 32),
+                                       (uint32_t)(x[4 * gq + 2] >> 32), (uint32_t)(x[4 * gq + 3] >> 32), Wh);
+                            transpose4((uint32_t)x[4 * gq], (uint32_t)x[4 * gq + 1], (uint32_t)x[4 * gq + 2],
+                                       (uint32_t)x[4 * gq + 3], Wl);
+    #pragma unroll
+                            for (int j = 0; j < 4; ++j) {
+                                Wd[j] = Wh[j];
+                                Wd[4 + j] = Wl[j];
+                            }
+                        }
+                        {
+                            const uint32_t e0 = lut[code8];
+                            put(pos0, prmt(Wd[0], 0, e0), e0 >> 16);
+                            pos0 += e0 >> 16;
+                            const uint32_t e1 = lut[256 + code8];
+                            put(pos1, prmt(Wd[1], 0, e1), e1 >> 16);
+                            pos1 += e1 >> 16;
+                        }
+                        if (q >= 3) {
+                            const uint32_t e2 = lut[512 + code8];
+                            put(pos2, prmt(Wd[2], 0, e2), e2 >> 16);
+                            pos2 += e2 >> 16;
+                        }
+                        if (q >= 4) {
+                            const uint32_t sel = full_lane ? (0x3210u | (32u << 16)) : lut[512 + dense8];
+    #pragma unroll
+                            for (int j = 3; j < W / 8; ++j) {
+                                if (j < q)
+                                    put(8 * (dense0 + (uint32_t)(j - 3) * len + 4 * gq), prmt(Wd[j], 0, sel), sel >> 16);
+                            }
                         }
                     }
                 }
             }
-        }
-        // hand the record to the storer (its bulk store reads it through the
-        // async proxy)
-        fence_proxy_async_smem();
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&ready[st]);
+            // hand the record to the storer (its bulk store reads it through the
+            // async proxy)
+            fence_proxy_async_smem();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&ready[st]);
+            return true;
+        };
+        if (!(full_tile ? tile_body(std::true_type{}) : tile_body(std::false_type{}))) break;
     }
 }
 
