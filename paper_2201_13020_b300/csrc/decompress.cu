@@ -554,232 +554,246 @@ __global__ void __launch_bounds__(kDThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
         const uint64_t k0 = (uint64_t)tile * G;
         const uint32_t Gt = (uint32_t)min_u64(G, g.nb - k0);
 
-        const int sub = lane % LPB;
-        const uint32_t blk = (uint32_t)(warp * BPW + lane / LPB);
-        const bool exists = blk < Gt && !bad;
-        const uint64_t kg = k0 + blk;
-        const int len = exists ? (int)min_u64(b, g.n - kg * b) : 0;
-        int nvalid = len - sub * VPL;
-        nvalid = nvalid < 0 ? 0 : (nvalid > VPL ? VPL : nvalid);
-        const bool full_lane = nvalid == VPL;
-        const uint32_t segmask = (LPB == 32 ? kFull : ((1u << LPB) - 1u)) << (lane & ~(LPB - 1));
-        U x[VPL];
-        if (!bad) {
-            // ---- the block's entry: mid-byte offset, rank, reqBits ----------
-            const uint2 bi = exists ? reinterpret_cast<const uint2 *>(slot + L.info)[blk] : make_uint2(0, 0);
-            const uint32_t mbase = bi.x, rank = bi.y & 0xFFFFu, rq = bi.y >> 16;
-            const bool raw = rq == 0xFFu;
-            const bool coded = rq != 0u && !raw;
-            const int s = (8 - (int)(rq & 7u)) & 7;
-            const int q = coded ? ((int)rq + s) >> 3 : 2;
-            const int lmax = q < 3 ? q : 3;
-            uint32_t codes[NCODE];
-#pragma unroll
-            for (int i = 0; i < NCODE; ++i) codes[i] = 0;
-            if (coded) {
-                const uint8_t *lead = rec + rank * (b / 4) + sub * (VPL / 4);
-                if constexpr (NCODE == 2) {
-                    const uint2 v = *reinterpret_cast<const uint2 *>(lead);
-                    codes[0] = v.x;
-                    codes[1] = v.y;
-                } else {
-                    codes[0] = *reinterpret_cast<const uint32_t *>(lead);
-                }
+        // Tiles wholly inside the stream's field and the decoded range, with
+        // every output row stored by the tensor copy, run a copy of the work
+        // below compiled for that case: no checks of the ends per block, row
+        // or group of values
+        const bool full_tile = st_verdict[st] == 0 && Fd->use_tma && (k0 + G) * b <= g.n && k0 >= Fd->blk_lo &&
+                               k0 + G <= Fd->blk_hi;
+        auto tile_body = [&](auto full_c) {
+            constexpr bool FT = decltype(full_c)::value;
+            const int sub = lane % LPB;
+            const uint32_t blk = (uint32_t)(warp * BPW + lane / LPB);
+            const bool exists = FT || (blk < Gt && !bad);
+            const uint64_t kg = k0 + blk;
+            const int len = FT ? (int)b : (exists ? (int)min_u64(b, g.n - kg * b) : 0);
+            int nvalid = VPL;
+            if constexpr (!FT) {
+                nvalid = len - sub * VPL;
+                nvalid = nvalid < 0 ? 0 : (nvalid > VPL ? VPL : nvalid);
             }
-            const U mu_bits = exists ? reinterpret_cast<const U *>(slot + L.mu)[blk] : U(0);
-
-            // ---- decode --------------------------------------------------
-            using CntT = std::conditional_t<(LPB * VPL > 1023), unsigned long long, uint32_t>;
-            constexpr int FB = LPB * VPL > 1023 ? 16 : 10;
-            constexpr CntT FM = (CntT(1) << FB) - 1;
-            CntT cnt = 0;
-            if (coded) {
-#pragma unroll
-                for (int i = 0; i < NCODE; ++i) {
-                    const int nv = nvalid - 16 * i;
-                    const uint32_t vm = nv >= 16 ? 0x55555555u : (nv <= 0 ? 0u : (0x55555555u >> (2 * (16 - nv))));
-                    const uint32_t lo = codes[i] & 0x55555555u, hi = (codes[i] >> 1) & 0x55555555u;
-                    cnt += (CntT)__popc(~(lo | hi) & vm) | ((CntT)__popc(~hi & vm) << FB) |
-                           ((CntT)__popc(~(lo & hi) & vm) << (2 * FB));
-                }
-            }
-            CntT incl = cnt;
-#pragma unroll
-            for (int d = 1; d < LPB; d <<= 1) {
-                const CntT y = __shfl_up_sync(kFull, incl, d);
-                if (sub >= d) incl += y;
-            }
-            const CntT tot = __shfl_sync(kFull, incl, (lane & ~(LPB - 1)) + LPB - 1);
-            const CntT off = incl - cnt;
-            const uint32_t n0 = (uint32_t)(tot & FM), n1 = (uint32_t)((tot >> FB) & FM),
-                           n2 = (uint32_t)((tot >> (2 * FB)) & FM);
-            const uint32_t cj[3] = {(uint32_t)(cnt & FM), (uint32_t)((cnt >> FB) & FM),
-                                    (uint32_t)((cnt >> (2 * FB)) & FM)};
-            uint32_t pos0 = mbase + (uint32_t)(off & FM);
-            uint32_t pos1 = mbase + n0 + (uint32_t)((off >> FB) & FM);
-            uint32_t pos2 = mbase + n0 + n1 + (uint32_t)((off >> (2 * FB)) & FM);
-            const uint32_t dense0 = mbase + n0 + n1 + n2 + (uint32_t)sub * VPL;
-
-            // carries into the lane for the planes that can inherit (j < lmax):
-            // the last own byte of the nearest lower lane of the block that owns one
-            uint32_t carry[3];
-            {
-                const uint32_t below = segmask & ((1u << lane) - 1u);
-                const uint32_t pj[3] = {pos0, pos1, pos2};
-#pragma unroll
-                for (int j = 0; j < 3; ++j) {
-                    const bool has = coded && j < lmax && cj[j] > 0;
-                    const uint32_t last = has ? rec[pj[j] + cj[j] - 1] : 0u;
-                    const uint32_t m = __ballot_sync(kFull, has) & below;
-                    const uint32_t v = __shfl_sync(kFull, last, m ? 31 - __clz(m) : 0);
-                    carry[j] = m ? v : 0u;
-                }
-            }
-
-            if (coded) {
-                const T mu = F::from(mu_bits);
-#pragma unroll
-                for (int gq = 0; gq < VPL / 4; ++gq) {
-                    uint32_t code8 = (codes[gq >> 2] >> (8 * (gq & 3))) & 0xFFu;
-                    uint32_t dense8 = 0;
-                    if (!full_lane) {
-                        const int nv = nvalid - 4 * gq;
-                        const uint32_t inval = nv >= 4 ? 0u : (nv <= 0 ? 0xFFu : (0xFFu << (2 * nv)) & 0xFFu);
-                        code8 |= inval;
-                        dense8 = inval;
-                    }
-                    // plane words: byte k = byte j of value 4gq + k; a leading
-                    // byte takes the nearest earlier owner's, or the carry
-                    uint32_t P[W / 8];
-#pragma unroll
-                    for (int j = 0; j < W / 8; ++j) P[j] = 0;
-                    {
-                        const uint32_t e0 = lut[code8];
-                        P[0] = dprmt(load_run(rec, pos0), carry[0], e0);
-                        pos0 += e0 >> 16;
-                        carry[0] = P[0] >> 24;
-                        const uint32_t e1 = lut[256 + code8];
-                        P[1] = dprmt(load_run(rec, pos1), carry[1], e1);
-                        pos1 += e1 >> 16;
-                        carry[1] = P[1] >> 24;
-                        if (q >= 3) {
-                            const uint32_t e2 = lut[512 + code8];
-                            P[2] = dprmt(load_run(rec, pos2), carry[2], e2);
-                            pos2 += e2 >> 16;
-                            carry[2] = P[2] >> 24;
-                        }
-                        if (q >= 4) {
-                            // dense planes: every valid value owns its byte
-                            const uint32_t sel = full_lane ? 0x3210u : lut[512 + dense8];
-#pragma unroll
-                            for (int j = 3; j < W / 8; ++j)
-                                if (j < q)
-                                    P[j] = dprmt(load_run(rec, dense0 + (uint32_t)(j - 3) * len + 4 * gq), 0, sel);
-                        }
-                    }
-                    // planes back to words: t = (P0.k, P1.k, P2.k, P3.k), most significant first
-                    U t[4];
-                    if constexpr (NPW == 1) {
-                        uint32_t Wq[4];
-                        transpose4d(P[3], P[2], P[1], P[0], Wq);
-#pragma unroll
-                        for (int kk = 0; kk < 4; ++kk) t[kk] = Wq[3 - kk];
+            const bool full_lane = FT || nvalid == VPL;
+            const uint32_t segmask = (LPB == 32 ? kFull : ((1u << LPB) - 1u)) << (lane & ~(LPB - 1));
+            U x[VPL];
+            if (FT || !bad) {
+                // ---- the block's entry: mid-byte offset, rank, reqBits ----------
+                const uint2 bi = exists ? reinterpret_cast<const uint2 *>(slot + L.info)[blk] : make_uint2(0, 0);
+                const uint32_t mbase = bi.x, rank = bi.y & 0xFFFFu, rq = bi.y >> 16;
+                const bool raw = rq == 0xFFu;
+                const bool coded = rq != 0u && !raw;
+                const int s = (8 - (int)(rq & 7u)) & 7;
+                const int q = coded ? ((int)rq + s) >> 3 : 2;
+                const int lmax = q < 3 ? q : 3;
+                uint32_t codes[NCODE];
+    #pragma unroll
+                for (int i = 0; i < NCODE; ++i) codes[i] = 0;
+                if (coded) {
+                    const uint8_t *lead = rec + rank * (b / 4) + sub * (VPL / 4);
+                    if constexpr (NCODE == 2) {
+                        const uint2 v = *reinterpret_cast<const uint2 *>(lead);
+                        codes[0] = v.x;
+                        codes[1] = v.y;
                     } else {
-                        uint32_t Wh[4], Wl[4];
-                        transpose4d(P[3], P[2], P[1], P[0], Wh);
-                        transpose4d(P[7], P[6], P[5], P[4], Wl);
-#pragma unroll
-                        for (int kk = 0; kk < 4; ++kk) t[kk] = ((U)Wh[3 - kk] << 32) | (U)Wl[3 - kk];
+                        codes[0] = *reinterpret_cast<const uint32_t *>(lead);
                     }
-#pragma unroll
-                    for (int kk = 0; kk < 4; ++kk) x[4 * gq + kk] = F::bits(F::add(F::from((U)(t[kk] << s)), mu));
                 }
-            } else if (raw) {
-                const uint8_t *p = rec + mbase + (uint32_t)sub * VPL * w;
-#pragma unroll
-                for (int m = 0; m < VPL; ++m) {
-                    U u = 0;
-                    if (m < nvalid) {
-#pragma unroll
-                        for (int i = 0; i < w; ++i) u |= (U)p[m * w + i] << (8 * i);
-                    }
-                    x[m] = u;
-                }
-            } else {
-#pragma unroll
-                for (int m = 0; m < VPL; ++m) x[m] = mu_bits;
-            }
-            // strictness: the record's pad bytes (fewer than 16) must be zero
-            if (warp == 0) {
-                const uint32_t used = st_used[st];
-                if (used + lane < st_size[st] && rec[used + lane]) flag_status(Fd->status, 3u);
-            }
-        }
-        // this warp no longer reads the tile's record or slot
-        __syncwarp();
-        if (lane == 0) dmbar_arrive(&consumed[st]);
-        if (bad) continue;
+                const U mu_bits = exists ? reinterpret_cast<const U *>(slot + L.mu)[blk] : U(0);
 
-        // ---- output: full rows through the warp's buffer and a tensor store,
-        // the ragged last row with plain stores ------------------------------
-        // rows of the output count from the range's first row; a warp whose
-        // rows all lie at or after it stores through the tensor map (rows past
-        // the end are clipped), one that straddles the start stores plainly
-        const uint64_t wrow0 = (uint64_t)tile * 256 * RPL + (uint64_t)warp * 32 * RPL;  // warp's first row
-        const bool tma_rows = Fd->use_tma && wrow0 >= Fd->row_lo && wrow0 - Fd->row_lo < Fd->rows_full;
-        const bool wanted = kg >= Fd->blk_lo && kg < Fd->blk_hi;
-        if (tma_rows) {
-            // the buffer is free once the previous tile's store has read it
-            if (lane == 0) bulk_wait_read_all();
-            __syncwarp();
-        }
-        if (exists && wanted && nvalid > 0) {
-#pragma unroll
-            for (int rr = 0; rr < RPL; ++rr) {
-                constexpr int VPR = 128 / w;  // values per row
-                const int nv = nvalid - rr * VPR;
-                if (nv <= 0) continue;
-                const uint32_t rowi = lane_row0 + rr;
-                if (tma_rows && wrow0 + rowi - Fd->row_lo < Fd->rows_full) {
-                    uint8_t *row = wbuf + (rowi << 7);
-#pragma unroll
-                    for (int c = 0; c < 8; ++c) {
-                        uint4 v;
-                        U *u = reinterpret_cast<U *>(&v);
-#pragma unroll
-                        for (int kk = 0; kk < 16 / w; ++kk) u[kk] = x[rr * VPR + c * (16 / w) + kk];
-                        *reinterpret_cast<uint4 *>(row + ((c ^ (rowi & 7u)) << 4)) = v;
+                // ---- decode --------------------------------------------------
+                using CntT = std::conditional_t<(LPB * VPL > 1023), unsigned long long, uint32_t>;
+                constexpr int FB = LPB * VPL > 1023 ? 16 : 10;
+                constexpr CntT FM = (CntT(1) << FB) - 1;
+                CntT cnt = 0;
+                if (coded) {
+    #pragma unroll
+                    for (int i = 0; i < NCODE; ++i) {
+                        const int nv = nvalid - 16 * i;
+                        const uint32_t vm = nv >= 16 ? 0x55555555u : (nv <= 0 ? 0u : (0x55555555u >> (2 * (16 - nv))));
+                        const uint32_t lo = codes[i] & 0x55555555u, hi = (codes[i] >> 1) & 0x55555555u;
+                        cnt += (CntT)__popc(~(lo | hi) & vm) | ((CntT)__popc(~hi & vm) << FB) |
+                               ((CntT)__popc(~(lo & hi) & vm) << (2 * FB));
+                    }
+                }
+                CntT incl = cnt;
+    #pragma unroll
+                for (int d = 1; d < LPB; d <<= 1) {
+                    const CntT y = __shfl_up_sync(kFull, incl, d);
+                    if (sub >= d) incl += y;
+                }
+                const CntT tot = __shfl_sync(kFull, incl, (lane & ~(LPB - 1)) + LPB - 1);
+                const CntT off = incl - cnt;
+                const uint32_t n0 = (uint32_t)(tot & FM), n1 = (uint32_t)((tot >> FB) & FM),
+                               n2 = (uint32_t)((tot >> (2 * FB)) & FM);
+                const uint32_t cj[3] = {(uint32_t)(cnt & FM), (uint32_t)((cnt >> FB) & FM),
+                                        (uint32_t)((cnt >> (2 * FB)) & FM)};
+                uint32_t pos0 = mbase + (uint32_t)(off & FM);
+                uint32_t pos1 = mbase + n0 + (uint32_t)((off >> FB) & FM);
+                uint32_t pos2 = mbase + n0 + n1 + (uint32_t)((off >> (2 * FB)) & FM);
+                const uint32_t dense0 = mbase + n0 + n1 + n2 + (uint32_t)sub * VPL;
+
+                // carries into the lane for the planes that can inherit (j < lmax):
+                // the last own byte of the nearest lower lane of the block that owns one
+                uint32_t carry[3];
+                {
+                    const uint32_t below = segmask & ((1u << lane) - 1u);
+                    const uint32_t pj[3] = {pos0, pos1, pos2};
+    #pragma unroll
+                    for (int j = 0; j < 3; ++j) {
+                        const bool has = coded && j < lmax && cj[j] > 0;
+                        const uint32_t last = has ? rec[pj[j] + cj[j] - 1] : 0u;
+                        const uint32_t m = __ballot_sync(kFull, has) & below;
+                        const uint32_t v = __shfl_sync(kFull, last, m ? 31 - __clz(m) : 0);
+                        carry[j] = m ? v : 0u;
+                    }
+                }
+
+                if (coded) {
+                    const T mu = F::from(mu_bits);
+    #pragma unroll
+                    for (int gq = 0; gq < VPL / 4; ++gq) {
+                        uint32_t code8 = (codes[gq >> 2] >> (8 * (gq & 3))) & 0xFFu;
+                        uint32_t dense8 = 0;
+                        if (!full_lane) {
+                            const int nv = nvalid - 4 * gq;
+                            const uint32_t inval = nv >= 4 ? 0u : (nv <= 0 ? 0xFFu : (0xFFu << (2 * nv)) & 0xFFu);
+                            code8 |= inval;
+                            dense8 = inval;
+                        }
+                        // plane words: byte k = byte j of value 4gq + k; a leading
+                        // byte takes the nearest earlier owner's, or the carry
+                        uint32_t P[W / 8];
+    #pragma unroll
+                        for (int j = 0; j < W / 8; ++j) P[j] = 0;
+                        {
+                            const uint32_t e0 = lut[code8];
+                            P[0] = dprmt(load_run(rec, pos0), carry[0], e0);
+                            pos0 += e0 >> 16;
+                            carry[0] = P[0] >> 24;
+                            const uint32_t e1 = lut[256 + code8];
+                            P[1] = dprmt(load_run(rec, pos1), carry[1], e1);
+                            pos1 += e1 >> 16;
+                            carry[1] = P[1] >> 24;
+                            if (q >= 3) {
+                                const uint32_t e2 = lut[512 + code8];
+                                P[2] = dprmt(load_run(rec, pos2), carry[2], e2);
+                                pos2 += e2 >> 16;
+                                carry[2] = P[2] >> 24;
+                            }
+                            if (q >= 4) {
+                                // dense planes: every valid value owns its byte
+                                const uint32_t sel = full_lane ? 0x3210u : lut[512 + dense8];
+    #pragma unroll
+                                for (int j = 3; j < W / 8; ++j)
+                                    if (j < q)
+                                        P[j] = dprmt(load_run(rec, dense0 + (uint32_t)(j - 3) * len + 4 * gq), 0, sel);
+                            }
+                        }
+                        // planes back to words: t = (P0.k, P1.k, P2.k, P3.k), most significant first
+                        U t[4];
+                        if constexpr (NPW == 1) {
+                            uint32_t Wq[4];
+                            transpose4d(P[3], P[2], P[1], P[0], Wq);
+    #pragma unroll
+                            for (int kk = 0; kk < 4; ++kk) t[kk] = Wq[3 - kk];
+                        } else {
+                            uint32_t Wh[4], Wl[4];
+                            transpose4d(P[3], P[2], P[1], P[0], Wh);
+                            transpose4d(P[7], P[6], P[5], P[4], Wl);
+    #pragma unroll
+                            for (int kk = 0; kk < 4; ++kk) t[kk] = ((U)Wh[3 - kk] << 32) | (U)Wl[3 - kk];
+                        }
+    #pragma unroll
+                        for (int kk = 0; kk < 4; ++kk) x[4 * gq + kk] = F::bits(F::add(F::from((U)(t[kk] << s)), mu));
+                    }
+                } else if (raw) {
+                    const uint8_t *p = rec + mbase + (uint32_t)sub * VPL * w;
+    #pragma unroll
+                    for (int m = 0; m < VPL; ++m) {
+                        U u = 0;
+                        if (m < nvalid) {
+    #pragma unroll
+                            for (int i = 0; i < w; ++i) u |= (U)p[m * w + i] << (8 * i);
+                        }
+                        x[m] = u;
                     }
                 } else {
-                    U *dst = reinterpret_cast<U *>(Fd->out) + (kg - Fd->blk_lo) * b + sub * VPL + rr * VPR;
-                    if (nv >= VPR) {
-#pragma unroll
+    #pragma unroll
+                    for (int m = 0; m < VPL; ++m) x[m] = mu_bits;
+                }
+                // strictness: the record's pad bytes (fewer than 16) must be zero
+                if (warp == 0) {
+                    const uint32_t used = st_used[st];
+                    if (used + lane < st_size[st] && rec[used + lane]) flag_status(Fd->status, 3u);
+                }
+            }
+            // this warp no longer reads the tile's record or slot
+            __syncwarp();
+            if (lane == 0) dmbar_arrive(&consumed[st]);
+            if (!FT && bad) return;
+
+            // ---- output: full rows through the warp's buffer and a tensor store,
+            // the ragged last row with plain stores ------------------------------
+            // rows of the output count from the range's first row; a warp whose
+            // rows all lie at or after it stores through the tensor map (rows past
+            // the end are clipped), one that straddles the start stores plainly
+            const uint64_t wrow0 = (uint64_t)tile * 256 * RPL + (uint64_t)warp * 32 * RPL;  // warp's first row
+            const bool tma_rows = FT || (Fd->use_tma && wrow0 >= Fd->row_lo && wrow0 - Fd->row_lo < Fd->rows_full);
+            const bool wanted = FT || (kg >= Fd->blk_lo && kg < Fd->blk_hi);
+            if (tma_rows) {
+                // the buffer is free once the previous tile's store has read it
+                if (lane == 0) bulk_wait_read_all();
+                __syncwarp();
+            }
+            if (exists && wanted && nvalid > 0) {
+    #pragma unroll
+                for (int rr = 0; rr < RPL; ++rr) {
+                    constexpr int VPR = 128 / w;  // values per row
+                    const int nv = nvalid - rr * VPR;
+                    if (nv <= 0) continue;
+                    const uint32_t rowi = lane_row0 + rr;
+                    if (FT || (tma_rows && wrow0 + rowi - Fd->row_lo < Fd->rows_full)) {
+                        uint8_t *row = wbuf + (rowi << 7);
+    #pragma unroll
                         for (int c = 0; c < 8; ++c) {
                             uint4 v;
                             U *u = reinterpret_cast<U *>(&v);
-#pragma unroll
+    #pragma unroll
                             for (int kk = 0; kk < 16 / w; ++kk) u[kk] = x[rr * VPR + c * (16 / w) + kk];
-                            reinterpret_cast<uint4 *>(dst)[c] = v;
+                            *reinterpret_cast<uint4 *>(row + ((c ^ (rowi & 7u)) << 4)) = v;
                         }
                     } else {
-#pragma unroll
-                        for (int m = 0; m < VPR; ++m)
-                            if (m < nv) dst[m] = x[rr * VPR + m];
+                        U *dst = reinterpret_cast<U *>(Fd->out) + (kg - Fd->blk_lo) * b + sub * VPL + rr * VPR;
+                        if (nv >= VPR) {
+    #pragma unroll
+                            for (int c = 0; c < 8; ++c) {
+                                uint4 v;
+                                U *u = reinterpret_cast<U *>(&v);
+    #pragma unroll
+                                for (int kk = 0; kk < 16 / w; ++kk) u[kk] = x[rr * VPR + c * (16 / w) + kk];
+                                reinterpret_cast<uint4 *>(dst)[c] = v;
+                            }
+                        } else {
+    #pragma unroll
+                            for (int m = 0; m < VPR; ++m)
+                                if (m < nv) dst[m] = x[rr * VPR + m];
+                        }
                     }
                 }
             }
-        }
-        if (tma_rows) {
-            fence_proxy_async_smem();
-            __syncwarp();
-            if (lane == 0) {
-                asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(
-                                 reinterpret_cast<uint64_t>(&Fd->tmap)),
-                             "r"(0), "r"((int)(wrow0 - Fd->row_lo)), "r"(smem_addr(wbuf))
-                             : "memory");
-                bulk_commit();
+            if (tma_rows) {
+                fence_proxy_async_smem();
+                __syncwarp();
+                if (lane == 0) {
+                    asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(
+                                     reinterpret_cast<uint64_t>(&Fd->tmap)),
+                                 "r"(0), "r"((int)(wrow0 - Fd->row_lo)), "r"(smem_addr(wbuf))
+                                 : "memory");
+                    bulk_commit();
+                }
             }
-        }
+        };
+        if (full_tile) tile_body(std::true_type{});
+        else tile_body(std::false_type{});
     }
     // stores must finish reading shared memory (and land) before the CTA leaves
     if (lane == 0) bulk_wait_all();
