@@ -763,19 +763,19 @@ __global__ void __launch_bounds__(kCThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
             // input's ragged end (or every row without the tensor copy) from global
             constexpr int VPR = 128 / w;  // values per row
             U x[VPL];
-    #pragma unroll
+#pragma unroll
             for (int rr = 0; rr < RPL; ++rr) {
                 const uint32_t rowi = lane_row0 + rr;
                 if (FT || (tma && row0 + rowi < rows_full)) {
-    #pragma unroll
+#pragma unroll
                     for (int c = 0; c < 8; ++c) {
                         const uint4 v = *reinterpret_cast<const uint4 *>(buf + (rowi << 7) + ((c ^ (rowi & 7u)) << 4));
                         const U *u = reinterpret_cast<const U *>(&v);
-    #pragma unroll
+#pragma unroll
                         for (int kk = 0; kk < 16 / w; ++kk) x[rr * VPR + c * (16 / w) + kk] = u[kk];
                     }
                 } else {
-    #pragma unroll
+#pragma unroll
                     for (int m = 0; m < VPR; ++m) x[rr * VPR + m] = rr * VPR + m < nvalid ? src[rr * VPR + m] : U(0);
                 }
             }
@@ -783,10 +783,10 @@ __global__ void __launch_bounds__(kCThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
             // (the exact slow path below re-reads the input from global memory)
             {
                 const uint4 z = make_uint4(0, 0, 0, 0);
-    #pragma unroll
+#pragma unroll
                 for (int rr = 0; rr < RPL; ++rr) {
                     const uint32_t rowi = lane_row0 + rr;
-    #pragma unroll
+#pragma unroll
                     for (int c = 0; c < 8; ++c) *reinterpret_cast<uint4 *>(buf + (rowi << 7) + ((c ^ (rowi & 7u)) << 4)) = z;
                 }
                 if (warp == kConsumerWarps - 1)
@@ -833,7 +833,7 @@ __global__ void __launch_bounds__(kCThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
             constexpr CntT FM = (CntT(1) << FB) - 1;
             CntT cnt = 0;
             if (exists && kind == kNonConst) {
-    #pragma unroll
+#pragma unroll
                 for (int i = 0; i < NCODE; ++i) {
                     const int nv = nvalid - 16 * i;
                     const uint32_t vm = nv >= 16 ? 0x55555555u : (nv <= 0 ? 0u : (0x55555555u >> (2 * (16 - nv))));
@@ -843,7 +843,7 @@ __global__ void __launch_bounds__(kCThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
                 }
             }
             CntT incl = cnt;
-    #pragma unroll
+#pragma unroll
             for (int d = 1; d < LPB; d <<= 1) {
                 const CntT y = __shfl_up_sync(kFull, incl, d);
                 if (sub >= d) incl += y;
@@ -901,7 +901,7 @@ __global__ void __launch_bounds__(kCThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
                     for (int m = 0; m < nvalid; ++m) {
                         const U v = src[m];
                         const uint32_t p = mbase + (uint32_t)(sub * VPL + m) * w;
-    #pragma unroll
+#pragma unroll
                         for (int h = 0; h < w / 4; ++h) put(8 * (p + 4 * h), (uint32_t)(v >> (32 * h)), 32);
                     }
                 } else {
@@ -922,7 +922,7 @@ __global__ void __launch_bounds__(kCThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
                     uint32_t pos1 = 8 * (mbase + n0 + (uint32_t)((off >> FB) & FM));
                     uint32_t pos2 = 8 * (mbase + n0 + n1 + (uint32_t)((off >> (2 * FB)) & FM));
                     const uint32_t dense0 = mbase + n0 + n1 + n2 + (uint32_t)sub * VPL;
-    #pragma unroll
+#pragma unroll
                     for (int gq = 0; gq < VPL / 4; ++gq) {
                         // lookup codes: values past the end of a partial block never match
                         uint32_t code8 = (codes[gq >> 2] >> (8 * (gq & 3))) & 0xFFu;
@@ -938,7 +938,7 @@ __global__ void __launch_bounds__(kCThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
                             uint32_t Wq[4];
                             transpose4((uint32_t)x[4 * gq], (uint32_t)x[4 * gq + 1], (uint32_t)x[4 * gq + 2],
                                        (uint32_t)x[4 * gq + 3], Wq);
-    #pragma unroll
+#pragma unroll
                             for (int j = 0; j < 4; ++j) Wd[j] = Wq[j];
                         } else {
                             uint32_t Wh[4], Wl[4];
@@ -946,7 +946,7 @@ __global__ void __launch_bounds__(kCThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
                                        (uint32_t)(x[4 * gq + 2] >> 32), (uint32_t)(x[4 * gq + 3] >> 32), Wh);
                             transpose4((uint32_t)x[4 * gq], (uint32_t)x[4 * gq + 1], (uint32_t)x[4 * gq + 2],
                                        (uint32_t)x[4 * gq + 3], Wl);
-    #pragma unroll
+#pragma unroll
                             for (int j = 0; j < 4; ++j) {
                                 Wd[j] = Wh[j];
                                 Wd[4 + j] = Wl[j];
@@ -967,7 +967,7 @@ __global__ void __launch_bounds__(kCThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
                         }
                         if (q >= 4) {
                             const uint32_t sel = full_lane ? (0x3210u | (32u << 16)) : lut[512 + dense8];
-    #pragma unroll
+#pragma unroll
                             for (int j = 3; j < W / 8; ++j) {
                                 if (j < q)
                                     put(8 * (dense0 + (uint32_t)(j - 3) * len + 4 * gq), prmt(Wd[j], 0, sel), sel >> 16);

@@ -585,7 +585,7 @@ __global__ void __launch_bounds__(kDThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
                 const int q = coded ? ((int)rq + s) >> 3 : 2;
                 const int lmax = q < 3 ? q : 3;
                 uint32_t codes[NCODE];
-    #pragma unroll
+#pragma unroll
                 for (int i = 0; i < NCODE; ++i) codes[i] = 0;
                 if (coded) {
                     const uint8_t *lead = rec + rank * (b / 4) + sub * (VPL / 4);
@@ -605,7 +605,7 @@ __global__ void __launch_bounds__(kDThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
                 constexpr CntT FM = (CntT(1) << FB) - 1;
                 CntT cnt = 0;
                 if (coded) {
-    #pragma unroll
+#pragma unroll
                     for (int i = 0; i < NCODE; ++i) {
                         const int nv = nvalid - 16 * i;
                         const uint32_t vm = nv >= 16 ? 0x55555555u : (nv <= 0 ? 0u : (0x55555555u >> (2 * (16 - nv))));
@@ -615,7 +615,7 @@ __global__ void __launch_bounds__(kDThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
                     }
                 }
                 CntT incl = cnt;
-    #pragma unroll
+#pragma unroll
                 for (int d = 1; d < LPB; d <<= 1) {
                     const CntT y = __shfl_up_sync(kFull, incl, d);
                     if (sub >= d) incl += y;
@@ -637,7 +637,7 @@ __global__ void __launch_bounds__(kDThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
                 {
                     const uint32_t below = segmask & ((1u << lane) - 1u);
                     const uint32_t pj[3] = {pos0, pos1, pos2};
-    #pragma unroll
+#pragma unroll
                     for (int j = 0; j < 3; ++j) {
                         const bool has = coded && j < lmax && cj[j] > 0;
                         const uint32_t last = has ? rec[pj[j] + cj[j] - 1] : 0u;
@@ -649,7 +649,7 @@ __global__ void __launch_bounds__(kDThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
 
                 if (coded) {
                     const T mu = F::from(mu_bits);
-    #pragma unroll
+#pragma unroll
                     for (int gq = 0; gq < VPL / 4; ++gq) {
                         uint32_t code8 = (codes[gq >> 2] >> (8 * (gq & 3))) & 0xFFu;
                         uint32_t dense8 = 0;
@@ -662,7 +662,7 @@ __global__ void __launch_bounds__(kDThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
                         // plane words: byte k = byte j of value 4gq + k; a leading
                         // byte takes the nearest earlier owner's, or the carry
                         uint32_t P[W / 8];
-    #pragma unroll
+#pragma unroll
                         for (int j = 0; j < W / 8; ++j) P[j] = 0;
                         {
                             const uint32_t e0 = lut[code8];
@@ -682,7 +682,7 @@ __global__ void __launch_bounds__(kDThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
                             if (q >= 4) {
                                 // dense planes: every valid value owns its byte
                                 const uint32_t sel = full_lane ? 0x3210u : lut[512 + dense8];
-    #pragma unroll
+#pragma unroll
                                 for (int j = 3; j < W / 8; ++j)
                                     if (j < q)
                                         P[j] = dprmt(load_run(rec, dense0 + (uint32_t)(j - 3) * len + 4 * gq), 0, sel);
@@ -693,31 +693,31 @@ __global__ void __launch_bounds__(kDThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
                         if constexpr (NPW == 1) {
                             uint32_t Wq[4];
                             transpose4d(P[3], P[2], P[1], P[0], Wq);
-    #pragma unroll
+#pragma unroll
                             for (int kk = 0; kk < 4; ++kk) t[kk] = Wq[3 - kk];
                         } else {
                             uint32_t Wh[4], Wl[4];
                             transpose4d(P[3], P[2], P[1], P[0], Wh);
                             transpose4d(P[7], P[6], P[5], P[4], Wl);
-    #pragma unroll
+#pragma unroll
                             for (int kk = 0; kk < 4; ++kk) t[kk] = ((U)Wh[3 - kk] << 32) | (U)Wl[3 - kk];
                         }
-    #pragma unroll
+#pragma unroll
                         for (int kk = 0; kk < 4; ++kk) x[4 * gq + kk] = F::bits(F::add(F::from((U)(t[kk] << s)), mu));
                     }
                 } else if (raw) {
                     const uint8_t *p = rec + mbase + (uint32_t)sub * VPL * w;
-    #pragma unroll
+#pragma unroll
                     for (int m = 0; m < VPL; ++m) {
                         U u = 0;
                         if (m < nvalid) {
-    #pragma unroll
+#pragma unroll
                             for (int i = 0; i < w; ++i) u |= (U)p[m * w + i] << (8 * i);
                         }
                         x[m] = u;
                     }
                 } else {
-    #pragma unroll
+#pragma unroll
                     for (int m = 0; m < VPL; ++m) x[m] = mu_bits;
                 }
                 // strictness: the record's pad bytes (fewer than 16) must be zero
@@ -745,7 +745,7 @@ __global__ void __launch_bounds__(kDThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
                 __syncwarp();
             }
             if (exists && wanted && nvalid > 0) {
-    #pragma unroll
+#pragma unroll
                 for (int rr = 0; rr < RPL; ++rr) {
                     constexpr int VPR = 128 / w;  // values per row
                     const int nv = nvalid - rr * VPR;
@@ -753,27 +753,27 @@ __global__ void __launch_bounds__(kDThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
                     const uint32_t rowi = lane_row0 + rr;
                     if (FT || (tma_rows && wrow0 + rowi - Fd->row_lo < Fd->rows_full)) {
                         uint8_t *row = wbuf + (rowi << 7);
-    #pragma unroll
+#pragma unroll
                         for (int c = 0; c < 8; ++c) {
                             uint4 v;
                             U *u = reinterpret_cast<U *>(&v);
-    #pragma unroll
+#pragma unroll
                             for (int kk = 0; kk < 16 / w; ++kk) u[kk] = x[rr * VPR + c * (16 / w) + kk];
                             *reinterpret_cast<uint4 *>(row + ((c ^ (rowi & 7u)) << 4)) = v;
                         }
                     } else {
                         U *dst = reinterpret_cast<U *>(Fd->out) + (kg - Fd->blk_lo) * b + sub * VPL + rr * VPR;
                         if (nv >= VPR) {
-    #pragma unroll
+#pragma unroll
                             for (int c = 0; c < 8; ++c) {
                                 uint4 v;
                                 U *u = reinterpret_cast<U *>(&v);
-    #pragma unroll
+#pragma unroll
                                 for (int kk = 0; kk < 16 / w; ++kk) u[kk] = x[rr * VPR + c * (16 / w) + kk];
                                 reinterpret_cast<uint4 *>(dst)[c] = v;
                             }
                         } else {
-    #pragma unroll
+#pragma unroll
                             for (int m = 0; m < VPR; ++m)
                                 if (m < nv) dst[m] = x[rr * VPR + m];
                         }
