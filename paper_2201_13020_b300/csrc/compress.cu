@@ -15,12 +15,16 @@
 // Per CTA: a ring of three tile buffers and three roles.  A producer thread
 // takes tickets and copies tiles in with the TMA unit (2-D tensor copy, rows
 // of 128 B, 128-byte swizzle, so that each lane reads its row without bank
-// conflicts); eight consumer warps encode a tile and build its record in
-// place; a storer warp places and stores records.  The roles hand stages to
+// conflicts); it takes a tile's ticket only once the consumers are on the tile
+// before it, which keeps the look-back waits short.  Eight consumer warps
+// encode a tile and build its record in place; a storer warp places and
+// stores records.  The roles hand stages to
 // each other through mbarriers (full / encoded / ready / empty), so encoding
 // never waits for a look-back or a store, and every wait is bounded.  The
 // same kernel serves one field (its descriptor is a kernel parameter) and
-// batches (a table of descriptors in device memory, BATCH).  Per tile:
+// batches (a table of descriptors in device memory, BATCH).  Tiles wholly
+// inside the input run a copy of the per-tile work compiled for full blocks.
+// Per tile:
 //   1. each consumer warp loads its rows and clears them (the buffer becomes
 //      the record), then encodes in registers -- block statistics
 //      (Algorithm 1): NaN-propagating min/max per lane, reduced over the
@@ -30,20 +34,22 @@
 //      bound_check_needed); otherwise a fast test runs and an exact slow path
 //      re-checks a block that fails it, raising reqBits while a value exceeds
 //      e.  Then the identical-leading-byte codes against the previous value
-//      and the lanes' mid-byte counts.  The warp writes its blocks' mu values
-//      and publishes its totals;
+//      (from each word's top 32 bits) and the lanes' mid-byte counts.  The
+//      warp writes its blocks' mu values, publishes its totals and forms its
+//      lanes' plane counts;
 //   2. the warps meet once (an mbarrier); warp reductions of the warps'
 //      totals give every block its rank and mid-byte offset; warp 0 publishes
-//      the tile's record size for the look-back and writes the state bits;
+//      the tile's record size for the look-back;
 //   3. lanes write lead codes, reqBits bytes and the mid-byte planes (plane j
 //      = byte j of every value whose code is <= j, ascending index): a 4x4
 //      byte transpose of four values gives their byte-j word, a 256-entry
 //      table compacts the selected bytes, and shared-memory OR writes place the
-//      run at its bit offset;
+//      run at its bit offset (two funnel shifts);
 //   4. the storer finishes the look-back, writes the tile index entry and
-//      bulk-stores the record (cp.async.bulk) to its offset; once the store
-//      has read the buffer, the producer refills it.  The last CTA to finish
-//      writes each field's header.
+//      bulk-stores the record (cp.async.bulk) to its offset, writing the
+//      tile's state bits and counts while the store reads; once it has read
+//      the buffer, the producer refills it.  The last CTA to finish writes
+//      each field's header.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -730,7 +736,7 @@ __global__ void __launch_bounds__(kCThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
         uint8_t *buf = smem + st * L.buf_stride;
         uint8_t *meta = smem + (L.meta0 + st * L.meta_stride);
         uint8_t *sm_kind = meta + L.m_kind;
-        uint4 *sm_w = reinterpret_cast<uint4 *>(meta + L.m_w);  // per warp: nn, mid, raw, escalated
+        uint4 *sm_w = reinterpret_cast<uint4 *>(meta + L.m_w);  // per warp: nn << 20 | mid, raw, escalated
         const uint64_t k0 = (uint64_t)tile * G;
         const uint32_t Gt = (uint32_t)min_u64(G, g.nb - k0);
         const uint64_t row0 = (uint64_t)tile * 256 * RPL;
