@@ -28,8 +28,11 @@
 //     (one 2-D box of 32 rows per warp).  The ragged last row goes out with
 //     plain stores.  Warp 0 also checks that the record's padding is zero.
 // The same kernel serves a single stream (its descriptor is a kernel
-// parameter) and batches (a table of descriptors in device memory, BATCH),
-// and decodes a block range for random access.
+// parameter; CTA c takes tiles c, c + gridDim.x, ...) and batches (a table
+// of descriptors in device memory, BATCH; CTAs take tiles by ticket, which
+// balances fields of unequal cost), and decodes a block range for random
+// access.  Tiles wholly inside the field and the range run a copy of the
+// decoders' work compiled for full blocks.
 //
 // Work layout as in the compressor: every lane owns 128 contiguous output
 // bytes (32 f32 or 16 f64 values); a block of b values spans LPB = b / VPL
