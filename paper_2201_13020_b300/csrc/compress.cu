@@ -299,6 +299,14 @@ __device__ __forceinline__ void encode_lane(typename Fmt<T>::U (&x)[VPL], uint32
     R = R < 0 ? 0 : (R > F::M ? F::M : R);
     req0 = 1 + F::E + R;
     req = req0;
+    if (__all_sync(kFull, kind != kNonConst)) {
+        // no block of the warp keeps truncated values (all constant, raw or
+        // absent): truncation, bound checks and lead codes would go unused
+#pragma unroll
+        for (int i = 0; i < NCODE; ++i) codes[i] = 0;
+        mk_out = kind == kRaw ? (uint32_t)nvalid * w : 0u;
+        return;
+    }
     const bool check = kind == kNonConst && bound_check_needed<T>(mn, mx, mu, R, (U)e_bits);
 
     // truncation; with `check`, a fast test of every value (one rounding)
