@@ -346,7 +346,7 @@ __device__ __forceinline__ void encode_lane(typename Fmt<T>::U (&x)[VPL], uint32
     if (pending && sub == 0) atomicAdd(&ws->diag[0], 1u);
     int rounds = 0;
     while (__any_sync(kFull, pending)) {
-        if (SZX_CHECKS && ++rounds > 40) {
+        if (SZX_CHECKS && ++rounds > W) {  // reqBits rises one bit a round, at most to W
             if (lane == 0) report_bad(ws, tile, 3);
             if (pending) kind = kRaw;
             break;
@@ -896,7 +896,9 @@ __global__ void __launch_bounds__(kCThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
             // every record write goes through put() (positions in bits, c8 = 8 x
             // bytes): a self-checked build verifies that it lands inside the record
             auto put = [&](uint32_t pb, uint32_t run, uint32_t c8) {
-                if (SZX_CHECKS && ((pb >> 3) + 8 > L.buf_bytes || ((pb + c8) >> 3) > rec_bytes)) {
+                // (a run of no bytes -- a group past a partial block's end -- ORs
+                // zeros: only its words must lie in the buffer)
+                if (SZX_CHECKS && ((pb >> 3) + 8 > L.buf_bytes || (c8 && ((pb + c8) >> 3) > rec_bytes))) {
                     report_bad(Fd->ws, tile, 1);
                     return;
                 }
