@@ -582,6 +582,46 @@ __global__ void __launch_bounds__(kCThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
             const Geometry &g = F->g;
             uint64_t *lookback = F->lookback;
             const uint32_t rec_bytes = st_rec[st];
+            auto counts_and_state = [&]() {
+                // the field's counts (the header is written once every CTA is
+                // done) and the tile's state bits, from the warps' totals and
+                // the block kinds in the stage's metadata
+                const uint8_t *meta = smem + (L.meta0 + st * L.meta_stride);
+                const uint4 wt = lane < kConsumerWarps ? reinterpret_cast<const uint4 *>(meta + L.m_w)[lane]
+                                                       : make_uint4(0, 0, 0, 0);
+                const uint32_t nn_t = __reduce_add_sync(kFull, wt.x) >> 20;
+                const uint32_t raw_t = __reduce_add_sync(kFull, wt.y), esc_t = __reduce_add_sync(kFull, wt.z);
+                if (lane == 0) {
+                    Workspace *ws = F->ws;
+                    if (nn_t) atomicAdd(&ws->nn, (unsigned long long)nn_t);
+                    if (raw_t) atomicAdd(&ws->nraw, (unsigned long long)raw_t);
+                    if (esc_t) atomicAdd(&ws->nesc, (unsigned long long)esc_t);
+                }
+                // bit i of byte j is set when block 8j + i is not constant
+                const uint8_t *sm_kind = meta + L.m_kind;
+                const uint64_t k0 = (uint64_t)tile * G;
+                const uint32_t Gt = (uint32_t)min_u64(G, g.nb - k0);
+                uint8_t *state = F->out + g.off_state + (size_t)k0 / 8;
+                for (uint32_t j = lane; j < (Gt + 7) / 8; j += 32) {
+                    uint32_t byte = 0;
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) {
+                        const uint32_t kk = j * 8 + i;
+                        if (kk < Gt && sm_kind[kk] != kConst) byte |= 1u << i;
+                    }
+                    state[j] = (uint8_t)byte;
+                }
+            };
+            // A tile whose record is empty (every block constant) has nothing
+            // to store: its counts and state bits go out now, and its buffer
+            // is free before the look-back.  Otherwise they go out while the
+            // store reads the record.
+            const bool empty_rec = rec_bytes == 0;
+            if (empty_rec) {
+                counts_and_state();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&empty[st]);
+            }
             // warp-parallel decoupled look-back: 32 predecessors per probe,
             // lane i looking at tile - 1 - i; stop at the nearest inclusive
             // prefix, adding the aggregates in between
@@ -639,40 +679,14 @@ __global__ void __launch_bounds__(kCThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
                     bulk_commit();
                 }
             }
-            {
-                // while the store reads the record: the field's counts (the
-                // header is written once every CTA is done) and the state
-                // bits, from the warps' totals and the block kinds
-                const uint8_t *meta = smem + (L.meta0 + st * L.meta_stride);
-                const uint4 wt = lane < kConsumerWarps ? reinterpret_cast<const uint4 *>(meta + L.m_w)[lane]
-                                                       : make_uint4(0, 0, 0, 0);
-                const uint32_t nn_t = __reduce_add_sync(kFull, wt.x) >> 20;
-                const uint32_t raw_t = __reduce_add_sync(kFull, wt.y), esc_t = __reduce_add_sync(kFull, wt.z);
+            if (!empty_rec) {
+                counts_and_state();
+                __syncwarp();
                 if (lane == 0) {
-                    Workspace *ws = F->ws;
-                    if (nn_t) atomicAdd(&ws->nn, (unsigned long long)nn_t);
-                    if (raw_t) atomicAdd(&ws->nraw, (unsigned long long)raw_t);
-                    if (esc_t) atomicAdd(&ws->nesc, (unsigned long long)esc_t);
+                    // the buffer is free once the store has read it
+                    bulk_wait_read_all();
+                    mbar_arrive(&empty[st]);
                 }
-                // bit i of byte j is set when block 8j + i is not constant
-                const uint8_t *sm_kind = meta + L.m_kind;
-                const uint64_t k0 = (uint64_t)tile * G;
-                const uint32_t Gt = (uint32_t)min_u64(G, g.nb - k0);
-                uint8_t *state = out + g.off_state + (size_t)k0 / 8;
-                for (uint32_t j = lane; j < (Gt + 7) / 8; j += 32) {
-                    uint32_t byte = 0;
-#pragma unroll
-                    for (int i = 0; i < 8; ++i) {
-                        const uint32_t kk = j * 8 + i;
-                        if (kk < Gt && sm_kind[kk] != kConst) byte |= 1u << i;
-                    }
-                    state[j] = (uint8_t)byte;
-                }
-            }
-            if (lane == 0) {
-                // the buffer is free once the store has read it
-                if (rec_bytes) bulk_wait_read_all();
-                mbar_arrive(&empty[st]);
             }
             __syncwarp();
         }
