@@ -98,18 +98,19 @@ __device__ __forceinline__ uint32_t field_of(const CompressLaunch &lc, uint64_t 
 }
 
 // ---------------------------------------------------------------------------
-// compaction table: for plane j in 0..2 and the 2-bit codes of four values
-// (value k at bits 2k), entry = byte-permute selector taking, in order, the
-// bytes of the values whose code is <= j (unused nibbles select zero), plus
-// the number of such values << 16.  Built at compile time.
+// compaction table: for the 2-bit codes of four values (value k at bits 2k),
+// one 16-byte entry whose word j (j = 0..2; word 3 repeats word 2) is the
+// byte-permute selector taking, in order, the bytes of the values whose code
+// is <= j (unused nibbles select zero), plus the number of such values << 16.
+// Built at compile time.
 
 struct PlaneLut {
-    uint32_t v[768];
+    uint32_t v[1024];
 };
 constexpr PlaneLut make_plane_lut() {
     PlaneLut t{};
-    for (uint32_t i = 0; i < 768; ++i) {
-        const uint32_t j = i >> 8, code = i & 255u;
+    for (uint32_t i = 0; i < 1024; ++i) {
+        const uint32_t j = (i & 3u) < 2u ? (i & 3u) : 2u, code = i >> 2;
         uint32_t sel = 0x4444u, cnt = 0;
         for (uint32_t k = 0; k < 4; ++k) {
             if (((code >> (2 * k)) & 3u) <= j) {
@@ -392,14 +393,24 @@ __device__ __forceinline__ void encode_lane(typename Fmt<T>::U (&x)[VPL], uint32
         if (sub == 0) prev = 0;
         // a set bit in byte lmax (counted from the top) caps the count at lmax
         const uint32_t cap = 1u << (31 - 8 * lmax);
+        // each value's code in its own word first, then an OR tree (no
+        // serial chain through the code words)
+        uint32_t part[VPL];
 #pragma unroll
         for (int m = 0; m < VPL; ++m) {
             const uint32_t top = (uint32_t)(x[m] >> (W - 32));
             int l = __clz((top ^ prev) | cap) >> 3;
             if (!FULL && m >= nvalid) l = 0;
-            codes[m >> 4] += (uint32_t)l << (2 * (m & 15));
+            part[m] = (uint32_t)l << (2 * (m & 15));
             prev = top;
         }
+#pragma unroll
+        for (int d = 1; d < 16; d <<= 1) {
+#pragma unroll
+            for (int m = 0; m + d < VPL; m += 2 * d) part[m] |= part[m + d];
+        }
+#pragma unroll
+        for (int i = 0; i < NCODE; ++i) codes[i] = part[16 * i];
     }
     uint32_t suml = 0;
 #pragma unroll
@@ -443,7 +454,7 @@ __host__ __device__ inline CSmem compress_smem(uint32_t G, uint32_t b, uint32_t 
     s.meta_stride = (m + 15) & ~15u;
     s.meta0 = (kStages - 1) * s.buf_stride + s.buf_bytes;  // after the last buffer (16-aligned)
     s.lut = s.meta0 + kStages * s.meta_stride;
-    const uint32_t o = s.lut + 3 * 256 * 4;
+    const uint32_t o = s.lut + 256 * 16;
     s.total = ((o + 1023) & ~1023u) + 1024;  // + slack to realign the dynamic base
     return s;
 }
@@ -487,7 +498,7 @@ __global__ void __launch_bounds__(kCThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
     {
         const uint4 *src = reinterpret_cast<const uint4 *>(kPlaneLut.v);
         uint4 *dst = reinterpret_cast<uint4 *>(lut);
-        for (int i = tid; i < 768 / 4; i += kCThreads) dst[i] = src[i];
+        for (int i = tid; i < 256; i += kCThreads) dst[i] = src[i];
     }
     if (tid == 0) {
         for (int i = 0; i < kStages; ++i) {
@@ -982,21 +993,17 @@ __global__ void __launch_bounds__(kCThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
                                 Wd[4 + j] = Wl[j];
                             }
                         }
-                        {
-                            const uint32_t e0 = lut[code8];
-                            put(pos0, prmt(Wd[0], 0, e0), e0 >> 16);
-                            pos0 += e0 >> 16;
-                            const uint32_t e1 = lut[256 + code8];
-                            put(pos1, prmt(Wd[1], 0, e1), e1 >> 16);
-                            pos1 += e1 >> 16;
-                        }
+                        const uint4 e = reinterpret_cast<const uint4 *>(lut)[code8];
+                        put(pos0, prmt(Wd[0], 0, e.x), e.x >> 16);
+                        pos0 += e.x >> 16;
+                        put(pos1, prmt(Wd[1], 0, e.y), e.y >> 16);
+                        pos1 += e.y >> 16;
                         if (q >= 3) {
-                            const uint32_t e2 = lut[512 + code8];
-                            put(pos2, prmt(Wd[2], 0, e2), e2 >> 16);
-                            pos2 += e2 >> 16;
+                            put(pos2, prmt(Wd[2], 0, e.z), e.z >> 16);
+                            pos2 += e.z >> 16;
                         }
                         if (q >= 4) {
-                            const uint32_t sel = full_lane ? (0x3210u | (32u << 16)) : lut[512 + dense8];
+                            const uint32_t sel = full_lane ? (0x3210u | (32u << 16)) : lut[4 * dense8 + 2];
 #pragma unroll
                             for (int j = 3; j < W / 8; ++j) {
                                 if (j < q)
