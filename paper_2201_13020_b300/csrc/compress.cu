@@ -393,24 +393,47 @@ __device__ __forceinline__ void encode_lane(typename Fmt<T>::U (&x)[VPL], uint32
         if (sub == 0) prev = 0;
         // a set bit in byte lmax (counted from the top) caps the count at lmax
         const uint32_t cap = 1u << (31 - 8 * lmax);
-        // each value's code in its own word first, then an OR tree (no
-        // serial chain through the code words)
-        uint32_t part[VPL];
+        if constexpr (FULL) {
+            // c = clz holds the code in its bits 3-4.  Shifting c so that
+            // those bits land on the code's place 2k (k = m mod 16) leaves
+            // c's bits 0-2 just below it; values with the same k mod 4 OR
+            // into one word, where those bits never reach another code, and
+            // one mask per word keeps the codes alone
+            uint32_t acc[NCODE][4];
 #pragma unroll
-        for (int m = 0; m < VPL; ++m) {
-            const uint32_t top = (uint32_t)(x[m] >> (W - 32));
-            int l = __clz((top ^ prev) | cap) >> 3;
-            if (!FULL && m >= nvalid) l = 0;
-            part[m] = (uint32_t)l << (2 * (m & 15));
-            prev = top;
+            for (int i = 0; i < NCODE; ++i) acc[i][0] = acc[i][1] = acc[i][2] = acc[i][3] = 0;
+#pragma unroll
+            for (int m = 0; m < VPL; ++m) {
+                const uint32_t top = (uint32_t)(x[m] >> (W - 32));
+                const uint32_t c = (uint32_t)__clz((top ^ prev) | cap);
+                const int p = 2 * (m & 15) - 3;
+                acc[m >> 4][m & 3] |= p >= 0 ? (c << p) : (c >> -p);
+                prev = top;
+            }
+#pragma unroll
+            for (int i = 0; i < NCODE; ++i)
+                codes[i] = (acc[i][0] & 0x03030303u) | (acc[i][1] & 0x0C0C0C0Cu) | (acc[i][2] & 0x30303030u) |
+                           (acc[i][3] & 0xC0C0C0C0u);
+        } else {
+            // each value's code in its own word first, then an OR tree (no
+            // serial chain through the code words)
+            uint32_t part[VPL];
+#pragma unroll
+            for (int m = 0; m < VPL; ++m) {
+                const uint32_t top = (uint32_t)(x[m] >> (W - 32));
+                int l = __clz((top ^ prev) | cap) >> 3;
+                if (m >= nvalid) l = 0;
+                part[m] = (uint32_t)l << (2 * (m & 15));
+                prev = top;
+            }
+#pragma unroll
+            for (int d = 1; d < 16; d <<= 1) {
+#pragma unroll
+                for (int m = 0; m + d < VPL; m += 2 * d) part[m] |= part[m + d];
+            }
+#pragma unroll
+            for (int i = 0; i < NCODE; ++i) codes[i] = part[16 * i];
         }
-#pragma unroll
-        for (int d = 1; d < 16; d <<= 1) {
-#pragma unroll
-            for (int m = 0; m + d < VPL; m += 2 * d) part[m] |= part[m + d];
-        }
-#pragma unroll
-        for (int i = 0; i < NCODE; ++i) codes[i] = part[16 * i];
     }
     uint32_t suml = 0;
 #pragma unroll
