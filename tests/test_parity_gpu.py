@@ -12,6 +12,7 @@ import pytest
 import oracle
 import szx_stream as ss
 from exact import exact_abs_diff_le
+from cases import VALUE_RELS, bound_for, inputs_tile, value_distribution_cases
 
 torch = pytest.importorskip("torch")
 import paper_2201_13020_b300 as szx  # noqa: E402
@@ -83,35 +84,13 @@ def test_sizes_and_blocks(dtype, block):
         assert_parity(x, eb, block)
 
 
-def inputs_tile(block, dtype):
-    w = np.dtype(dtype).itemsize
-    return max(8, 32768 // (block * w)) * block
-
-
 @pytest.mark.parametrize("dtype", [np.float32, np.float64])
 def test_value_distributions(dtype):
-    rng = np.random.default_rng(5)
-    n = 3 * inputs_tile(128, dtype) + 333
-    cases = {
-        "smooth": np.sin(np.linspace(0, 50, n)) + 1e-3 * rng.normal(size=n),
-        "noise": rng.normal(size=n),
-        "cauchy": rng.standard_cauchy(size=n),
-        "tiny": rng.normal(size=n) * 1e-38,
-        "huge": rng.normal(size=n) * (1e37 if dtype == np.float32 else 1e300),
-        "offset": 1000.0 + np.cumsum(rng.normal(size=n)) * 0.01,
-        "steps": np.repeat(rng.normal(size=n // 100 + 1), 100)[:n],
-        "zeros": np.where(rng.random(n) < 0.5, 0.0, -0.0),
-        "signs": rng.choice([-1.0, 1.0], size=n) * rng.uniform(0.5, 1.0, size=n),
-    }
-    for name, v in cases.items():
+    for name, v in value_distribution_cases(dtype).items():
         x = v.astype(dtype)
-        for rel in (1e-1, 1e-3, 1e-6):
-            rngv = float(np.max(x)) - float(np.min(x))
-            eb = rel * rngv if np.isfinite(rngv) and rngv > 0 else 1e-3
-            if not np.isfinite(eb) or eb <= 0:
-                eb = 1e-3
+        for rel in VALUE_RELS:
             try:
-                assert_parity(x, eb, 128)
+                assert_parity(x, bound_for(x, rel), 128)
             except AssertionError as exc:
                 raise AssertionError(f"{name} rel={rel}: {exc}") from None
 
