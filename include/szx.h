@@ -20,11 +20,13 @@
  * Conventions for every call below:
  *   - Pointers named d_* are CUDA device pointers on the current device and
  *     must be 16-byte aligned; the caller allocates and owns all of them.
- *     The compress calls keep their scratch in the tail of the caller's
- *     output buffer (see szx_compress_bound) and allocate nothing; the only
- *     device allocation of the codec calls is the small array of status
- *     words that the synchronous szx_decompress takes once per device, on its
- *     first call there (szx_compress_static_async allocates nothing at all).
+ *     No compress or decompress call allocates memory: the compress calls
+ *     keep their scratch in the tail of the caller's output buffer (see
+ *     szx_compress_bound) or, for szx_compress_static_async, in a fixed array
+ *     inside the library; the synchronous szx_decompress takes its status
+ *     word from another fixed array inside the library.  (The batch planning
+ *     calls and szx_server_create allocate host memory, and the server its
+ *     own small status words, as documented there.)
  *   - `stream` is a cudaStream_t (0 = the legacy default stream).  All device
  *     work is enqueued on it in order.
  *   - Values are IEEE 754 binary32 (SZX_F32) or binary64 (SZX_F64), little
@@ -82,6 +84,11 @@ typedef struct {
  * per-block metadata) followed by the call's device scratch space (tile
  * tickets and the look-back status words of the offset scan).  Returns 0 for
  * invalid arguments.  Host-only; no CUDA call.
+ * Paper: Algorithm 1 stores either mu_k alone (constant block) or a block's
+ * lead codes and mid bytes, and the mid bytes of a value are at most its
+ * whole width (Eq. 4 clamps R_k at the mantissa width); the bound is that
+ * worst case, every block kept verbatim, plus the per-block metadata of the
+ * stream layout.
  */
 size_t szx_compress_bound(size_t n, szx_dtype dtype, uint32_t block);
 
@@ -140,8 +147,11 @@ szx_status szx_compress_async(const void *d_in, size_t n, szx_dtype dtype,
  *
  * Set-up: the first call made with a given device current looks up that
  * device's array address (cudaGetSymbolAddress, which may load the
- * library's device code); make that first call before any stream capture.
- * Each call clears the array prefix it uses on `stream` before its kernel.
+ * library's device code) and keeps it; make that first call before any
+ * stream capture.  A cudaDeviceReset (or any other destruction of the
+ * device's primary context) between calls is not supported: the kept
+ * address would be stale.  Each call clears the array prefix it uses on
+ * `stream` before its kernel.
  *
  * Sharing: all calls on one device use the same array.  Calls that can
  * overlap in time (on different streams, or from different host threads
@@ -164,6 +174,11 @@ szx_status szx_compress_static_async(const void *d_in, size_t n,
  * one 64-byte device-to-host copy, synchronous on `stream`).  Errors:
  * SZX_ERR_INVALID (null), SZX_ERR_CORRUPT (bad magic, version, dtype, block,
  * tile size, or total_bytes > in_bytes), SZX_ERR_CUDA.
+ * Paper: the header carries what decompression needs besides the blocks
+ * (Sec. III's problem: N, the value type and e; Sec. V-A.2's block size b);
+ * the paper fixes no byte layout, so the fields and their order are this
+ * library's (little endian: magic, version, dtype, b, blocks per tile, n, the
+ * bits of e, counts of non-constant, raw and escalated blocks, total bytes).
  */
 szx_status szx_header_read(const void *d_in, size_t in_bytes, szx_header *h,
                            szx_stream_t stream);
@@ -173,10 +188,16 @@ szx_status szx_header_read(const void *d_in, size_t in_bytes, szx_header *h,
  * stream's dtype; out_capacity >= n * 4 or n * 8 bytes).  *n_out and
  * *dtype_out receive the header's values (either may be NULL).  Every read
  * of the stream is bounds-checked on the device; a malformed stream returns
- * SZX_ERR_CORRUPT.  Synchronous.  The device status word it uses is one of a
- * set of 256 that the library allocates on its first call on each device and
- * keeps until exit; concurrent calls from up to 256 host threads get distinct
- * words.
+ * SZX_ERR_CORRUPT.  Synchronous (one 64-byte header read, the kernel, one
+ * 4-byte status read).  Allocates nothing: its device status word is one of
+ * 256 words of a fixed array inside the library, taken round-robin, so that
+ * up to 256 calls in flight at once (from different host threads) get
+ * distinct words.
+ * Paper: the inverse of Algorithm 1 -- a constant block decodes to mu_k; a
+ * non-constant block rebuilds each truncated word from its lead code (the
+ * identical leading bytes come from the previous value) and its mid bytes,
+ * undoes the Eq. 5 shift and adds mu_k (d'_i = RN((t_i << s) + mu_k)); Sec.
+ * V-B describes the GPU decoder whose prefix scan the tile index replaces.
  */
 szx_status szx_decompress(const void *d_in, size_t in_bytes, void *d_out,
                           size_t out_capacity, size_t *n_out,
@@ -187,7 +208,11 @@ szx_status szx_decompress(const void *d_in, size_t in_bytes, void *d_out,
  * holds (from szx_header_read, or from the compressing side).  The kernel
  * re-checks the stream's header against *h.  On completion *d_status (device
  * pointer, may be NULL) holds a szx_status; the call sets it to SZX_OK first.
- * Safe to capture in a CUDA graph.
+ * Safe to capture in a CUDA graph.  Errors returned at once: SZX_ERR_INVALID
+ * (null or misaligned pointers, a header with an invalid dtype, block, n or
+ * tile size), SZX_ERR_CORRUPT (total_bytes outside [sections, in_bytes]),
+ * SZX_ERR_TOO_SMALL (out_capacity), SZX_ERR_CUDA.
+ * Paper: as szx_decompress (the inverse of Algorithm 1; Sec. V-B).
  */
 szx_status szx_decompress_async(const void *d_in, size_t in_bytes,
                                 const szx_header *h, void *d_out,

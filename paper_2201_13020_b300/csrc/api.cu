@@ -37,28 +37,23 @@ uint64_t stream_max(uint64_t n, uint32_t b, uint32_t w) {
 
 szx_status from_cuda(cudaError_t e) { return e == cudaSuccess ? SZX_OK : SZX_ERR_CUDA; }
 
-// Per-device status words for the synchronous decompress (allocated once per
-// device on first use, kept until exit).
+// Status words of the synchronous decompress: a fixed array in the library's
+// device memory (every device that loads the library holds one), so the call
+// allocates nothing.  Its address is looked up on every call (a host-side
+// lookup once the module is loaded).  Calls take words round-robin, so up to
+// kSlots calls in flight at once get distinct words.
 constexpr int kSlots = 256;
-std::mutex g_ctx_mu;
-uint32_t *g_status[64] = {};
+static __device__ __align__(256) uint32_t g_sync_status[kSlots];
 std::atomic<uint32_t> g_slot{0};
 
 uint32_t *status_slot(szx_status *st) {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+    void *base = nullptr;
+    if (cudaGetSymbolAddress(&base, g_sync_status) != cudaSuccess || !base) {
         *st = SZX_ERR_CUDA;
         return nullptr;
     }
-    std::lock_guard<std::mutex> lock(g_ctx_mu);
-    if (!g_status[dev]) {
-        if (cudaMalloc(&g_status[dev], kSlots * sizeof(uint32_t)) != cudaSuccess) {
-            *st = SZX_ERR_CUDA;
-            return nullptr;
-        }
-    }
     *st = SZX_OK;
-    return g_status[dev] + (g_slot.fetch_add(1) % kSlots);
+    return static_cast<uint32_t *>(base) + (g_slot.fetch_add(1) % kSlots);
 }
 
 szx_status parse_header(const uint8_t *h, uint64_t in_bytes, szx_header *out) {

@@ -14,7 +14,9 @@
 // The look-back workspace (a 128-byte header of counters plus one 8-byte
 // flag word per tile) lives in g_static_ws below.  Its device address is
 // looked up once per device with cudaGetSymbolAddress, under a mutex, on the
-// first call made with that device current; later calls reuse it.  Every
+// first call made with that device current; later calls reuse it.  So a
+// cudaDeviceReset between calls (which reloads the module, possibly at
+// another address) is not supported, as szx.h states.  Every
 // call clears the part of the array it uses (cudaMemsetAsync on the caller's
 // stream) before the kernel starts, because the tile counters and look-back
 // flags must start at zero.  All calls on one device share the array, so two

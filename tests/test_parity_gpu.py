@@ -95,6 +95,37 @@ def test_value_distributions(dtype):
                 raise AssertionError(f"{name} rel={rel}: {exc}") from None
 
 
+def _pow2_bounds(p, dtype):
+    """e = 2^p and its two neighbours in the value's format."""
+    e = dtype(2.0 ** p)
+    return [float(e), float(np.nextafter(e, dtype(np.inf))), float(np.nextafter(e, dtype(0)))]
+
+
+@pytest.mark.parametrize("dtype", [np.float32, np.float64])
+@pytest.mark.parametrize("block", [32, 128, 1024])
+def test_power_of_two_bounds(dtype, block):
+    """Bounds e = 2^p, the next value above and the next below, with p spanning
+    the data's exponents.  This is where Eq. 4's estimate is tightest (the
+    lowest kept bit weighs 2^p(e), up to e itself) and where the kernel's
+    block-level proof that the per-value check passes changes its answer:
+    the proof compares powers of two against e's significand, which is 1 at
+    e = 2^p, 2 - ulp just below it and 1 + ulp just above.  Byte-exact against
+    the oracle, at least three tiles with a ragged tail."""
+    rng = np.random.default_rng(block * 3 + (dtype == np.float64))
+    n = 3 * inputs_tile(block, dtype) + 77
+    walk = (np.cumsum(rng.normal(size=n)) * 0.37).astype(dtype)      # |x| up to ~2^6
+    offset = (1000.0 + np.cumsum(rng.normal(size=n)) * 1e-3).astype(dtype)  # p(x) = 9, small r
+    cases = [("walk", walk, (-16, -8, -4, -1, 0, 3)), ("offset", offset, (-14, -13, -12, -10))]
+    for name, x, ps in cases:
+        for p in ps:
+            for eb in _pow2_bounds(p, dtype):
+                try:
+                    s, y = assert_parity(x, eb, block)
+                except AssertionError as exc:
+                    raise AssertionError(f"{name} p={p} eb={eb!r}: {exc}") from None
+                assert exact_abs_diff_le(x, y, _e(eb, dtype)).all(), (name, p, eb)
+
+
 @pytest.mark.parametrize("dtype", [np.float32, np.float64])
 def test_nonfinite_and_overflow_blocks_are_raw(dtype):
     rng = np.random.default_rng(8)

@@ -1,9 +1,13 @@
 """The serving loop (szx_server_*): every result is the same alone and in
-the mix (streams byte-identical, decodes bit-exact), admission waits for pool
+the mix (streams byte-identical, decodes bit-exact) and the same as the CPU
+oracle's (the complex f64 state vectors included), admission waits for pool
 memory, a request that can never fit is reported, and the pool accounting
 returns to empty."""
 import numpy as np
 import pytest
+
+import oracle
+from exact import exact_abs_diff_le
 
 torch = pytest.importorskip("torch")
 import paper_2201_13020_b300 as szx  # noqa: E402
@@ -43,13 +47,26 @@ def test_mixed_requests_match_each_request_alone():
         assert r.admit_s >= r.arrival - 1e-9 and r.done_s >= r.admit_s
         if r.kind == "compress":
             alone = szx.compress(r.x, r.eb, r.block)
-            assert torch.equal(server.view(r.offset, r.nbytes), alone), f"request {i}: stream differs"
+            served = server.view(r.offset, r.nbytes)
+            assert torch.equal(served, alone), f"request {i}: stream differs"
+            # the oracle on the same values: the served stream byte for byte
+            ref = oracle.compress(r.x.cpu().numpy(), r.eb, r.block)
+            assert np.array_equal(served.cpu().numpy(), ref), f"request {i}: stream differs from the oracle"
         else:
             src = reqs[r.source]
             alone = szx.decompress(szx.compress(src.x, src.eb, src.block))
             got = server.output(r)
             it = torch.int32 if alone.dtype == torch.float32 else torch.int64
             assert torch.equal(got.view(it), alone.view(it)), f"request {i}: decode differs"
+            xs = src.x.cpu().numpy()
+            ref = oracle.decompress(oracle.compress(xs, src.eb, src.block))
+            ui = np.uint32 if xs.dtype == np.float32 else np.uint64
+            assert np.array_equal(got.cpu().numpy().view(ui), ref.view(ui)), \
+                f"request {i}: decode differs from the oracle"
+            e = oracle.error_bound(src.eb, oracle.F32 if xs.dtype == np.float32 else oracle.F64)
+            assert exact_abs_diff_le(xs, got.cpu().numpy(), e).all(), f"request {i}: bound"
+    kinds = {reqs[r.source].x.dtype for r in reqs if r.kind == "decompress"}
+    assert kinds == {torch.float32, torch.float64}  # state vectors and f32 fields were both decoded
     # give everything back: the pool is empty again
     for r in reqs:
         if r.kind == "compress" or r.keep_output:

@@ -19,20 +19,39 @@ def _vp(p):
     return ctypes.c_void_p(p)
 
 
-def test_static_limit_and_capacity_rejected_on_host():
-    # Both checks return before any CUDA call, so fake (aligned, non-null)
-    # device addresses are never dereferenced.
+def _tile_values(dtype, block):
+    """Values per tile: G = max(8, 32768 / (b * w)) blocks of b values."""
+    w = 4 if dtype == _lib.SZX_F32 else 8
+    return max(8, 32768 // (block * w)) * block
+
+
+@pytest.mark.parametrize("dtype,block", [(_lib.SZX_F32, 128), (_lib.SZX_F64, 128), (_lib.SZX_F64, 1024),
+                                         (_lib.SZX_F32, 32)])
+def test_static_limit_and_capacity_rejected_on_host(dtype, block):
+    # Every check below returns before any CUDA call, so the fake (aligned,
+    # non-null) device addresses are never dereferenced.  f64 with b = 1024 is
+    # the geometry where a tile holds the minimum of 8 blocks (64 KiB).
     L = _lib.lib()
     max_tiles = ((1 << 20) - 128) // 8
-    n_tile = 64 * 128  # f32, block 128: 64 blocks per tile
-    n_over = (max_tiles + 1) * n_tile
-    st = L.szx_compress_static_async(_vp(256), n_over, _lib.SZX_F32, 1e-3, 128, _vp(512), 1 << 62,
+    tile = _tile_values(dtype, block)
+    # one tile beyond the array: rejected as too large for the fixed scratch
+    n_over = (max_tiles + 1) * tile
+    st = L.szx_compress_static_async(_vp(256), n_over, dtype, 1e-3, block, _vp(512), 1 << 62, None, None)
+    assert st == SZX_ERR_INVALID
+    # so is a ragged tile past the limit
+    st = L.szx_compress_static_async(_vp(256), max_tiles * tile + 1, dtype, 1e-3, block, _vp(512), 1 << 62,
                                      None, None)
     assert st == SZX_ERR_INVALID
+    # exactly the limit is accepted by the tile check: a capacity just short
+    # of the stream maximum then fails on capacity, not on the tile count
+    n_max = max_tiles * tile
+    smax = L.szx_stream_max_bytes(n_max, dtype, block)
+    assert smax > 0
+    st = L.szx_compress_static_async(_vp(256), n_max, dtype, 1e-3, block, _vp(512), smax - 16, None, None)
+    assert st == SZX_ERR_TOO_SMALL
     n_ok = 10_000
-    smax = L.szx_stream_max_bytes(n_ok, _lib.SZX_F32, 128)
-    st = L.szx_compress_static_async(_vp(256), n_ok, _lib.SZX_F32, 1e-3, 128, _vp(512), smax - 16,
-                                     None, None)
+    smax = L.szx_stream_max_bytes(n_ok, dtype, block)
+    st = L.szx_compress_static_async(_vp(256), n_ok, dtype, 1e-3, block, _vp(512), smax - 16, None, None)
     assert st == SZX_ERR_TOO_SMALL
 
 
@@ -74,4 +93,7 @@ def test_static_scratch_matches_existing_entry_point_twice_in_a_row():
         assert rr[1] == SZX_OK and rs == rr
         nbytes = rr[0]
         assert torch.equal(buf[:nbytes], ref[:nbytes])
+        # nothing is written past the stream's own bytes: neither inside the
+        # capacity nor in the guard region after it
+        assert bool((buf[nbytes:smax] == 0xA5).all())
         assert bool((buf[smax:] == 0xA5).all())
