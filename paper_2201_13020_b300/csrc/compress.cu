@@ -34,7 +34,8 @@
 //      bound_check_needed); otherwise a fast test runs and an exact slow path
 //      re-checks a block that fails it, raising reqBits while a value exceeds
 //      e.  Then the identical-leading-byte codes against the previous value
-//      (from each word's top 32 bits) and the lanes' mid-byte counts.  The
+//      (from each word's top 32 bits: the position of the top set bit of the
+//      xor gives the code) and the lanes' mid-byte counts.  The
 //      warp writes its blocks' mu values, publishes its totals and forms its
 //      lanes' plane counts;
 //   2. the warps meet once (an mbarrier); warp reductions of the warps'
@@ -44,7 +45,10 @@
 //      = byte j of every value whose code is <= j, ascending index): a 4x4
 //      byte transpose of four values gives their byte-j word, a 256-entry
 //      table compacts the selected bytes, and shared-memory OR writes place the
-//      run at its bit offset (two funnel shifts);
+//      run at its bit offset (two funnel shifts).  When every lane of a warp
+//      keeps byte 2 of all its values (no code 3), plane 2 goes out as whole
+//      words, each one funnel shift of two consecutive groups, with plain
+//      stores and an OR for the two edge words only;
 //   4. the storer finishes the look-back, writes the tile index entry and
 //      bulk-stores the record (cp.async.bulk) to its offset, writing the
 //      tile's state bits and counts while the store reads; once it has read
@@ -151,6 +155,13 @@ __device__ __forceinline__ float max3_nan(float a, float b, float c) {
 }
 
 __device__ __forceinline__ uint32_t prmt(uint32_t a, uint32_t b, uint32_t s) { return __byte_perm(a, b, s); }
+
+// Position (0..31) of the most significant set bit of a nonzero word.
+__device__ __forceinline__ uint32_t top_bit(uint32_t x) {
+    uint32_t f;
+    asm("bfind.u32 %0, %1;" : "=r"(f) : "r"(x));
+    return f;
+}
 
 // OR a run of up to 4 bytes (little-endian in `run`, zero above its length)
 // into the zero-initialised byte buffer at bit offset pb (a multiple of 8).
@@ -394,10 +405,12 @@ __device__ __forceinline__ void encode_lane(typename Fmt<T>::U (&x)[VPL], uint32
         // a set bit in byte lmax (counted from the top) caps the count at lmax
         const uint32_t cap = 1u << (31 - 8 * lmax);
         if constexpr (FULL) {
-            // c = clz holds the code in its bits 3-4.  Shifting c so that
-            // those bits land on the code's place 2k (k = m mod 16) leaves
-            // c's bits 0-2 just below it; values with the same k mod 4 OR
-            // into one word, where those bits never reach another code, and
+            // f = the position of the top set bit of (xor | cap); the code is
+            // 3 - (f >> 3), the complement of f's bits 3-4.  Shifting f so
+            // that those bits land on the code's place 2k (k = m mod 16)
+            // leaves f's bits 0-2 just below it; values with the same k mod 4
+            // go to one word, 8 bits apart, where those bits never reach
+            // another code (so adding is OR-ing: one shift-add per value), and
             // one mask per word keeps the codes alone
             uint32_t acc[NCODE][4];
 #pragma unroll
@@ -405,15 +418,15 @@ __device__ __forceinline__ void encode_lane(typename Fmt<T>::U (&x)[VPL], uint32
 #pragma unroll
             for (int m = 0; m < VPL; ++m) {
                 const uint32_t top = (uint32_t)(x[m] >> (W - 32));
-                const uint32_t c = (uint32_t)__clz((top ^ prev) | cap);
+                const uint32_t f = top_bit((top ^ prev) | cap);
                 const int p = 2 * (m & 15) - 3;
-                acc[m >> 4][m & 3] |= p >= 0 ? (c << p) : (c >> -p);
+                acc[m >> 4][m & 3] += p >= 0 ? (f << p) : (f >> -p);
                 prev = top;
             }
 #pragma unroll
             for (int i = 0; i < NCODE; ++i)
-                codes[i] = (acc[i][0] & 0x03030303u) | (acc[i][1] & 0x0C0C0C0Cu) | (acc[i][2] & 0x30303030u) |
-                           (acc[i][3] & 0xC0C0C0C0u);
+                codes[i] = ~((acc[i][0] & 0x03030303u) | (acc[i][1] & 0x0C0C0C0Cu) | (acc[i][2] & 0x30303030u) |
+                             (acc[i][3] & 0xC0C0C0C0u));
         } else {
             // each value's code in its own word first, then an OR tree (no
             // serial chain through the code words)
@@ -952,6 +965,34 @@ __global__ void __launch_bounds__(kCThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
                 }
                 or_bytes(words, pb, run);
             };
+            // whole words of a dense plane-2 run: OR for the two edge words
+            // (shared with the writers before and after), a plain store for a
+            // word this lane alone writes
+            auto or_word = [&](uint32_t widx, uint32_t v) {
+                if (SZX_CHECKS && 4 * widx + 4 > L.buf_bytes) {
+                    report_bad(Fd->ws, tile, 4);
+                    return;
+                }
+                atomicOr(words + widx, v);
+            };
+            auto put_word = [&](uint32_t widx, uint32_t v) {
+                if (SZX_CHECKS && 4 * widx + 4 > rec_bytes) {
+                    report_bad(Fd->ws, tile, 5);
+                    return;
+                }
+                words[widx] = v;
+            };
+            // Does every plane-2 run of the warp hold byte 2 of all its lane's
+            // values (no code 3, every value valid)?  Then each word of such a
+            // run is one funnel shift of two consecutive 4-byte groups (see
+            // below).  Decided for the whole warp, so that no lane diverges.
+            bool dense2;
+            {
+                const int s2 = (8 - (req & 7)) & 7;
+                const bool has2 = exists && kind == kNonConst && ((req + s2) >> 3) >= 3;
+                const bool all2 = full_lane && (uint32_t)((cnt >> (2 * FB)) & FM) == (uint32_t)VPL;
+                dense2 = __all_sync(kFull, !has2 || all2);
+            }
             if (exists && kind != kConst) {
                 const uint32_t mbase = nn_t * (b / 4 + 1) + mid_before + mk_blk_excl;
                 if (sub == 0) {
@@ -986,6 +1027,7 @@ __global__ void __launch_bounds__(kCThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
                     uint32_t pos1 = 8 * (mbase + n0 + (uint32_t)((off >> FB) & FM));
                     uint32_t pos2 = 8 * (mbase + n0 + n1 + (uint32_t)((off >> (2 * FB)) & FM));
                     const uint32_t dense0 = mbase + n0 + n1 + n2 + (uint32_t)sub * VPL;
+                    uint32_t w2prev = 0;  // plane 2 on the dense path: the previous group's bytes
 #pragma unroll
                     for (int gq = 0; gq < VPL / 4; ++gq) {
                         // lookup codes: values past the end of a partial block never match
@@ -1022,8 +1064,18 @@ __global__ void __launch_bounds__(kCThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
                         put(pos1, prmt(Wd[1], 0, e.y), e.y >> 16);
                         pos1 += e.y >> 16;
                         if (q >= 3) {
-                            put(pos2, prmt(Wd[2], 0, e.z), e.z >> 16);
-                            pos2 += e.z >> 16;
+                            if (dense2) {
+                                // word gq of the run holds the tail of group
+                                // gq - 1 and the head of group gq; only the
+                                // first word is shared with the writer before
+                                // it (OR), the others are this lane's alone
+                                if (gq == 0) or_word(pos2 >> 5, __funnelshift_l(0u, Wd[2], pos2));
+                                else put_word((pos2 >> 5) + gq, __funnelshift_l(w2prev, Wd[2], pos2));
+                                w2prev = Wd[2];
+                            } else {
+                                put(pos2, prmt(Wd[2], 0, e.z), e.z >> 16);
+                                pos2 += e.z >> 16;
+                            }
                         }
                         if (q >= 4) {
                             const uint32_t sel = full_lane ? (0x3210u | (32u << 16)) : lut[4 * dense8 + 2];
@@ -1034,6 +1086,8 @@ __global__ void __launch_bounds__(kCThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
                             }
                         }
                     }
+                    // the dense run's last word is shared with the writer after it
+                    if (dense2 && q >= 3) or_word((pos2 >> 5) + VPL / 4, __funnelshift_l(w2prev, 0u, pos2));
                 }
             }
             // hand the record to the storer (its bulk store reads it through the
