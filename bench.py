@@ -11,9 +11,14 @@ larger than L2, so no flush is needed between steps.
 
 `value` is whole-job throughput in GB/s of input bytes (Eq. 2-3 of the paper:
 N * b / T) per round trip; compress and decompress rates are reported beside
-it.  The reference arm times the CPU oracle on a bounded slice of the same
-field on the host cores.  With N > 1 (torchrun) every rank codes its own field
-(independent problems: weak scaling, no collective on the data path).
+it.  On one GPU the line also carries the other configurations, each from its
+own timed loop: `config3` (the 384^3 f64 field), `batch96` (96 mixed fields,
+batched against per-field plain launches) and `serve` (Poisson requests,
+continuous batching against a plain queue).  `cpu_baseline` and the reference
+arm time the CPU oracle on the same fixed slice of the field, one process per
+host core on disjoint block ranges (and one thread beside it).  With N > 1
+(torchrun) every rank codes its own field (independent problems: weak
+scaling, no collective on the data path).
 """
 import argparse
 import json
@@ -131,34 +136,106 @@ def cpu_model():
     return "unknown"
 
 
-def time_oracle(x_host, eb, max_seconds=12.0):
-    """The oracle (as it stands, one thread) on a bounded slice of the field."""
+SAMPLE_PLANES = 128  # the oracle's slice of the field: the first 128 z-planes (128 MiB at 512^3)
+
+
+def _oracle_chunk(task):
+    """One oracle process's share: compress and decompress values [lo, hi) of
+    the shared slice `reps` times; returns its seconds (spawned worker)."""
+    shm_name, n, lo, hi, eb, block, reps = task
+    import time as _t
+    from multiprocessing import shared_memory
+
     import numpy as np
 
     import oracle
-    plane = x_host.size // SHAPE_RUN[0]
-    slab = 32 * plane  # 32 z-planes
-    best = None
-    used = 0
-    t_c = t_d = 0.0
-    start = time.perf_counter()
-    for z0 in range(0, x_host.size, slab):
-        part = np.ascontiguousarray(x_host[z0:z0 + slab])
+    shm = shared_memory.SharedMemory(name=shm_name)
+    try:
+        part = np.array(np.ndarray((n,), dtype=np.float32, buffer=shm.buf)[lo:hi])
+    finally:
+        shm.close()
+    oracle.lib()
+    t0 = _t.perf_counter()
+    for _ in range(reps):
+        oracle.decompress(oracle.compress(part, eb, block))
+    return _t.perf_counter() - t0
+
+
+class OracleTimer:
+    """The oracle (as it stands) on a fixed slice of the field: one thread, and
+    one process per host core on disjoint block ranges (blocks are coded
+    independently, Algorithm 1, so the ranges make the same streams as one
+    pass).  Processes are spawned (CUDA is already initialised in this
+    process) and kept for repeated measurements."""
+
+    def __init__(self, x_host, eb):
+        import multiprocessing as mp
+        from concurrent.futures import ProcessPoolExecutor
+        from multiprocessing import shared_memory
+
+        import numpy as np
+        plane = x_host.size // SHAPE_RUN[0]
+        self.planes = min(SAMPLE_PLANES, SHAPE_RUN[0])
+        self.n = self.planes * plane
+        self.eb = eb
+        self.shm = shared_memory.SharedMemory(create=True, size=self.n * 4)
+        np.ndarray((self.n,), dtype=np.float32, buffer=self.shm.buf)[:] = x_host[:self.n]
+        self.x = np.array(x_host[:self.n])
+        self.cores = os.cpu_count() or 1
+        # (an executor, not a Pool: a worker that fails is reported, not respawned)
+        self.pool = ProcessPoolExecutor(self.cores, mp_context=mp.get_context("spawn"))
+        # equal block-aligned ranges, one per process
+        nb = -(-self.n // BLOCK)
+        edges = [min(self.n, (nb * i // self.cores) * BLOCK) for i in range(self.cores + 1)]
+        self.ranges = [(edges[i], edges[i + 1]) for i in range(self.cores) if edges[i + 1] > edges[i]]
+        list(self.pool.map(_oracle_chunk, [(self.shm.name, self.n, lo, hi, eb, BLOCK, 1) for lo, hi in self.ranges]))
+
+    def single_thread(self, reps=1):
+        import oracle
+        t_c = t_d = 0.0
+        for _ in range(reps):
+            t0 = time.perf_counter()
+            s = oracle.compress(self.x, self.eb, BLOCK)
+            t1 = time.perf_counter()
+            oracle.decompress(s)
+            t2 = time.perf_counter()
+            t_c += t1 - t0
+            t_d += t2 - t1
+        b = self.n * 4 * reps
+        return {"value": b / 1e9 / (t_c + t_d), "unit": "GB/s", "cores": 1,
+                "compress_mbs": b / 1e6 / t_c, "decompress_mbs": b / 1e6 / t_d, "seconds": t_c + t_d}
+
+    def all_cores(self, reps=6):
         t0 = time.perf_counter()
-        s = oracle.compress(part, eb, BLOCK)
-        t1 = time.perf_counter()
-        oracle.decompress(s)
-        t2 = time.perf_counter()
-        t_c += t1 - t0
-        t_d += t2 - t1
-        used += part.nbytes
-        if time.perf_counter() - start > max_seconds:
-            break
-    best = used / 1e9 / (t_c + t_d)
-    return {"value": best, "unit": "GB/s", "cores": 1, "kind": "oracle",
-            "sample": f"{used >> 20} MiB of the field ({used // (plane * 4)} z-planes), one thread, "
-                      f"compress {used / 1e6 / t_c:.0f} MB/s, decompress {used / 1e6 / t_d:.0f} MB/s",
-            "cpu": cpu_model(), "seconds": t_c + t_d}
+        busy = list(self.pool.map(_oracle_chunk, [(self.shm.name, self.n, lo, hi, self.eb, BLOCK, reps)
+                                                 for lo, hi in self.ranges]))
+        wall = time.perf_counter() - t0
+        return {"value": self.n * 4 * reps / 1e9 / wall, "unit": "GB/s", "cores": len(self.ranges),
+                "seconds": wall, "cpu_seconds": sum(busy)}
+
+    def sample(self):
+        return (f"the first {self.planes} z-planes of the field ({self.n * 4 >> 20} MiB, "
+                f"{-(-self.n // BLOCK)} blocks): compress + decompress")
+
+    def close(self):
+        self.pool.shutdown()
+        self.shm.close()
+        self.shm.unlink()
+
+
+def time_oracle(x_host, eb):
+    """cpu_baseline: the oracle on the fixed slice, on every host core
+    (`value`) and on one thread (`single_thread`)."""
+    ot = OracleTimer(x_host, eb)
+    try:
+        one = ot.single_thread(reps=2)
+        runs = [ot.all_cores() for _ in range(3)]
+        allc = sorted(runs, key=lambda r: r["value"])[1]  # the median of three
+    finally:
+        ot.close()
+    return {"value": allc["value"], "unit": "GB/s", "cores": allc["cores"], "kind": "oracle",
+            "sample": ot.sample() + f", {allc['cores']} processes on disjoint block ranges",
+            "cpu": cpu_model(), "single_thread": one, "all_cores": allc}
 
 
 def max_over_ranks(ms, world, device):
@@ -209,45 +286,47 @@ def run_reference(args, world, rank):
     eb = inputs.rel_to_abs(x, REL)
     xh = x.cpu().numpy()
     del x
-    per_step = []
-    samples = []
-    # each step times the oracle on a bounded slice (about 2 s of CPU work), so
-    # that the whole run ends within a few minutes at the default step counts
-    step_s = min(args.ref_seconds, 2.0)
-    for i in range(args.warmup + args.steps):
-        r = time_oracle(xh, eb, max_seconds=step_s)
-        if i >= args.warmup:
-            per_step.append(r)
-            samples.append(r["value"])
+    # each step: the oracle on the same fixed slice as the cpu_baseline leg,
+    # one process per host core on disjoint block ranges
+    ot = OracleTimer(xh, eb)
+    try:
+        samples, secs = [], []
+        for i in range(args.warmup + args.steps):
+            r = ot.all_cores()
+            if i >= args.warmup:
+                samples.append(r["value"])
+                secs.append(r["seconds"])
+        one = ot.single_thread(reps=1)
+    finally:
+        ot.close()
     v = statistics.median(samples)
-    last = per_step[-1]
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "GB/s", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * last["seconds"],
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.median(secs),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic", "config": config_block(world),
-            "cpu_baseline": {"value": v, "unit": "GB/s", "cores": 1, "kind": "oracle", "sample": last["sample"]},
+            "cpu_baseline": {"value": v, "unit": "GB/s", "cores": ot.cores, "kind": "oracle",
+                             "sample": ot.sample() + f", {len(ot.ranges)} processes on disjoint block ranges",
+                             "cpu": cpu_model(), "single_thread": one},
             "e2e": {"value": v, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
 
 
-def run_batch96(args, world, rank, local):
-    """Many fields: 96 fields, sizes log-uniform 256 KiB - 512 MiB, 70% f32 / 30%
-    f64, 1-D / 2-D / 3-D generators, REL from {1e-2, 1e-3, 1e-4}, block 128.
+def measure_batch96(args, rank, count=96):
+    """Many fields: `count` fields, sizes log-uniform 256 KiB - 512 MiB, 70% f32 /
+    30% f64, 1-D / 2-D / 3-D generators, REL from {1e-2, 1e-3, 1e-4}, block 128.
     Times the round trip three ways on the same data: per-field plain launches
     (two per field and direction), the batched plan (one persistent launch per
     (dtype, block) group, CTAs per SM autotuned), and the batched plan replayed
-    from a CUDA graph; checks that batched and plain streams are identical."""
+    from a CUDA graph; checks that batched and plain streams are identical.
+    Returns the measurement as a dict."""
     import numpy as np
     import torch
 
     import paper_2201_13020_b300 as szx
     from paper_2201_13020_b300 import inputs
-    torch.cuda.set_device(local)
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    fields = inputs.mixed_fields(96, 256 << 10, 512 << 20, seed=4 + rank, device="cuda")
+    t_start = time.perf_counter()
+    fields = inputs.mixed_fields(count, 256 << 10, 512 << 20, seed=4 + rank, device="cuda")
     xs = [f[0] for f in fields]
     ebs = [inputs.rel_to_abs(x, rel) for x, rel, _ in fields]
     k = len(xs)
@@ -312,17 +391,18 @@ def run_batch96(args, world, rank, local):
             fc()
             fd()
         torch.cuda.synchronize()
-        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
-        tc = td = 0.0
-        for _ in range(args.steps):
-            ev[0].record(stream)
+        # steps queued back to back (the host's launch time is part of each
+        # arm's cost), events around each direction
+        ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+        for e in ev:
+            e[0].record(stream)
             fc()
-            ev[1].record(stream)
+            e[1].record(stream)
             fd()
-            ev[2].record(stream)
-            torch.cuda.synchronize()
-            tc += ev[0].elapsed_time(ev[1])
-            td += ev[1].elapsed_time(ev[2])
+            e[2].record(stream)
+        torch.cuda.synchronize()
+        tc = sum(e[0].elapsed_time(e[1]) for e in ev)
+        td = sum(e[1].elapsed_time(e[2]) for e in ev)
         times[name] = (tc / args.steps, td / args.steps)
     torch.cuda.synchronize()
     if int(st.abs().sum()) or int(d_st.abs().sum()):
@@ -340,49 +420,65 @@ def run_batch96(args, world, rank, local):
     best = out["batched_graph"]
     peak, peak_kind = peaks()
     alg = in_bytes + stream_bytes
+    res = {"workload": f"batch{k}_mixed_f32f64_256KiB-512MiB_block128", "fields": k, "input_bytes": in_bytes,
+           "stream_bytes": stream_bytes, "cr": in_bytes / stream_bytes,
+           "f64_fields": int(sum(c == szx.SZX_F64 for c in code)), "arms": out,
+           "speedup_vs_plain": {"batched": out["batched"]["round_trip_gbs"] / out["plain"]["round_trip_gbs"],
+                                "batched_graph": best["round_trip_gbs"] / out["plain"]["round_trip_gbs"]},
+           "hbm_frac_algorithmic": {"compress": alg / (best["compress_ms"] * 1e-3) / 1e9 / peak,
+                                    "decompress": alg / (best["decompress_ms"] * 1e-3) / 1e9 / peak,
+                                    "peak": f"hbm_gbs {peak} of {peak_kind}"},
+           "autotune_ctas_per_sm": {"compress": tuned_c, "decompress": tuned_d},
+           "steps": args.steps, "gpu_launches": args.steps * (len(tuned_c) + len(tuned_d)),
+           "wall_s": time.perf_counter() - t_start}
+    del graphs, batch, dbatch, b_out, d_ys, p_out, ys, xs, fields
+    torch.cuda.empty_cache()
+    return res
+
+
+def run_batch96(args, world, rank, local):
+    import torch
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    r = measure_batch96(args, rank)
+    best = r["arms"]["batched_graph"]
     if rank == 0:
         line = {"metric": METRIC, "value": best["round_trip_gbs"] * world, "unit": "GB/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": best["compress_ms"] + best["decompress_ms"], "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-                "config": {"workload": "batch96_mixed_f32f64_256KiB-512MiB_block128", "fields": k,
-                           "input_bytes": in_bytes, "stream_bytes": stream_bytes, "cr": in_bytes / stream_bytes,
-                           "f64_fields": sum(c == szx.SZX_F64 for c in code),
+                "config": {"workload": r["workload"], "fields": r["fields"], "input_bytes": r["input_bytes"],
+                           "stream_bytes": r["stream_bytes"], "cr": r["cr"], "f64_fields": r["f64_fields"],
                            "l2": "no flush: the batch (8 GB) exceeds the 126 MB L2",
                            "parallelism": f"replicas{world}"},
-                "arms": out,
-                "speedup_vs_plain": {"batched": out["plain"]["round_trip_gbs"] and
-                                     out["batched"]["round_trip_gbs"] / out["plain"]["round_trip_gbs"],
-                                     "batched_graph": best["round_trip_gbs"] / out["plain"]["round_trip_gbs"]},
-                "hbm_frac_algorithmic": {"compress": alg / (best["compress_ms"] * 1e-3) / 1e9 / peak,
-                                         "decompress": alg / (best["decompress_ms"] * 1e-3) / 1e9 / peak,
-                                         "peak": f"hbm_gbs {peak} of {peak_kind}"},
-                "autotune_ctas_per_sm": {"compress": tuned_c, "decompress": tuned_d},
-                "gpu_launches": args.steps * (len(tuned_c) + len(tuned_d)),
-                "gpu": torch.cuda.get_device_name(local)}
+                "arms": r["arms"], "speedup_vs_plain": r["speedup_vs_plain"],
+                "hbm_frac_algorithmic": r["hbm_frac_algorithmic"], "autotune_ctas_per_sm": r["autotune_ctas_per_sm"],
+                "gpu_launches": r["gpu_launches"], "gpu": torch.cuda.get_device_name(local)}
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
     return 0
 
 
-def run_serve(args, world, rank, local):
+def measure_serve(args, rank, count, rate):
     """Serving: Poisson arrivals, 60% compress / 40% decompress of earlier
     resident streams, sizes log-uniform 64 KiB - 256 MiB; half the compress
     requests are complex f64 state vectors (unit-norm Gaussian, interleaved
     re/im, 2^k amplitudes with 2^k * 16 bytes nearest the drawn size), half
     f32 fields (the 1-D recipe); REL from {1e-2, 1e-3, 1e-4}; streams resident
     in a 120 GB pool.  Two arms on the same requests: one slot (a plain queue)
-    and continuous batching (8 slots, overlapped on the device)."""
+    and continuous batching (8 slots, overlapped on the device).  Returns the
+    measurement as a dict."""
     import math
 
     import numpy as np
     import torch
 
     from paper_2201_13020_b300 import inputs, serve
-    torch.cuda.set_device(local)
+    t_start = time.perf_counter()
     rng = np.random.default_rng(77 + rank)
-    count, rate = args.requests, args.rate
     specs = []
     t = 0.0
     comp = []
@@ -419,16 +515,20 @@ def run_serve(args, world, rank, local):
         return out
 
     arms = {}
+    # one long-lived 120 GB pool for both arms (a pool allocated or freed just
+    # before a run slows the host's launches for a while); each arm first runs
+    # the whole request list once untimed, then gives its streams back
+    pool = torch.empty((120 << 30) + 256, dtype=torch.uint8, device="cuda")
+    pool = pool[(-pool.data_ptr()) % 256:][:120 << 30]
     for name, slots in (("queue_1slot", 1), ("continuous_8slots", 8)):
-        server = serve.Server(120 << 30, slots=slots)
-        # warm-up on the same server (module load, kernel set-up), then give
-        # its resident streams back
-        warm = [r for r in requests()[:12] if r.kind == "compress"]
+        server = serve.Server(slots=slots, pool=pool)
+        warm = requests()
         server.run(warm)
         for r in warm:
-            server.release(r.offset, r.nbytes)
+            if r.kind == "compress":
+                server.release(r.offset, r.nbytes)
         reqs = requests()
-        with ClockSampler(local) as clocks:
+        with ClockSampler(torch.cuda.current_device()) as clocks:
             span = server.run(reqs)
         torch.cuda.synchronize()
         bad = [i for i, r in enumerate(reqs) if r.status != 0]
@@ -446,19 +546,36 @@ def run_serve(args, world, rank, local):
                       "gbs": total / span / 1e9, "makespan_s": span, "input_bytes": total,
                       "max_in_flight": server.max_in_flight, "clocks": clocks.summary(),
                       "resident_stream_bytes": int(sum(r.nbytes for r in reqs if r.kind == "compress"))}
+        for r in reqs:
+            if r.kind == "compress":
+                server.release(r.offset, r.nbytes)
         server.close()
         del server, reqs
-        torch.cuda.empty_cache()
+    del pool, data
+    torch.cuda.empty_cache()
     best = arms["continuous_8slots"]
+    return {"workload": f"serve_poisson{rate:g}_req{count}_64KiB-256MiB_60c40d", "requests": count,
+            "compress": sum(k == "compress" for k, _, _ in specs),
+            "decompress": sum(k == "decompress" for k, _, _ in specs), "pool_bytes": 120 << 30,
+            "arrival_rate_per_s": rate, "block": BLOCK, "gbs": best["gbs"], "p50_ms": best["p50_ms"],
+            "p99_ms": best["p99_ms"], "speedup_vs_queue": best["gbs"] / arms["queue_1slot"]["gbs"],
+            "arms": arms, "wall_s": time.perf_counter() - t_start}
+
+
+def run_serve(args, world, rank, local):
+    import torch
+    torch.cuda.set_device(local)
+    r = measure_serve(args, rank, args.requests, args.rate)
+    best = r["arms"]["continuous_8slots"]
     if rank == 0:
         line = {"metric": METRIC, "value": best["gbs"], "unit": "GB/s", "n_gpus": world, "steps": 1, "warmup": 1,
                 "ms_per_step": best["makespan_s"] * 1e3, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f64(state vectors)+f32", "data": "synthetic",
-                "config": {"workload": f"serve_poisson{rate:g}_req{count}_64KiB-256MiB_60c40d",
-                           "requests": count, "compress": sum(k == "compress" for k, _, _ in specs),
-                           "decompress": sum(k == "decompress" for k, _, _ in specs), "pool_bytes": 120 << 30,
-                           "arrival_rate_per_s": rate, "block": BLOCK, "parallelism": f"replicas{world}"},
-                "p50_ms": best["p50_ms"], "p99_ms": best["p99_ms"], "arms": arms,
+                "config": {"workload": r["workload"], "requests": r["requests"], "compress": r["compress"],
+                           "decompress": r["decompress"], "pool_bytes": r["pool_bytes"],
+                           "arrival_rate_per_s": r["arrival_rate_per_s"], "block": BLOCK,
+                           "parallelism": f"replicas{world}"},
+                "p50_ms": best["p50_ms"], "p99_ms": best["p99_ms"], "arms": r["arms"],
                 "gpu": torch.cuda.get_device_name(local)}
         print(json.dumps(line), flush=True)
     return 0
@@ -588,15 +705,15 @@ def run_blocksweep(args, world, rank, local):
     return 0
 
 
-def run_grf384f64(args, world, rank, local):
-    """The f64 field: 384^3, spectrum |k|^-11/3 plus 1e-6 white noise; REL
-    1e-4 and 1e-6, block 128 and 256: compress and decompress rates, CR and
-    the HBM fraction of the algorithmic bytes."""
+def measure_f64(args, rank, rels=(1e-4, 1e-6), blocks=(128, 256)):
+    """The f64 field: 384^3, spectrum |k|^-11/3 plus 1e-6 white noise; per REL
+    and block: compress and decompress medians, rates, CR and the HBM fraction
+    of the algorithmic bytes (input + stream).  Returns a dict of rows."""
     import torch
 
     import paper_2201_13020_b300 as szx
     from paper_2201_13020_b300 import inputs
-    torch.cuda.set_device(local)
+    t_start = time.perf_counter()
     g = inputs.grf_3d((384, 384, 384), -11.0 / 3.0, seed=3 + rank, device="cuda", dtype=torch.float64)
     gen = torch.Generator(device="cuda")
     gen.manual_seed(33 + rank)
@@ -607,45 +724,59 @@ def run_grf384f64(args, world, rank, local):
     stream = torch.cuda.current_stream()
     peak, peak_kind = peaks()
     rows = {}
-    for rel in (1e-4, 1e-6):
+    for rel in rels:
         eb = inputs.rel_to_abs(x, rel)
-        for b in (128, 256):
+        for b in blocks:
             out = torch.empty(szx.compress_bound(n, szx.SZX_F64, b), dtype=torch.uint8, device="cuda")
             res = torch.zeros(2, dtype=torch.int64, device="cuda")
             nbytes = szx.compress(x, eb, b, out=out).numel()
             h = szx.header(out[:nbytes])
             y = torch.empty_like(x)
             st = torch.zeros(1, dtype=torch.int32, device="cuda")
-            ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
-            tc, td = [], []
-            for i in range(args.warmup + args.steps):
-                ev[0].record(stream)
+            for _ in range(args.warmup):
                 szx.compress_async(x, eb, b, out, res)
-                ev[1].record(stream)
                 szx.decompress_async(out[:nbytes], h, y, st)
-                ev[2].record(stream)
-                torch.cuda.synchronize()
-                if i >= args.warmup:
-                    tc.append(ev[0].elapsed_time(ev[1]))
-                    td.append(ev[1].elapsed_time(ev[2]))
+            torch.cuda.synchronize()
+            # the steps queued back to back, events around each kernel
+            ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+            queue_ahead(stream, args.steps)
+            for e in ev:
+                e[0].record(stream)
+                szx.compress_async(x, eb, b, out, res)
+                e[1].record(stream)
+                szx.decompress_async(out[:nbytes], h, y, st)
+                e[2].record(stream)
+            torch.cuda.synchronize()
+            tc = [e[0].elapsed_time(e[1]) for e in ev]
+            td = [e[1].elapsed_time(e[2]) for e in ev]
             if int(st.item()) or int(res[1].item()) or float((x - y).abs().max()) > eb:
                 raise RuntimeError(f"rel {rel} block {b}: failed")
             mc, md = statistics.median(tc), statistics.median(td)
             alg = in_bytes + nbytes
-            rows[f"rel{rel:g}_b{b}"] = {"compress_gbs": in_bytes / (mc * 1e-3) / 1e9,
+            rows[f"rel{rel:g}_b{b}"] = {"compress_us": 1e3 * mc, "decompress_us": 1e3 * md,
+                                         "compress_gbs": in_bytes / (mc * 1e-3) / 1e9,
                                          "decompress_gbs": in_bytes / (md * 1e-3) / 1e9,
                                          "cr": in_bytes / nbytes,
                                          "hbm_frac_compress": alg / (mc * 1e-3) / 1e9 / peak,
                                          "hbm_frac_decompress": alg / (md * 1e-3) / 1e9 / peak,
                                          "escalated_blocks": h.escalated, "raw_blocks": h.raw}
             del out, y
+    del x
+    torch.cuda.empty_cache()
+    return {"workload": "grf384_f64_k-11/3_noise1e-6", "peak": f"hbm_gbs {peak} of {peak_kind}",
+            "steps": args.steps, "rows": rows, "wall_s": time.perf_counter() - t_start}
+
+
+def run_grf384f64(args, world, rank, local):
+    import torch
+    torch.cuda.set_device(local)
+    r = measure_f64(args, rank)
     if rank == 0:
-        line = {"metric": METRIC, "value": rows["rel0.0001_b128"]["compress_gbs"], "unit": "GB/s",
+        line = {"metric": METRIC, "value": r["rows"]["rel0.0001_b128"]["compress_gbs"], "unit": "GB/s",
                 "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                "config": {"workload": "grf384_f64_k-11/3_noise1e-6", "peak": f"hbm_gbs {peak} of {peak_kind}",
-                           "parallelism": f"replicas{world}"},
-                "rows": rows, "gpu": torch.cuda.get_device_name(local)}
+                "config": {"workload": r["workload"], "peak": r["peak"], "parallelism": f"replicas{world}"},
+                "rows": r["rows"], "gpu": torch.cuda.get_device_name(local)}
         print(json.dumps(line), flush=True)
     return 0
 
@@ -664,8 +795,11 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--ref-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="default workload: skip the config3 / batch96 / serve sub-objects")
+    ap.add_argument("--batch-fields", type=int, default=96, help="fields of the batch96 sub-object")
+    ap.add_argument("--serve-requests", type=int, default=600, help="requests of the serve sub-object")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--size", type=int, default=512, help="cube edge (default 512; smaller only for captures)")
     ap.add_argument("--workload", default="grf512", choices=["grf512", "batch96", "serve", "dump", "blocksweep", "grf384f64"],
@@ -786,6 +920,7 @@ def main():
     # while step s's values are copied out (the link is full duplex); the
     # device never runs ahead of the data it needs.
     e2e = e2e_serial = None
+    xd = yd = outs = None
     if args.e2e_steps > 0:
         xh = torch.empty(n, dtype=torch.float32, pin_memory=True)
         xh.copy_(x)
@@ -866,10 +1001,24 @@ def main():
         if not (torch.equal(yh[0], y.cpu()) and torch.equal(yh[1], y.cpu())):
             raise RuntimeError("e2e decode differs from the device-resident decode")
 
+    # the other configurations, measured in the same run on one GPU: the f64
+    # field, the batched form against per-field plain launches, and the
+    # serving loop against a plain queue (their own timed loops; not part of
+    # `value`)
+    extras = {}
+    if world == 1 and not args.no_extras:
+        xh = x.cpu().numpy()
+        del out, y, xd, yd, outs
+        torch.cuda.empty_cache()
+        extras["config3"] = measure_f64(args, rank, rels=(1e-4, 1e-6), blocks=(128,))
+        extras["batch96"] = measure_batch96(args, rank, count=args.batch_fields)
+        extras["serve"] = measure_serve(args, rank, count=args.serve_requests, rate=30000.0)
+    else:
+        xh = x.cpu().numpy() if rank == 0 else None
+
     cpu_base = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu_base = time_oracle(x.cpu().numpy(), eb, max_seconds=args.ref_seconds)
-        cpu_base.pop("seconds", None)
+        cpu_base = time_oracle(xh, eb)
 
     if rank == 0:
         line = {
@@ -892,6 +1041,7 @@ def main():
                        "blocks": -(-n // BLOCK)},
             "gpu": torch.cuda.get_device_name(local),
         }
+        line.update(extras)
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()

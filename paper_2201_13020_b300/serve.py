@@ -61,13 +61,25 @@ class Request:
 
 
 class Server:
-    def __init__(self, pool_bytes, slots=8, device="cuda"):
+    """pool_bytes: size of the device pool the server allocates; or pool: a
+    CUDA uint8 tensor to use as the pool instead (256-byte aligned), so that
+    several servers in turn can share one long-lived allocation.  Allocating
+    and freeing pools of many GB between runs is slow on the host for a while
+    afterwards, which would show up as slower launches."""
+
+    def __init__(self, pool_bytes=None, slots=8, device="cuda", pool=None):
         import torch
         L = _bind()
         self._t = torch
-        self.pool = torch.empty(pool_bytes + 256, dtype=torch.uint8, device=device)
-        off = (-self.pool.data_ptr()) % 256
-        self.pool = self.pool[off:off + pool_bytes]
+        if pool is not None:
+            if pool.dtype != torch.uint8 or not pool.is_cuda or pool.data_ptr() % 256:
+                raise ValueError("pool must be a 256-byte aligned CUDA uint8 tensor")
+            self.pool = pool
+            pool_bytes = pool.numel()
+        else:
+            self.pool = torch.empty(pool_bytes + 256, dtype=torch.uint8, device=device)
+            off = (-self.pool.data_ptr()) % 256
+            self.pool = self.pool[off:off + pool_bytes]
         self._srv = ctypes.c_void_p(0)
         _check(L.szx_server_create(ctypes.c_void_p(self.pool.data_ptr()), pool_bytes, slots,
                                    ctypes.byref(self._srv)), "szx_server_create")
