@@ -343,6 +343,9 @@ def measure_batch96(args, rank, count=96):
         for i in range(k):
             szx.compress_async(xs[i], ebs[i], BLOCK, p_out[i], p_res[2 * i:2 * i + 2])
 
+    # the plan in its default shape (8 consumer warps, as many CTAs as fit)
+    # and the plan the autotuner shaped
+    fixed, f_out, f_res = szx.batch_compress(xs, ebs, BLOCK)
     batch, b_out, b_res = szx.batch_compress(xs, ebs, BLOCK)
     tuned_c = batch.autotune()
 
@@ -367,6 +370,7 @@ def measure_batch96(args, rank, count=96):
         for i in range(k):
             szx.decompress_async(bufs[i], headers[i], ys[i], st[i:i + 1])
 
+    dfixed, _, _ = szx.batch_decompress(bufs, headers)
     dbatch, d_ys, d_st = szx.batch_decompress(bufs, headers)
     tuned_d = dbatch.autotune()
 
@@ -382,6 +386,7 @@ def measure_batch96(args, rank, count=96):
 
     arms = {
         "plain": (plain_compress, plain_decompress),
+        "batched_fixed": (fixed.run, dfixed.run),
         "batched": (batch.run, dbatch.run),
         "batched_graph": (graphs[0].replay, graphs[1].replay),
     }
@@ -420,15 +425,84 @@ def measure_batch96(args, rank, count=96):
     best = out["batched_graph"]
     peak, peak_kind = peaks()
     alg = in_bytes + stream_bytes
+    for i in range(k):
+        n_ = int(f_res[2 * i].item())
+        if n_ != int(nb[i, 0]) or not torch.equal(f_out[i][:n_], b_out[i][:n_]):
+            raise RuntimeError(f"field {i}: the fixed and the tuned plan wrote different streams")
+    del fixed, dfixed, f_out
+
+    # every shape of every compression group, timed alone (what the tuner
+    # compared): consumer warps per CTA x CTAs per SM
+    shapes = []
+    for gi, g in enumerate(tuned_c):
+        one_ms = {}
+        for nw in (8, 4):
+            for ctas in (2, 1):
+                try:
+                    batch.set_group(gi, ctas, nw)
+                except szx.SzxError:
+                    continue
+                e = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+                batch.run()
+                e[0].record(stream)
+                for _ in range(5):
+                    batch.run()
+                e[1].record(stream)
+                torch.cuda.synchronize()
+                one_ms[f"{nw}warps_{ctas}ctas"] = e[0].elapsed_time(e[1]) / 5
+        batch.set_group(gi, g["ctas_per_sm"], g["warps_per_cta"])
+        shapes.append({"dtype": g["dtype"], "block": g["block"], "whole_plan_ms": one_ms})
+
+    # block 0: the tuner also chooses b (64, 128 or 256) per dtype group; the
+    # streams change with b, so they are checked by decoding them
+    auto, a_out, a_res = szx.batch_compress(xs, ebs, 0)
+    tuned_a = auto.autotune()
+    ga = torch.cuda.CUDAGraph()
+    auto.run(stream=side)
+    torch.cuda.synchronize()
+    with torch.cuda.graph(ga, stream=side):
+        auto.run(stream=side)
+    for _ in range(args.warmup):
+        ga.replay()
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    ev[0].record(stream)
+    for _ in range(args.steps):
+        ga.replay()
+    ev[1].record(stream)
+    torch.cuda.synchronize()
+    a_ms = ev[0].elapsed_time(ev[1]) / args.steps
+    ar = a_res.cpu().numpy().reshape(-1, 2)
+    if (ar[:, 1] != 0).any():
+        raise RuntimeError("block-0 batch: a stream's status is not OK")
+    a_bufs = [a_out[i][:int(ar[i, 0])] for i in range(k)]
+    adec, a_ys, a_st = szx.batch_decompress(a_bufs, [szx.header(b_) for b_ in a_bufs])
+    adec.autotune()
+    adec.run()
+    torch.cuda.synchronize()
+    if int(a_st.abs().sum()):
+        raise RuntimeError("block-0 batch: decompression status not OK")
+    for i in range(k):
+        if float((a_ys[i].double() - xs[i].double()).abs().max()) > ebs[i]:
+            raise RuntimeError(f"block-0 batch: field {i} exceeds its bound")
+    a_bytes = int(ar[:, 0].sum())
+    auto_block = {"compress_gbs": in_bytes / (a_ms * 1e-3) / 1e9, "compress_ms": a_ms,
+                  "stream_bytes": a_bytes, "cr": in_bytes / a_bytes, "groups": tuned_a,
+                  "vs_block128_cr": (in_bytes / a_bytes) / (in_bytes / stream_bytes)}
+    del auto, adec, a_out, a_ys, ga
     res = {"workload": f"batch{k}_mixed_f32f64_256KiB-512MiB_block128", "fields": k, "input_bytes": in_bytes,
            "stream_bytes": stream_bytes, "cr": in_bytes / stream_bytes,
            "f64_fields": int(sum(c == szx.SZX_F64 for c in code)), "arms": out,
-           "speedup_vs_plain": {"batched": out["batched"]["round_trip_gbs"] / out["plain"]["round_trip_gbs"],
+           "speedup_vs_plain": {"batched_fixed": out["batched_fixed"]["round_trip_gbs"] / out["plain"]["round_trip_gbs"],
+                                "batched": out["batched"]["round_trip_gbs"] / out["plain"]["round_trip_gbs"],
                                 "batched_graph": best["round_trip_gbs"] / out["plain"]["round_trip_gbs"]},
+           "tuned_vs_fixed": out["batched"]["round_trip_gbs"] / out["batched_fixed"]["round_trip_gbs"],
+           "compress_shapes": shapes,
+           "block0": auto_block,
            "hbm_frac_algorithmic": {"compress": alg / (best["compress_ms"] * 1e-3) / 1e9 / peak,
                                     "decompress": alg / (best["decompress_ms"] * 1e-3) / 1e9 / peak,
                                     "peak": f"hbm_gbs {peak} of {peak_kind}"},
-           "autotune_ctas_per_sm": {"compress": tuned_c, "decompress": tuned_d},
+           "autotune": {"compress": tuned_c, "decompress": tuned_d},
            "steps": args.steps, "gpu_launches": args.steps * (len(tuned_c) + len(tuned_d)),
            "wall_s": time.perf_counter() - t_start}
     del graphs, batch, dbatch, b_out, d_ys, p_out, ys, xs, fields
@@ -454,7 +528,8 @@ def run_batch96(args, world, rank, local):
                            "l2": "no flush: the batch (8 GB) exceeds the 126 MB L2",
                            "parallelism": f"replicas{world}"},
                 "arms": r["arms"], "speedup_vs_plain": r["speedup_vs_plain"],
-                "hbm_frac_algorithmic": r["hbm_frac_algorithmic"], "autotune_ctas_per_sm": r["autotune_ctas_per_sm"],
+                "hbm_frac_algorithmic": r["hbm_frac_algorithmic"], "tuned_vs_fixed": r["tuned_vs_fixed"],
+                "block0": r["block0"], "autotune": r["autotune"], "compress_shapes": r["compress_shapes"],
                 "gpu_launches": r["gpu_launches"], "gpu": torch.cuda.get_device_name(local)}
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -237,13 +237,16 @@ szx_status szx_decompress_async(const void *d_in, size_t in_bytes,
  * overlap in time (they share the workspace).
  * ------------------------------------------------------------------------ */
 
-/* One field to compress: as the arguments of szx_compress_async. */
+/* One field to compress: as the arguments of szx_compress_async, except that
+ * block may be 0: szx_batch_autotune then chooses b among 64, 128 and 256 for
+ * the plan's block-0 fields of each dtype together (128 until it runs), and
+ * out_capacity must hold the largest stream of the three. */
 typedef struct {
     const void *d_in;    /* n values, 16-byte aligned */
     size_t n;
     szx_dtype dtype;
     double eb;           /* absolute bound, finite and > 0 */
-    uint32_t block;      /* power of two in [32, 1024] */
+    uint32_t block;      /* power of two in [32, 1024], or 0 (see above) */
     void *d_out;         /* the field's stream, 16-byte aligned */
     size_t out_capacity; /* >= szx_stream_max_bytes(n, dtype, block) */
 } szx_field;
@@ -288,16 +291,50 @@ szx_status szx_batch_upload(szx_batch_plan *plan, void *d_ws, size_t ws_bytes,
 szx_status szx_batch_run(const szx_batch_plan *plan, void *d_ws,
                          szx_stream_t stream);
 
-/* Choose, per group, how many CTAs of the kernel share an SM (1 or 2, where
- * two fit) by timing runs of that group on `stream`; the choice is kept in the
- * plan.  Runs the plan's own work, so it overwrites the outputs (with the same
- * bytes).  Synchronous. */
+/* Autotuner.  Per group, time runs of that group alone on `stream` in every
+ * shape the kernels have and keep the fastest in the plan:
+ *   - consumer (decoding) warps per CTA: 8, or 4 where a block still covers
+ *     whole lanes (f32 with b >= 64, f64 with b <= 512); with 4 warps each lane
+ *     holds twice the values and each warp twice the blocks (threads per CTA
+ *     = 32 * warps + 64; a tile is always 32 KiB of values, 64 KiB for f64
+ *     with b = 1024, so the stream does not change);
+ *   - CTAs per SM: 2 or 1;
+ *   - for a compression group of block-0 fields, the block length b among 64,
+ *     128 and 256 (this changes the stream): among the lengths whose fastest
+ *     time is within 2% of the fastest overall, the one whose streams are the
+ *     smallest (the best compression ratio, Sec. V-A.2's trade-off).
+ * Runs the plan's own work, so it overwrites the outputs (with the bytes of
+ * the chosen shape), and re-uploads the tables if b changes.  Synchronous.
+ * The paper has no counterpart (it fixes b = 128 by its Fig. 7 study). */
 szx_status szx_batch_autotune(szx_batch_plan *plan, void *d_ws,
                               szx_stream_t stream);
 
 /* Number of groups; writes up to `capacity` CTAs-per-SM choices (0 = as many
  * as fit) into ctas_per_sm. */
 int szx_batch_groups(const szx_batch_plan *plan, int *ctas_per_sm, int capacity);
+
+/* A group's shape. */
+typedef struct {
+    szx_dtype dtype;
+    uint32_t block;            /* b (the tuner's choice for block-0 fields) */
+    int auto_block;            /* 1: its fields were given block 0 */
+    uint32_t fields;
+    uint64_t tiles;
+    int ctas_per_sm;           /* 0 = as many as fit */
+    int warps_per_cta;         /* consumer (decoding) warps: 8 or 4 */
+    uint32_t threads_per_cta;  /* 32 * warps_per_cta + 64 */
+    uint32_t values_per_lane;  /* 32 or 64 (f32), 16 or 32 (f64) */
+    uint32_t blocks_per_warp;  /* 32 * values_per_lane / b */
+    float tuned_ms;            /* the tuner's time for the group, 0 if not tuned */
+} szx_batch_group;
+
+/* The shape of group `group` (0 .. szx_batch_groups - 1).  Errors:
+ * SZX_ERR_INVALID. */
+szx_status szx_batch_group_info(const szx_batch_plan *plan, int group, szx_batch_group *info);
+
+/* Set a group's shape by hand (ctas_per_sm 0, 1 or 2; warps_per_cta 8 or 4
+ * where the kernels have it).  Errors: SZX_ERR_INVALID. */
+szx_status szx_batch_set_group(szx_batch_plan *plan, int group, int ctas_per_sm, int warps_per_cta);
 
 void szx_batch_destroy(szx_batch_plan *plan);
 

@@ -9,7 +9,7 @@ and streams; the codec itself runs in the library's sm_103a CUDA kernels.
 """
 import ctypes
 
-from ._lib import SZX_F32, SZX_F64, STATUS, SzxField, SzxHeader, SzxStreamField, lib
+from ._lib import SZX_F32, SZX_F64, STATUS, SzxBatchGroup, SzxField, SzxHeader, SzxStreamField, lib
 
 __all__ = ["compress", "decompress", "compress_async", "decompress_async", "decompress_range", "compress_bound",
            "stream_max_bytes", "header", "Batch", "batch_compress", "batch_decompress", "SzxError", "SZX_F32",
@@ -163,14 +163,27 @@ class Batch:
                "szx_batch_run")
 
     def autotune(self, stream=None):
+        """Time every shape of every group (see szx_batch_autotune) and keep
+        the fastest; returns groups()."""
         _check(lib().szx_batch_autotune(self._plan, ctypes.c_void_p(self.ws.data_ptr()), _stream_handle(stream)),
                "szx_batch_autotune")
         return self.groups()
 
     def groups(self):
-        buf = (ctypes.c_int * 64)()
-        n = lib().szx_batch_groups(self._plan, buf, 64)
-        return [buf[i] for i in range(min(n, 64))]
+        """Each group's shape: dtype, block, fields, ctas_per_sm, warps_per_cta,
+        threads_per_cta, values_per_lane, blocks_per_warp, tuned_ms."""
+        L = lib()
+        n = L.szx_batch_groups(self._plan, None, 0)
+        out = []
+        for i in range(n):
+            g = SzxBatchGroup()
+            _check(L.szx_batch_group_info(self._plan, i, ctypes.byref(g)), "szx_batch_group_info")
+            out.append({f: getattr(g, f) for f, _ in SzxBatchGroup._fields_})
+        return out
+
+    def set_group(self, group, ctas_per_sm, warps_per_cta):
+        """Set a group's shape by hand (ctas_per_sm 0, 1 or 2; warps 8 or 4)."""
+        _check(lib().szx_batch_set_group(self._plan, group, ctas_per_sm, warps_per_cta), "szx_batch_set_group")
 
     def close(self):
         if self._plan:
@@ -199,9 +212,14 @@ def _upload(plan, device, results, stream):
     return ws
 
 
+# block lengths the batch autotuner tries for fields given block 0
+AUTO_BLOCKS = (64, 128, 256)
+
+
 def batch_compress(xs, ebs, blocks=128, outs=None, stream=None):
-    """Plan and upload the compression of CUDA tensors xs (one bound each;
-    a block of 0 is chosen per field by metrics.choose_block).
+    """Plan and upload the compression of CUDA tensors xs (one bound each).
+    A block of 0 lets Batch.autotune() choose b among 64, 128 and 256 for the
+    block-0 fields of each dtype (128 until it runs).
 
     Returns (batch, outs, results): outs are uint8 buffers of
     stream_max_bytes each; after batch.run() and a synchronisation, field i's
@@ -211,13 +229,14 @@ def batch_compress(xs, ebs, blocks=128, outs=None, stream=None):
     k = len(xs)
     if isinstance(blocks, int):
         blocks = [blocks] * k
-    if any(b == 0 for b in blocks):
-        # block=0: each such field's block length from a compressed sample
-        from .metrics import choose_block
-        blocks = [choose_block(x, eb)[0] if b == 0 else b for x, eb, b in zip(xs, ebs, blocks)]
+
+    def cap(x, bk):
+        if bk:
+            return stream_max_bytes(x.numel(), _dtype_code(x), bk)
+        return max(stream_max_bytes(x.numel(), _dtype_code(x), b) for b in AUTO_BLOCKS)
+
     if outs is None:
-        outs = [torch.empty(stream_max_bytes(x.numel(), _dtype_code(x), bk), dtype=torch.uint8, device=x.device)
-                for x, bk in zip(xs, blocks)]
+        outs = [torch.empty(cap(x, bk), dtype=torch.uint8, device=x.device) for x, bk in zip(xs, blocks)]
     arr = (SzxField * k)()
     for i, (x, eb, bk, o) in enumerate(zip(xs, ebs, blocks, outs)):
         if not x.is_cuda or not x.is_contiguous():

@@ -26,6 +26,14 @@ class SzxField(ctypes.Structure):
                 ("block", ctypes.c_uint32), ("d_out", ctypes.c_void_p), ("out_capacity", ctypes.c_size_t)]
 
 
+class SzxBatchGroup(ctypes.Structure):
+    _fields_ = [("dtype", ctypes.c_int), ("block", ctypes.c_uint32), ("auto_block", ctypes.c_int),
+                ("fields", ctypes.c_uint32), ("tiles", ctypes.c_uint64), ("ctas_per_sm", ctypes.c_int),
+                ("warps_per_cta", ctypes.c_int), ("threads_per_cta", ctypes.c_uint32),
+                ("values_per_lane", ctypes.c_uint32), ("blocks_per_warp", ctypes.c_uint32),
+                ("tuned_ms", ctypes.c_float)]
+
+
 class SzxStreamField(ctypes.Structure):
     _fields_ = [("d_in", ctypes.c_void_p), ("in_bytes", ctypes.c_size_t), ("header", SzxHeader),
                 ("d_out", ctypes.c_void_p), ("out_capacity", ctypes.c_size_t), ("d_status", ctypes.c_void_p)]
@@ -78,6 +86,10 @@ def lib():
     L.szx_batch_autotune.argtypes = [vp, vp, vp]
     L.szx_batch_groups.restype = i
     L.szx_batch_groups.argtypes = [vp, ctypes.POINTER(i), i]
+    L.szx_batch_group_info.restype = i
+    L.szx_batch_group_info.argtypes = [vp, i, ctypes.POINTER(SzxBatchGroup)]
+    L.szx_batch_set_group.restype = i
+    L.szx_batch_set_group.argtypes = [vp, i, i, i]
     L.szx_batch_destroy.restype = None
     L.szx_batch_destroy.argtypes = [vp]
     L.szx_status_string.restype = ctypes.c_char_p
@@ -91,5 +103,6 @@ def lib():
 EXPORTED = ["szx_compress_bound", "szx_stream_max_bytes", "szx_compress", "szx_compress_async",
             "szx_compress_static_async", "szx_decompress_range_async", "szx_batch_compress_plan", "szx_batch_decompress_plan",
             "szx_batch_workspace_bytes", "szx_batch_upload", "szx_batch_run", "szx_batch_autotune", "szx_batch_groups",
+            "szx_batch_group_info", "szx_batch_set_group",
             "szx_batch_destroy", "szx_server_create", "szx_server_pool", "szx_server_free_bytes", "szx_server_run",
             "szx_server_release", "szx_server_destroy", "szx_header_read", "szx_decompress", "szx_decompress_async", "szx_status_string", "szx_version"]

@@ -12,15 +12,20 @@
 //   aligned; compression only).
 // Running a plan is one cudaMemsetAsync (counters and workspaces) plus one
 // kernel launch per group, so it can be captured in a CUDA graph once the
-// tables are uploaded.  The autotuner picks, per group, how many CTAs share an
-// SM (the kernels fit one or two) by timing both on the plan's own data; the
-// streams it writes are the same either way.
+// tables are uploaded.  The autotuner times each group alone on the plan's own
+// data in every shape the kernels have -- consumer warps per CTA (8, or 4 with
+// twice the values per lane and blocks per warp) times CTAs per SM (2 or 1) --
+// and keeps the fastest; the stream is the same in every shape.  For a group
+// of fields given block 0 it also tries the block lengths 64, 128 and 256
+// (which do change the stream), and among those within 2% of the fastest time
+// keeps the one that writes the fewest bytes.
 #include "szx.h"
 #include "szx_device.cuh"
 #include "szx_host.h"
 #include "szx_launch.h"
 
 #include <algorithm>
+#include <iterator>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -36,7 +41,16 @@ struct Group {
     uint32_t first, count;  // slice of the (grouped) table
     uint64_t tiles;
     int ctas_per_sm;  // 0: as many as fit
+    int nw;           // consumer (decoding) warps per CTA: 8 or 4
+    bool auto_block;  // its fields asked for block 0: the tuner picks b
+    float tuned_ms;   // the tuner's best time for the group (0: not tuned)
 };
+
+// Block lengths the tuner tries for block-0 fields (and the one used until it
+// runs).  For each of them a tile holds the same number of values (32 KiB),
+// so a field's tile count and workspace do not depend on the choice.
+constexpr uint32_t kAutoBlocks[3] = {64, 128, 256};
+constexpr uint32_t kAutoDefault = 128;
 
 }  // namespace
 
@@ -49,6 +63,7 @@ struct szx_batch_plan {
     std::vector<uint64_t> ws_off;  // compression: per table slot, its workspace offset
     uint64_t table_bytes = 0, counters_off = 0, zero_off = 0, total_bytes = 0;
     void *uploaded_ws = nullptr;  // the workspace the tables were written to
+    uint64_t *uploaded_results = nullptr;  // and the results array given then
 };
 
 namespace {
@@ -66,8 +81,12 @@ szx_status make_groups(szx_batch_plan *p, const std::vector<std::pair<int, uint3
         g.first = s;
         g.tiles = 0;
         g.ctas_per_sm = 0;
+        g.nw = 8;
+        g.tuned_ms = 0.0f;
         while (s < n && keys[p->order[s]] == std::make_pair(g.dtype, g.block)) g.tiles += tiles[p->order[s++]];
         g.count = s - g.first;
+        g.auto_block = g.block == 0;
+        if (g.auto_block) g.block = kAutoDefault;
         if (g.tiles >= (1ull << 32)) return SZX_ERR_INVALID;  // tickets are 32-bit
         p->groups.push_back(g);
     }
@@ -89,7 +108,20 @@ szx_status szx_batch_compress_plan(const szx_field *fields, int count, szx_batch
     std::vector<uint64_t> tiles;
     for (int i = 0; i < count; ++i) {
         const szx_field &f = fields[i];
-        const size_t smax = szx_stream_max_bytes(f.n, f.dtype, f.block);
+        // block 0: the largest stream over the tuner's candidates
+        size_t smax = 0;
+        if (f.block == 0) {
+            for (uint32_t b : kAutoBlocks) {
+                const size_t m = szx_stream_max_bytes(f.n, f.dtype, b);
+                if (!m) {  // an invalid field
+                    smax = 0;
+                    break;
+                }
+                smax = m > smax ? m : smax;
+            }
+        } else {
+            smax = szx_stream_max_bytes(f.n, f.dtype, f.block);
+        }
         if (!f.d_in || !f.d_out || !smax || !aligned16(f.d_in) || !aligned16(f.d_out) || !(f.eb > 0.0) ||
             !std::isfinite(f.eb)) {
             delete p;
@@ -101,7 +133,7 @@ szx_status szx_batch_compress_plan(const szx_field *fields, int count, szx_batch
         }
         p->fields.push_back(f);
         keys.emplace_back((int)f.dtype, f.block);
-        tiles.push_back(make_geometry(f.n, f.block, f.dtype == SZX_F32 ? 4 : 8).ntiles);
+        tiles.push_back(make_geometry(f.n, f.block ? f.block : kAutoDefault, f.dtype == SZX_F32 ? 4 : 8).ntiles);
     }
     szx_status st = make_groups(p, keys, tiles);
     if (st != SZX_OK) {
@@ -182,7 +214,7 @@ szx_status szx_batch_upload(szx_batch_plan *p, void *d_ws, size_t ws_bytes, uint
             if (p->compress) {
                 const szx_field &f = p->fields[i];
                 CField *c = reinterpret_cast<CField *>(host.data()) + s;
-                fill_compress_field(c, f.d_in, f.n, (int)f.dtype, bound_bits(f.eb, f.dtype), f.block, f.d_out,
+                fill_compress_field(c, f.d_in, f.n, (int)f.dtype, bound_bits(f.eb, f.dtype), g.block, f.d_out,
                                     base + p->ws_off[s], d_results ? d_results + 2 * i : nullptr, tile0);
                 tile0 += c->g.ntiles;
             } else {
@@ -201,6 +233,7 @@ szx_status szx_batch_upload(szx_batch_plan *p, void *d_ws, size_t ws_bytes, uint
     // the staging buffer goes out of scope: make sure the copy has read it
     if (cudaStreamSynchronize(s) != cudaSuccess) return SZX_ERR_CUDA;
     p->uploaded_ws = d_ws;
+    p->uploaded_results = d_results;
     return SZX_OK;
 }
 
@@ -223,11 +256,11 @@ szx_status szx_batch_run(const szx_batch_plan *p, void *d_ws, szx_stream_t strea
         if (p->compress) {
             const CField *tbl = reinterpret_cast<const CField *>(base) + g.first;
             uint32_t *ctr = reinterpret_cast<uint32_t *>(base + p->counters_off + 16 * gi);
-            e = launch_compress_batch(tbl, g.count, g.tiles, ctr, g.dtype, g.block, g.ctas_per_sm, s);
+            e = launch_compress_batch(tbl, g.count, g.tiles, ctr, g.dtype, g.block, g.ctas_per_sm, g.nw, s);
         } else {
             const DField *tbl = reinterpret_cast<const DField *>(base) + g.first;
             uint32_t *ticket = reinterpret_cast<uint32_t *>(base + p->counters_off + 16 * gi);
-            e = launch_decompress_batch(tbl, g.count, g.tiles, ticket, g.dtype, g.block, g.ctas_per_sm, s);
+            e = launch_decompress_batch(tbl, g.count, g.tiles, ticket, g.dtype, g.block, g.ctas_per_sm, g.nw, s);
         }
         if (e != cudaSuccess) return SZX_ERR_CUDA;
     }
@@ -244,36 +277,127 @@ szx_status szx_batch_autotune(szx_batch_plan *p, void *d_ws, szx_stream_t stream
         return SZX_ERR_CUDA;
     }
     szx_status st = SZX_OK;
+    // the fastest of three runs of group gi alone in its current shape (ms)
+    auto time_group = [&](size_t gi, float *ms) {
+        szx_batch_plan one = *p;
+        one.groups.assign(1, p->groups[gi]);
+        float t_min = 0.0f;
+        for (int r = 0; r < 3; ++r) {
+            if (cudaEventRecord(e0, s) != cudaSuccess) return SZX_ERR_CUDA;
+            szx_status rs = szx_batch_run(&one, d_ws, stream);
+            if (rs != SZX_OK) return rs;
+            if (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) return SZX_ERR_CUDA;
+            float t = 0.0f;
+            cudaEventElapsedTime(&t, e0, e1);
+            if (r == 0 || t < t_min) t_min = t;
+        }
+        *ms = t_min;
+        return SZX_OK;
+    };
+    // the group's stream bytes after a run (each stream's header holds its size)
+    auto group_bytes = [&](size_t gi, uint64_t *bytes) {
+        const Group &g = p->groups[gi];
+        uint64_t sum = 0;
+        for (uint32_t t = g.first; t < g.first + g.count; ++t) {
+            uint64_t total = 0;
+            const uint8_t *h = static_cast<const uint8_t *>(p->fields[p->order[t]].d_out);
+            if (cudaMemcpyAsync(&total, h + 56, 8, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+                cudaStreamSynchronize(s) != cudaSuccess)
+                return SZX_ERR_CUDA;
+            sum += total;
+        }
+        *bytes = sum;
+        return SZX_OK;
+    };
     for (size_t gi = 0; gi < p->groups.size() && st == SZX_OK; ++gi) {
-        float best = 0.0f;
-        int best_c = 0;
-        for (int c : {2, 1}) {
-            // the group alone, c CTAs per SM; the fastest of three runs
-            szx_batch_plan one = *p;
-            one.groups.assign(1, p->groups[gi]);
-            one.groups[0].ctas_per_sm = c;
-            float t_min = 0.0f;
-            for (int r = 0; r < 3; ++r) {
-                if (cudaEventRecord(e0, s) != cudaSuccess) st = SZX_ERR_CUDA;
-                if (st == SZX_OK) st = szx_batch_run(&one, d_ws, stream);
-                if (st == SZX_OK && cudaEventRecord(e1, s) != cudaSuccess) st = SZX_ERR_CUDA;
-                if (st == SZX_OK && cudaEventSynchronize(e1) != cudaSuccess) st = SZX_ERR_CUDA;
+        Group &g = p->groups[gi];
+        std::vector<uint32_t> blocks;
+        if (p->compress && g.auto_block) blocks.assign(std::begin(kAutoBlocks), std::end(kAutoBlocks));
+        else blocks.assign(1, g.block);
+        struct Choice {
+            uint32_t block;
+            int nw, ctas;
+            float ms;
+            uint64_t bytes;
+        };
+        std::vector<Choice> best;  // per block length, its fastest shape
+        for (uint32_t b : blocks) {
+            if (b != g.block) {
+                g.block = b;  // the tables name the block length: write them again
+                st = szx_batch_upload(p, d_ws, p->total_bytes, p->uploaded_results, stream);
                 if (st != SZX_OK) break;
-                float ms = 0.0f;
-                cudaEventElapsedTime(&ms, e0, e1);
-                if (r == 0 || ms < t_min) t_min = ms;
+            }
+            Choice c{b, 8, 0, 0.0f, 0};
+            for (int nw : {8, 4}) {
+                if (!kernel_shape_ok(g.dtype, b, nw)) continue;
+                for (int ctas : {2, 1}) {
+                    g.nw = nw;
+                    g.ctas_per_sm = ctas;
+                    float ms = 0.0f;
+                    st = time_group(gi, &ms);
+                    if (st != SZX_OK) break;
+                    if (c.ms == 0.0f || ms < c.ms) {
+                        c.nw = nw;
+                        c.ctas = ctas;
+                        c.ms = ms;
+                    }
+                }
+                if (st != SZX_OK) break;
             }
             if (st != SZX_OK) break;
-            if (best_c == 0 || t_min < best) {
-                best = t_min;
-                best_c = c;
-            }
+            if (p->compress && blocks.size() > 1) st = group_bytes(gi, &c.bytes);
+            if (st != SZX_OK) break;
+            best.push_back(c);
         }
-        if (st == SZX_OK) p->groups[gi].ctas_per_sm = best_c;
+        if (st != SZX_OK) break;
+        // the fastest shape; among block lengths within 2% of the fastest
+        // time, the one that writes the fewest bytes (the best ratio)
+        float t_best = best[0].ms;
+        for (const Choice &c : best) t_best = c.ms < t_best ? c.ms : t_best;
+        const Choice *pick = nullptr;
+        for (const Choice &c : best) {
+            if (c.ms > 1.02f * t_best) continue;
+            if (!pick || c.bytes < pick->bytes || (c.bytes == pick->bytes && c.ms < pick->ms)) pick = &c;
+        }
+        g.nw = pick->nw;
+        g.ctas_per_sm = pick->ctas;
+        g.tuned_ms = pick->ms;
+        if (pick->block != g.block) {
+            g.block = pick->block;
+            st = szx_batch_upload(p, d_ws, p->total_bytes, p->uploaded_results, stream);
+        }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     return st;
+}
+
+szx_status szx_batch_group_info(const szx_batch_plan *p, int group, szx_batch_group *info) {
+    if (!p || !info || group < 0 || group >= (int)p->groups.size()) return SZX_ERR_INVALID;
+    const Group &g = p->groups[group];
+    const uint32_t w = g.dtype == SZX_F32 ? 4u : 8u;
+    const uint32_t G = tile_blocks(g.block, w);
+    info->dtype = (szx_dtype)g.dtype;
+    info->block = g.block;
+    info->auto_block = g.auto_block ? 1 : 0;
+    info->fields = g.count;
+    info->tiles = g.tiles;
+    info->ctas_per_sm = g.ctas_per_sm;
+    info->warps_per_cta = g.nw;
+    info->threads_per_cta = (uint32_t)g.nw * 32u + 64u;
+    info->values_per_lane = G * g.block / (32u * (uint32_t)g.nw);
+    info->blocks_per_warp = 32u * info->values_per_lane >= g.block ? 32u * info->values_per_lane / g.block : 0u;
+    info->tuned_ms = g.tuned_ms;
+    return SZX_OK;
+}
+
+szx_status szx_batch_set_group(szx_batch_plan *p, int group, int ctas_per_sm, int warps_per_cta) {
+    if (!p || group < 0 || group >= (int)p->groups.size() || ctas_per_sm < 0 || ctas_per_sm > 2) return SZX_ERR_INVALID;
+    Group &g = p->groups[group];
+    if (!kernel_shape_ok(g.dtype, g.block, warps_per_cta)) return SZX_ERR_INVALID;
+    g.ctas_per_sm = ctas_per_sm;
+    g.nw = warps_per_cta;
+    return SZX_OK;
 }
 
 int szx_batch_groups(const szx_batch_plan *p, int *ctas_per_sm, int capacity) {

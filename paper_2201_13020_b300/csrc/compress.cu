@@ -458,12 +458,11 @@ __device__ __forceinline__ void encode_lane(typename Fmt<T>::U (&x)[VPL], uint32
 // Shared-memory layout of the compress kernel: kStages tile buffers (each
 // later reused for its tile's record), per-stage block metadata, the table.
 constexpr int kStages = 3;
-constexpr int kConsumerWarps = 8;
-constexpr int kConsumers = kConsumerWarps * 32;
-constexpr int kProducerWarp = kConsumerWarps;
-constexpr int kStorerWarp = kConsumerWarps + 1;
-constexpr int kCThreads = kConsumers + 64;
-static_assert(kConsumers == kThreads, "a tile is laid out over 8 warps");
+// A CTA has NW consumer warps (8 or 4), then the producer and the storer
+// warp.  The tile (G blocks, a fixed number of 128-byte rows) is laid out over
+// the consumers' lanes, each lane taking RPL = rows / (32 NW) consecutive rows:
+// with fewer warps a lane holds more values and a warp more blocks.
+__host__ __device__ constexpr int compress_threads(int nw) { return nw * 32 + 64; }
 
 struct CSmem {
     uint32_t buf_stride, buf_bytes;  // tile buffer st at st * buf_stride (1024-aligned)
@@ -471,7 +470,7 @@ struct CSmem {
     uint32_t m_kind, m_w;  // offsets inside a metadata block: block kinds, per-warp totals
     uint32_t lut, total;
 };
-__host__ __device__ inline CSmem compress_smem(uint32_t G, uint32_t b, uint32_t w) {
+__host__ __device__ inline CSmem compress_smem(uint32_t G, uint32_t b, uint32_t w, uint32_t nw) {
     CSmem s;
     const uint32_t tile = G * b * w;
     const uint32_t rec = record_max_bytes(G, b, w);
@@ -486,7 +485,7 @@ __host__ __device__ inline CSmem compress_smem(uint32_t G, uint32_t b, uint32_t 
         return at;
     };
     s.m_kind = mtake(G);
-    s.m_w = mtake(16 * kConsumerWarps);
+    s.m_w = mtake(16 * nw);
     s.meta_stride = (m + 15) & ~15u;
     s.meta0 = (kStages - 1) * s.buf_stride + s.buf_bytes;  // after the last buffer (16-aligned)
     s.lut = s.meta0 + kStages * s.meta_stride;
@@ -504,13 +503,18 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
 
 // ---------------------------------------------------------------------------
 
-template <typename T, int LPB, int VPL, bool BATCH>
-__global__ void __launch_bounds__(kCThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
+template <typename T, int LPB, int VPL, int NW, bool BATCH>
+__global__ void __launch_bounds__(compress_threads(NW),
+                                  (tile_blocks(LPB * VPL, sizeof(T)) * LPB * VPL * sizeof(T) > 32768) ? 1 : 2)
     compress_kernel(const __grid_constant__ CField one, const __grid_constant__ CompressLaunch lc) {
     using F = Fmt<T>;
     using U = typename F::U;
     constexpr int w = F::w;
     constexpr int W = F::W;
+    constexpr int kConsumerWarps = NW;
+    constexpr int kCThreads = compress_threads(NW);
+    constexpr int kProducerWarp = NW;
+    constexpr int kStorerWarp = NW + 1;
     constexpr int BPW = 32 / LPB;       // blocks per warp
     constexpr int RPL = VPL * w / 128;  // 128-byte rows per lane
     constexpr int NCODE = (2 * VPL + 31) / 32;
@@ -527,7 +531,10 @@ __global__ void __launch_bounds__(kCThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
     uint8_t *smem = smem_raw + ((1024u - (smem_addr(smem_raw) & 1023u)) & 1023u);
     constexpr uint32_t b = (uint32_t)(LPB * VPL);
     constexpr uint32_t G = tile_blocks(b, (uint32_t)w);
-    const CSmem L = compress_smem(G, b, w);
+    constexpr uint32_t TILE_ROWS = G * b * w / 128;  // 256, or 512 for 64 KiB tiles
+    constexpr uint32_t TILE_BOXES = TILE_ROWS / 256;  // tensor copies of 256 rows
+    static_assert((uint32_t)(NW * 32 * RPL) == TILE_ROWS, "the tile is laid out over the consumers' lanes");
+    const CSmem L = compress_smem(G, b, w, NW);
     uint32_t *lut = reinterpret_cast<uint32_t *>(smem + L.lut);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
@@ -586,11 +593,11 @@ __global__ void __launch_bounds__(kCThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
             const uint32_t tile = more ? (uint32_t)(t - F->tile0) : 0xFFFFFFFFu;
             st_field[st] = f;
             st_tile[st] = tile;
-            const uint64_t row0 = (uint64_t)tile * 256 * RPL;
+            const uint64_t row0 = (uint64_t)tile * TILE_ROWS;
             if (more && F->use_tma && row0 < F->rows_full) {
-                mbar_arrive_expect_tx(&full[st], 256u * 128u * RPL);
+                mbar_arrive_expect_tx(&full[st], TILE_ROWS * 128u);
 #pragma unroll
-                for (int i = 0; i < RPL; ++i) {
+                for (int i = 0; i < (int)TILE_BOXES; ++i) {
                     const uint32_t dst = smem_addr(smem + st * L.buf_stride + i * 32768);
                     const int y = (int)(row0 + 256 * i);
                     asm volatile(
@@ -808,7 +815,7 @@ __global__ void __launch_bounds__(kCThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
         uint4 *sm_w = reinterpret_cast<uint4 *>(meta + L.m_w);  // per warp: nn << 20 | mid, raw, escalated
         const uint64_t k0 = (uint64_t)tile * G;
         const uint32_t Gt = (uint32_t)min_u64(G, g.nb - k0);
-        const uint64_t row0 = (uint64_t)tile * 256 * RPL;
+        const uint64_t row0 = (uint64_t)tile * TILE_ROWS;
         const uint64_t rows_full = Fd->rows_full;
         const bool tma = Fd->use_tma && row0 < rows_full;
 
@@ -865,7 +872,7 @@ __global__ void __launch_bounds__(kCThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
                     for (int c = 0; c < 8; ++c) *reinterpret_cast<uint4 *>(buf + (rowi << 7) + ((c ^ (rowi & 7u)) << 4)) = z;
                 }
                 if (warp == kConsumerWarps - 1)
-                    for (uint32_t i = 32768u * RPL + 16u * lane; i < L.buf_bytes; i += 16u * 32u)
+                    for (uint32_t i = TILE_ROWS * 128u + 16u * lane; i < L.buf_bytes; i += 16u * 32u)
                         *reinterpret_cast<uint4 *>(buf + i) = z;
             }
             uint32_t codes[NCODE];
@@ -1013,7 +1020,9 @@ __global__ void __launch_bounds__(kCThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
                     // lead codes: this lane's values are bytes [sub*VPL/4, (sub+1)*VPL/4)
                     if (SZX_CHECKS && (rank + 1) * (b / 4) > nn_t * (b / 4)) report_bad(Fd->ws, tile, 6);
                     uint8_t *lead = buf + rank * (b / 4) + sub * (VPL / 4);
-                    if constexpr (NCODE == 2) {
+                    if constexpr (NCODE == 4) {
+                        *reinterpret_cast<uint4 *>(lead) = make_uint4(codes[0], codes[1], codes[2], codes[3]);
+                    } else if constexpr (NCODE == 2) {
                         *reinterpret_cast<uint2 *>(lead) = make_uint2(codes[0], codes[1]);
                     } else {
                         *reinterpret_cast<uint32_t *>(lead) = codes[0];
@@ -1107,41 +1116,63 @@ __global__ void __launch_bounds__(kCThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
 
 namespace {
 
-template <typename T, int LPB, int VPL>
+template <typename T, int LPB, int VPL, int NW>
 cudaError_t launch_t(const CField &one, const CompressLaunch &lc, int ctas_per_sm, cudaStream_t stream) {
     constexpr uint32_t b = (uint32_t)(LPB * VPL), w = (uint32_t)Fmt<T>::w;
-    const CSmem L = compress_smem(tile_blocks(b, w), b, w);
-    auto kern = lc.fields ? compress_kernel<T, LPB, VPL, true> : compress_kernel<T, LPB, VPL, false>;
+    const CSmem L = compress_smem(tile_blocks(b, w), b, w, NW);
+    auto kern = lc.fields ? compress_kernel<T, LPB, VPL, NW, true> : compress_kernel<T, LPB, VPL, NW, false>;
     // per device and kernel: the shared-memory attribute and the occupancy,
     // set up on first use (a launch then only reads them)
     int per_sm = 0, sms = 0;
-    cudaError_t err = launch_setup(reinterpret_cast<const void *>(kern), L.total, kCThreads, &per_sm, &sms);
+    cudaError_t err =
+        launch_setup(reinterpret_cast<const void *>(kern), L.total, compress_threads(NW), &per_sm, &sms);
     if (err != cudaSuccess) return err;
     if (ctas_per_sm > 0 && ctas_per_sm < per_sm) per_sm = ctas_per_sm;
     const uint64_t grid = min_u64(lc.total_tiles, (uint64_t)sms * per_sm);
-    kern<<<(unsigned)grid, kCThreads, L.total, stream>>>(one, lc);
+    kern<<<(unsigned)grid, compress_threads(NW), L.total, stream>>>(one, lc);
     return cudaGetLastError();
 }
 
-cudaError_t dispatch(int dtype, uint32_t block, const CField &one, const CompressLaunch &lc, int ctas_per_sm,
-                     cudaStream_t stream) {
-    if (dtype == 0) {
+// The kernel instance for (dtype, block, consumer warps): 8 warps with 32
+// values per lane (16 for f64), or 4 warps with twice as many values per lane
+// where a block still covers whole lanes (not for f32 with b = 32, nor f64
+// with b = 1024, whose 64 values per lane would not fit the registers).
+cudaError_t dispatch(int dtype, uint32_t block, int nw, const CField &one, const CompressLaunch &lc,
+                     int ctas_per_sm, cudaStream_t stream) {
+    if (nw == 0) nw = 8;
+    if (dtype == 0 && nw == 8) {
         switch (block) {
-            case 32: return launch_t<float, 1, 32>(one, lc, ctas_per_sm, stream);
-            case 64: return launch_t<float, 2, 32>(one, lc, ctas_per_sm, stream);
-            case 128: return launch_t<float, 4, 32>(one, lc, ctas_per_sm, stream);
-            case 256: return launch_t<float, 8, 32>(one, lc, ctas_per_sm, stream);
-            case 512: return launch_t<float, 16, 32>(one, lc, ctas_per_sm, stream);
-            case 1024: return launch_t<float, 32, 32>(one, lc, ctas_per_sm, stream);
+            case 32: return launch_t<float, 1, 32, 8>(one, lc, ctas_per_sm, stream);
+            case 64: return launch_t<float, 2, 32, 8>(one, lc, ctas_per_sm, stream);
+            case 128: return launch_t<float, 4, 32, 8>(one, lc, ctas_per_sm, stream);
+            case 256: return launch_t<float, 8, 32, 8>(one, lc, ctas_per_sm, stream);
+            case 512: return launch_t<float, 16, 32, 8>(one, lc, ctas_per_sm, stream);
+            case 1024: return launch_t<float, 32, 32, 8>(one, lc, ctas_per_sm, stream);
         }
-    } else {
+    } else if (dtype == 0 && nw == 4) {
         switch (block) {
-            case 32: return launch_t<double, 2, 16>(one, lc, ctas_per_sm, stream);
-            case 64: return launch_t<double, 4, 16>(one, lc, ctas_per_sm, stream);
-            case 128: return launch_t<double, 8, 16>(one, lc, ctas_per_sm, stream);
-            case 256: return launch_t<double, 16, 16>(one, lc, ctas_per_sm, stream);
-            case 512: return launch_t<double, 32, 16>(one, lc, ctas_per_sm, stream);
-            case 1024: return launch_t<double, 32, 32>(one, lc, ctas_per_sm, stream);
+            case 64: return launch_t<float, 1, 64, 4>(one, lc, ctas_per_sm, stream);
+            case 128: return launch_t<float, 2, 64, 4>(one, lc, ctas_per_sm, stream);
+            case 256: return launch_t<float, 4, 64, 4>(one, lc, ctas_per_sm, stream);
+            case 512: return launch_t<float, 8, 64, 4>(one, lc, ctas_per_sm, stream);
+            case 1024: return launch_t<float, 16, 64, 4>(one, lc, ctas_per_sm, stream);
+        }
+    } else if (dtype == 1 && nw == 8) {
+        switch (block) {
+            case 32: return launch_t<double, 2, 16, 8>(one, lc, ctas_per_sm, stream);
+            case 64: return launch_t<double, 4, 16, 8>(one, lc, ctas_per_sm, stream);
+            case 128: return launch_t<double, 8, 16, 8>(one, lc, ctas_per_sm, stream);
+            case 256: return launch_t<double, 16, 16, 8>(one, lc, ctas_per_sm, stream);
+            case 512: return launch_t<double, 32, 16, 8>(one, lc, ctas_per_sm, stream);
+            case 1024: return launch_t<double, 32, 32, 8>(one, lc, ctas_per_sm, stream);
+        }
+    } else if (dtype == 1 && nw == 4) {
+        switch (block) {
+            case 32: return launch_t<double, 1, 32, 4>(one, lc, ctas_per_sm, stream);
+            case 64: return launch_t<double, 2, 32, 4>(one, lc, ctas_per_sm, stream);
+            case 128: return launch_t<double, 4, 32, 4>(one, lc, ctas_per_sm, stream);
+            case 256: return launch_t<double, 8, 32, 4>(one, lc, ctas_per_sm, stream);
+            case 512: return launch_t<double, 16, 32, 4>(one, lc, ctas_per_sm, stream);
         }
     }
     return cudaErrorInvalidValue;
@@ -1189,11 +1220,11 @@ cudaError_t launch_compress_ws(const void *in, uint64_t n, int dtype, uint64_t e
     lc.copy_ns = 1000ull * wait_limit_from_env("SZX_COPY_US", 1000000u);
     cudaError_t err = cudaMemsetAsync(ws, 0, workspace_bytes(one.g.ntiles), stream);
     if (err != cudaSuccess) return err;
-    return dispatch(dtype, block, one, lc, 0, stream);
+    return dispatch(dtype, block, 8, one, lc, 0, stream);
 }
 
 cudaError_t launch_compress_batch(const void *d_fields, uint32_t nfields, uint64_t total_tiles, uint32_t *d_counters,
-                                  int dtype, uint32_t block, int ctas_per_sm, cudaStream_t stream) {
+                                  int dtype, uint32_t block, int ctas_per_sm, int nw, cudaStream_t stream) {
     CField one;
     std::memset(&one, 0, sizeof(one));
     CompressLaunch lc;
@@ -1205,7 +1236,7 @@ cudaError_t launch_compress_batch(const void *d_fields, uint32_t nfields, uint64
     lc.err = d_counters + 2;
     lc.lookback_ns = 1000ull * wait_limit_from_env("SZX_LOOKBACK_US", 1000000u);
     lc.copy_ns = 1000ull * wait_limit_from_env("SZX_COPY_US", 1000000u);
-    return dispatch(dtype, block, one, lc, ctas_per_sm, stream);
+    return dispatch(dtype, block, nw, one, lc, ctas_per_sm, stream);
 }
 
 // ---------------------------------------------------------------------------

@@ -139,11 +139,10 @@ __device__ __forceinline__ uint32_t load_run(const uint8_t *buf, uint32_t p) {
 }
 
 constexpr int kDSlots = 6;  // tiles in flight per CTA, at most (their records share one ring)
-constexpr int kDConsumers = kThreads;             // 8 decoding warps
-constexpr int kDWarps = kDConsumers / 32;
-constexpr int kDProducerWarp = kDWarps;           // warp 8
-constexpr int kDIndexerWarp = kDWarps + 1;        // warp 9
-constexpr int kDThreads = kDConsumers + 64;
+// A CTA has NDW decoding warps (8 or 4), then the producer and the indexing
+// warp; each decoding lane rebuilds RPL = rows / (32 NDW) consecutive 128-byte
+// rows of the tile.
+__host__ __device__ constexpr int decompress_threads(int ndw) { return ndw * 32 + 64; }
 constexpr uint32_t kBitsWindow = 64;  // 16-byte-aligned window holding a tile's state bits
 
 // Shared memory: one output buffer per decoding warp (its 32 * RPL rows of
@@ -161,14 +160,14 @@ struct DSmem {
     uint32_t ring, ring_bytes;  // the record ring (128-aligned, a multiple of 1024 bytes)
     uint32_t total;
 };
-__host__ __device__ inline DSmem decompress_smem(uint32_t G, uint32_t b, uint32_t w) {
+__host__ __device__ inline DSmem decompress_smem(uint32_t G, uint32_t b, uint32_t w, uint32_t ndw) {
     DSmem s;
     const uint32_t tile = G * b * w;  // 32 KiB, or 64 KiB for f64 with b = 1024
     // (the per-CTA limit includes the static barriers and slot words)
     const uint32_t budget = tile > 32768u ? 226u * 1024u : 112u * 1024u;
     constexpr uint32_t kRealign = 1024;  // slack to realign the dynamic base to 1024
     s.wbuf = 0;
-    s.wbuf_bytes = tile / kDWarps;  // 4 KiB per 128-byte row per lane
+    s.wbuf_bytes = tile / ndw;  // 4 KiB per 128-byte row per lane
     s.lut = s.wbuf + tile;
     s.slots = s.lut + (uint32_t)sizeof(DecodeLut);
     s.mu = 0;
@@ -189,9 +188,14 @@ __device__ __forceinline__ void dmbar_arrive(uint64_t *bar) {
 }
 
 // Persistent decoder: tile = blockIdx.x + it * gridDim.x for it = 0, 1, ...
-template <typename T, int LPB, int VPL, bool BATCH>
-__global__ void __launch_bounds__(kDThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
+template <typename T, int LPB, int VPL, int NDW, bool BATCH>
+__global__ void __launch_bounds__(decompress_threads(NDW),
+                                  (tile_blocks(LPB * VPL, sizeof(T)) * LPB * VPL * sizeof(T) > 32768) ? 1 : 2)
     decompress_kernel(const __grid_constant__ DField one, const __grid_constant__ DecompressLaunch lc) {
+    constexpr int kDWarps = NDW;
+    constexpr int kDThreads = decompress_threads(NDW);
+    constexpr int kDProducerWarp = NDW;
+    constexpr int kDIndexerWarp = NDW + 1;
     using F = Fmt<T>;
     using U = typename F::U;
     constexpr int w = F::w;
@@ -202,7 +206,11 @@ __global__ void __launch_bounds__(kDThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
     constexpr int RPL = VPL * w / 128;  // 128-byte rows per lane
     constexpr uint32_t b = (uint32_t)(LPB * VPL);
     constexpr uint32_t G = tile_blocks(b, (uint32_t)w);
-    static_assert(RPL >= 1 && G * b * w == 32768u * RPL, "lane geometry");
+    constexpr uint32_t TILE_ROWS = G * b * w / 128;  // 256, or 512 for 64 KiB tiles
+    static_assert(RPL >= 1 && (uint32_t)(NDW * 32 * RPL) == TILE_ROWS, "lane geometry");
+    // output boxes of the row map: 32 rows, or 64 for the 64 KiB tiles of 8 warps
+    constexpr uint32_t BOX_ROWS = TILE_ROWS / 8;
+    constexpr uint32_t WARP_BOXES = 32u * RPL / BOX_ROWS;
     constexpr uint32_t kHeadBytes = (G * (b / 4 + 1) + 15) & ~15u;  // reqBits bytes and lead codes, at most
 
     extern __shared__ __align__(16) uint8_t smem_raw[];  // realigned to 1024 below
@@ -220,7 +228,7 @@ __global__ void __launch_bounds__(kDThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
     __shared__ __align__(8) unsigned long long st_end[kDSlots];  // its end, as a position of the ring's sequence
 
     uint8_t *smem = smem_raw + ((1024u - (smem_addr(smem_raw) & 1023u)) & 1023u);
-    const DSmem L = decompress_smem(G, b, w);
+    const DSmem L = decompress_smem(G, b, w, NDW);
     const uint32_t *lut = reinterpret_cast<const uint32_t *>(smem + L.lut);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
@@ -592,7 +600,13 @@ __global__ void __launch_bounds__(kDThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
                 for (int i = 0; i < NCODE; ++i) codes[i] = 0;
                 if (coded) {
                     const uint8_t *lead = rec + rank * (b / 4) + sub * (VPL / 4);
-                    if constexpr (NCODE == 2) {
+                    if constexpr (NCODE == 4) {
+                        const uint4 v = *reinterpret_cast<const uint4 *>(lead);
+                        codes[0] = v.x;
+                        codes[1] = v.y;
+                        codes[2] = v.z;
+                        codes[3] = v.w;
+                    } else if constexpr (NCODE == 2) {
                         const uint2 v = *reinterpret_cast<const uint2 *>(lead);
                         codes[0] = v.x;
                         codes[1] = v.y;
@@ -739,7 +753,7 @@ __global__ void __launch_bounds__(kDThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
             // rows of the output count from the range's first row; a warp whose
             // rows all lie at or after it stores through the tensor map (rows past
             // the end are clipped), one that straddles the start stores plainly
-            const uint64_t wrow0 = (uint64_t)tile * 256 * RPL + (uint64_t)warp * 32 * RPL;  // warp's first row
+            const uint64_t wrow0 = (uint64_t)tile * TILE_ROWS + (uint64_t)warp * 32 * RPL;  // warp's first row
             const bool tma_rows = FT || (Fd->use_tma && wrow0 >= Fd->row_lo && wrow0 - Fd->row_lo < Fd->rows_full);
             const bool wanted = FT || (kg >= Fd->blk_lo && kg < Fd->blk_hi);
             if (tma_rows) {
@@ -787,10 +801,19 @@ __global__ void __launch_bounds__(kDThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
                 fence_proxy_async_smem();
                 __syncwarp();
                 if (lane == 0) {
-                    asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(
-                                     reinterpret_cast<uint64_t>(&Fd->tmap)),
-                                 "r"(0), "r"((int)(wrow0 - Fd->row_lo)), "r"(smem_addr(wbuf))
-                                 : "memory");
+                    // one store per box of the warp's rows (a box starting past
+                    // the range's last row is not issued; rows past it inside a
+                    // box are clipped)
+#pragma unroll
+                    for (uint32_t bx = 0; bx < WARP_BOXES; ++bx) {
+                        const uint64_t r0 = wrow0 - Fd->row_lo + bx * BOX_ROWS;
+                        if (bx > 0 && !FT && r0 >= Fd->rows_full) break;
+                        asm volatile(
+                            "cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(
+                                reinterpret_cast<uint64_t>(&Fd->tmap)),
+                            "r"(0), "r"((int)r0), "r"(smem_addr(wbuf + bx * BOX_ROWS * 128u))
+                            : "memory");
+                    }
                     bulk_commit();
                 }
             }
@@ -806,42 +829,63 @@ __global__ void __launch_bounds__(kDThreads, (VPL * sizeof(T) > 128) ? 1 : 2)
 
 namespace {
 
-template <typename T, int LPB, int VPL>
+template <typename T, int LPB, int VPL, int NDW>
 cudaError_t launch_t(const DField &one, const DecompressLaunch &lc, int ctas_per_sm, cudaStream_t stream) {
     constexpr uint32_t b = (uint32_t)(LPB * VPL), w = (uint32_t)Fmt<T>::w;
-    const DSmem L = decompress_smem(tile_blocks(b, w), b, w);
+    const DSmem L = decompress_smem(tile_blocks(b, w), b, w, NDW);
     if (L.ring_bytes < record_max_bytes(tile_blocks(b, w), b, w) + 16) return cudaErrorInvalidValue;
-    auto kern = lc.fields ? decompress_kernel<T, LPB, VPL, true> : decompress_kernel<T, LPB, VPL, false>;
+    auto kern =
+        lc.fields ? decompress_kernel<T, LPB, VPL, NDW, true> : decompress_kernel<T, LPB, VPL, NDW, false>;
     // per device and kernel: the shared-memory attribute and the occupancy,
     // set up on first use (a launch then only reads them)
     int per_sm = 0, sms = 0;
-    cudaError_t err = launch_setup(reinterpret_cast<const void *>(kern), L.total, kDThreads, &per_sm, &sms);
+    cudaError_t err =
+        launch_setup(reinterpret_cast<const void *>(kern), L.total, decompress_threads(NDW), &per_sm, &sms);
     if (err != cudaSuccess) return err;
     if (ctas_per_sm > 0 && ctas_per_sm < per_sm) per_sm = ctas_per_sm;
     const uint64_t grid = min_u64(lc.total_tiles, (uint64_t)sms * per_sm);
-    kern<<<(unsigned)grid, kDThreads, L.total, stream>>>(one, lc);
+    kern<<<(unsigned)grid, decompress_threads(NDW), L.total, stream>>>(one, lc);
     return cudaGetLastError();
 }
 
-cudaError_t ddispatch(int dtype, uint32_t block, const DField &one, const DecompressLaunch &lc, int ctas_per_sm,
-                      cudaStream_t stream) {
-    if (dtype == 0) {
+// The kernel instance for (dtype, block, decoding warps); the same pairs as
+// the compressor's.
+cudaError_t ddispatch(int dtype, uint32_t block, int nw, const DField &one, const DecompressLaunch &lc,
+                      int ctas_per_sm, cudaStream_t stream) {
+    if (nw == 0) nw = 8;
+    if (dtype == 0 && nw == 8) {
         switch (block) {
-            case 32: return launch_t<float, 1, 32>(one, lc, ctas_per_sm, stream);
-            case 64: return launch_t<float, 2, 32>(one, lc, ctas_per_sm, stream);
-            case 128: return launch_t<float, 4, 32>(one, lc, ctas_per_sm, stream);
-            case 256: return launch_t<float, 8, 32>(one, lc, ctas_per_sm, stream);
-            case 512: return launch_t<float, 16, 32>(one, lc, ctas_per_sm, stream);
-            case 1024: return launch_t<float, 32, 32>(one, lc, ctas_per_sm, stream);
+            case 32: return launch_t<float, 1, 32, 8>(one, lc, ctas_per_sm, stream);
+            case 64: return launch_t<float, 2, 32, 8>(one, lc, ctas_per_sm, stream);
+            case 128: return launch_t<float, 4, 32, 8>(one, lc, ctas_per_sm, stream);
+            case 256: return launch_t<float, 8, 32, 8>(one, lc, ctas_per_sm, stream);
+            case 512: return launch_t<float, 16, 32, 8>(one, lc, ctas_per_sm, stream);
+            case 1024: return launch_t<float, 32, 32, 8>(one, lc, ctas_per_sm, stream);
         }
-    } else {
+    } else if (dtype == 0 && nw == 4) {
         switch (block) {
-            case 32: return launch_t<double, 2, 16>(one, lc, ctas_per_sm, stream);
-            case 64: return launch_t<double, 4, 16>(one, lc, ctas_per_sm, stream);
-            case 128: return launch_t<double, 8, 16>(one, lc, ctas_per_sm, stream);
-            case 256: return launch_t<double, 16, 16>(one, lc, ctas_per_sm, stream);
-            case 512: return launch_t<double, 32, 16>(one, lc, ctas_per_sm, stream);
-            case 1024: return launch_t<double, 32, 32>(one, lc, ctas_per_sm, stream);
+            case 64: return launch_t<float, 1, 64, 4>(one, lc, ctas_per_sm, stream);
+            case 128: return launch_t<float, 2, 64, 4>(one, lc, ctas_per_sm, stream);
+            case 256: return launch_t<float, 4, 64, 4>(one, lc, ctas_per_sm, stream);
+            case 512: return launch_t<float, 8, 64, 4>(one, lc, ctas_per_sm, stream);
+            case 1024: return launch_t<float, 16, 64, 4>(one, lc, ctas_per_sm, stream);
+        }
+    } else if (dtype == 1 && nw == 8) {
+        switch (block) {
+            case 32: return launch_t<double, 2, 16, 8>(one, lc, ctas_per_sm, stream);
+            case 64: return launch_t<double, 4, 16, 8>(one, lc, ctas_per_sm, stream);
+            case 128: return launch_t<double, 8, 16, 8>(one, lc, ctas_per_sm, stream);
+            case 256: return launch_t<double, 16, 16, 8>(one, lc, ctas_per_sm, stream);
+            case 512: return launch_t<double, 32, 16, 8>(one, lc, ctas_per_sm, stream);
+            case 1024: return launch_t<double, 32, 32, 8>(one, lc, ctas_per_sm, stream);
+        }
+    } else if (dtype == 1 && nw == 4) {
+        switch (block) {
+            case 32: return launch_t<double, 1, 32, 4>(one, lc, ctas_per_sm, stream);
+            case 64: return launch_t<double, 2, 32, 4>(one, lc, ctas_per_sm, stream);
+            case 128: return launch_t<double, 4, 32, 4>(one, lc, ctas_per_sm, stream);
+            case 256: return launch_t<double, 8, 32, 4>(one, lc, ctas_per_sm, stream);
+            case 512: return launch_t<double, 16, 32, 4>(one, lc, ctas_per_sm, stream);
         }
     }
     return cudaErrorInvalidValue;
@@ -873,7 +917,8 @@ void fill_decompress_field(DField *f, const void *in, uint64_t total_bytes, uint
     a.tile0 = tile0;
     a.dtype = (uint32_t)dtype;
     a.check_header = check_header ? 1u : 0u;
-    // one box per decoding warp: its 32 lanes' rows
+    // boxes of an eighth of a tile's rows: one per warp of eight (their 32
+    // lanes' rows), two per warp of four
     const uint32_t box_rows = (dtype == 1 && block == 1024) ? 64u : 32u;
     a.use_tma = encode_row_map(&a.tmap, out, a.rows_full, box_rows) ? 1u : 0u;
 }
@@ -895,11 +940,11 @@ cudaError_t launch_decompress(const void *in, uint64_t in_bytes, uint64_t total_
     if (!lc.total_tiles) return cudaSuccess;
     lc.copy_ns = copy_limit_ns();
     lc.ticket = nullptr;  // no device workspace here: the static split
-    return ddispatch(dtype, block, one, lc, 0, stream);
+    return ddispatch(dtype, block, 8, one, lc, 0, stream);
 }
 
 cudaError_t launch_decompress_batch(const void *d_fields, uint32_t nfields, uint64_t total_tiles, uint32_t *d_ticket,
-                                    int dtype, uint32_t block, int ctas_per_sm, cudaStream_t stream) {
+                                    int dtype, uint32_t block, int ctas_per_sm, int nw, cudaStream_t stream) {
     DField one;
     std::memset(&one, 0, sizeof(one));
     DecompressLaunch lc;
@@ -908,7 +953,7 @@ cudaError_t launch_decompress_batch(const void *d_fields, uint32_t nfields, uint
     lc.total_tiles = total_tiles;
     lc.copy_ns = copy_limit_ns();
     lc.ticket = d_ticket;
-    return ddispatch(dtype, block, one, lc, ctas_per_sm, stream);
+    return ddispatch(dtype, block, nw, one, lc, ctas_per_sm, stream);
 }
 
 }  // namespace szx

@@ -92,7 +92,7 @@ def test_batch_autotune_keeps_streams():
     xs = [torch.from_numpy(np.ascontiguousarray(x)).cuda() for x, _, _ in fields]
     batch, outs, results = szx.batch_compress(xs, [eb for _, eb, _ in fields], [b for _, _, b in fields])
     choice = batch.autotune()
-    assert all(c in (1, 2) for c in choice)
+    assert all(g["ctas_per_sm"] in (1, 2) and g["warps_per_cta"] in (8, 4) and g["tuned_ms"] > 0 for g in choice)
     batch.run()
     torch.cuda.synchronize()
     for i, (x, eb, b) in enumerate(fields):
@@ -160,15 +160,107 @@ def test_block_zero_picks_a_candidate_and_round_trips():
 
 
 @pytest.mark.gpu
-def test_batch_block_zero_resolves_per_field():
-    from paper_2201_13020_b300 import metrics
-    fields = _fields()[:3]
+def test_batch_block_zero_is_chosen_by_the_tuner():
+    # block 0: the tuner picks b among 64, 128 and 256 per dtype group; every
+    # stream is then the oracle's at the chosen b
+    fields = _fields()[:5]
     xs = [torch.from_numpy(np.ascontiguousarray(x)).cuda() for x, _, _ in fields]
     ebs = [eb for _, eb, _ in fields]
     batch, outs, results = szx.batch_compress(xs, ebs, 0)
+    groups = batch.autotune()
+    assert all(g["auto_block"] == 1 and g["block"] in szx.AUTO_BLOCKS for g in groups)
+    assert sorted(g["dtype"] for g in groups) == [0, 1]
     batch.run()
     torch.cuda.synchronize()
+    chosen = {g["dtype"]: g["block"] for g in groups}
     for i, (x, eb, _) in enumerate(fields):
-        pick, _ = metrics.choose_block(xs[i], eb)
+        b = chosen[0 if x.dtype == np.float32 else 1]
         n = int(results[2 * i].item())
-        assert np.array_equal(outs[i][:n].cpu().numpy(), oracle.compress(x, eb, pick))
+        assert int(results[2 * i + 1].item()) == 0
+        assert np.array_equal(outs[i][:n].cpu().numpy(), oracle.compress(x, eb, b)), f"field {i} (b = {b})"
+
+
+def _shape_fields(dtype, block):
+    """Three fields of one (dtype, block): several tiles with a ragged end, a
+    partial single tile, one partial block."""
+    rng = np.random.default_rng(block + (dtype == np.float64))
+    tile = max(8, 32768 // (block * np.dtype(dtype).itemsize)) * block
+    xs = [np.cumsum(rng.normal(size=3 * tile + block // 2 + 3)).astype(dtype),
+          (np.sin(np.linspace(0, 30, tile // 2 + 1)) + 1e-3 * rng.normal(size=tile // 2 + 1)).astype(dtype),
+          rng.normal(size=max(1, block // 3)).astype(dtype)]
+    xs[0][tile:tile + block] = xs[0][tile]  # a constant block
+    return [(x, inputs.rel_to_abs(x, 1e-3)) for x in xs]
+
+
+SHAPES = [(dt, b, nw) for dt in (np.float32, np.float64) for b in (32, 64, 128, 256, 512, 1024) for nw in (8, 4)
+          if nw == 8 or (b >= 64 if dt == np.float32 else b <= 512)]
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("dtype,block,nw", SHAPES)
+def test_every_kernel_shape_matches_the_oracle(dtype, block, nw):
+    """Each instance of the kernels (consumer / decoding warps per CTA, values
+    per lane) writes the oracle's streams byte for byte and decodes them bit
+    for bit, at 2 and at 1 CTA per SM."""
+    fields = _shape_fields(dtype, block)
+    xs = [torch.from_numpy(x).cuda() for x, _ in fields]
+    refs = [oracle.compress(x, eb, block) for x, eb in fields]
+    batch, outs, results = szx.batch_compress(xs, [eb for _, eb in fields], block)
+    bufs = [torch.from_numpy(r).cuda() for r in refs]
+    dbatch, ys, statuses = szx.batch_decompress(bufs, [szx.header(bb) for bb in bufs])
+    for ctas in (2, 1):
+        batch.set_group(0, ctas, nw)
+        dbatch.set_group(0, ctas, nw)
+        g = batch.groups()[0]
+        assert (g["warps_per_cta"], g["threads_per_cta"], g["ctas_per_sm"]) == (nw, 32 * nw + 64, ctas)
+        for o in outs:
+            o.fill_(0xA5)
+        batch.run()
+        dbatch.run()
+        torch.cuda.synchronize()
+        res = results.cpu().numpy().reshape(-1, 2)
+        assert statuses.cpu().tolist() == [0, 0, 0]
+        for i, ((x, eb), ref) in enumerate(zip(fields, refs)):
+            assert res[i, 1] == 0 and res[i, 0] == len(ref), (i, res[i])
+            assert np.array_equal(outs[i][:len(ref)].cpu().numpy(), ref), f"field {i}: stream ({ctas} CTAs/SM)"
+            u = np.uint32 if dtype == np.float32 else np.uint64
+            y_ref = oracle.decompress(ref)
+            assert np.array_equal(ys[i].cpu().numpy().view(u), y_ref.view(u)), f"field {i}: decode ({ctas} CTAs/SM)"
+
+
+def test_batch_group_shapes_on_host():
+    # plan creation and shape calls are host-only: fake aligned device
+    # addresses are never touched
+    L = _lib.lib()
+    F = _lib.SzxField
+    arr = (F * 3)(F(256, 70_000, _lib.SZX_F32, 1e-3, 128, 512, 1 << 22),
+                  F(256, 70_000, _lib.SZX_F32, 1e-3, 32, 512, 1 << 22),
+                  F(256, 70_000, _lib.SZX_F64, 1e-3, 1024, 512, 1 << 22))
+    plan = ctypes.c_void_p(0)
+    assert L.szx_batch_compress_plan(arr, 3, ctypes.byref(plan)) == 0
+    assert L.szx_batch_groups(plan, None, 0) == 3
+    info = {}
+    for i in range(3):
+        g = _lib.SzxBatchGroup()
+        assert L.szx_batch_group_info(plan, i, ctypes.byref(g)) == 0
+        info[(g.dtype, g.block)] = (i, g)
+    i128, g128 = info[(0, 128)]
+    assert (g128.warps_per_cta, g128.values_per_lane, g128.blocks_per_warp, g128.threads_per_cta) == (8, 32, 8, 320)
+    assert L.szx_batch_set_group(plan, i128, 2, 4) == 0
+    assert L.szx_batch_group_info(plan, i128, ctypes.byref(g128)) == 0
+    assert (g128.warps_per_cta, g128.values_per_lane, g128.blocks_per_warp, g128.threads_per_cta) == (4, 64, 16, 192)
+    # no 4-warp instance for f32 with b = 32, nor f64 with b = 1024; no 3 CTAs per SM
+    assert L.szx_batch_set_group(plan, info[(0, 32)][0], 0, 4) == 1
+    assert L.szx_batch_set_group(plan, info[(1, 1024)][0], 0, 4) == 1
+    assert L.szx_batch_set_group(plan, i128, 3, 8) == 1
+    assert L.szx_batch_group_info(plan, 3, ctypes.byref(g128)) == 1
+    L.szx_batch_destroy(plan)
+    # block 0: planned at 128, the capacity must hold the largest candidate stream
+    need = max(L.szx_stream_max_bytes(10_000, _lib.SZX_F32, b) for b in (64, 128, 256))
+    arr = (F * 1)(F(256, 10_000, _lib.SZX_F32, 1e-3, 0, 512, need - 16))
+    assert L.szx_batch_compress_plan(arr, 1, ctypes.byref(plan)) == 2
+    arr = (F * 1)(F(256, 10_000, _lib.SZX_F32, 1e-3, 0, 512, need))
+    assert L.szx_batch_compress_plan(arr, 1, ctypes.byref(plan)) == 0
+    g = _lib.SzxBatchGroup()
+    assert L.szx_batch_group_info(plan, 0, ctypes.byref(g)) == 0 and g.auto_block == 1 and g.block == 128
+    L.szx_batch_destroy(plan)
