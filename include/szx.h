@@ -310,7 +310,7 @@ szx_status szx_batch_autotune(szx_batch_plan *plan, void *d_ws,
                               szx_stream_t stream);
 
 /* Number of groups; writes up to `capacity` CTAs-per-SM choices (0 = as many
- * as fit) into ctas_per_sm. */
+ * as fit) into ctas_per_sm (which may be NULL when capacity is 0). */
 int szx_batch_groups(const szx_batch_plan *plan, int *ctas_per_sm, int capacity);
 
 /* A group's shape. */
