@@ -44,8 +44,10 @@
 // value's) forward from the nearest earlier owner, or from the carry into
 // the lane -- the last own byte of the nearest lower lane of the block that
 // owns one (a ballot and a shuffle).  This is the paper's index propagation
-// (Sec. V-B) in one step per plane.  A byte transpose turns planes back into
-// words; then v' = t << s and d' = RN(v' + mu).
+// (Sec. V-B) in one step per plane.  When every lane of a warp owns byte 2
+// of all its values, plane 2 needs neither: each group's word is a funnel
+// shift of two consecutive words of the run.  A byte transpose turns planes
+// back into words; then v' = t << s and d' = RN(v' + mu).
 #include <cstring>
 #include <type_traits>
 
@@ -664,8 +666,25 @@ __global__ void __launch_bounds__(decompress_threads(NDW),
                     }
                 }
 
+                // Does every plane-2 run of the warp hold byte 2 of all its
+                // lane's values (no code 3, every value valid)?  Then each
+                // group's word of plane 2 is one funnel shift of two
+                // consecutive words of the run (one new load per group), with
+                // no permute and no carry.  Decided for the whole warp.
+                bool dense2;
+                {
+                    bool no3 = true;
+#pragma unroll
+                    for (int i = 0; i < NCODE; ++i) no3 = no3 && (codes[i] & (codes[i] >> 1) & 0x55555555u) == 0u;
+                    dense2 = __all_sync(kFull, !(coded && q >= 3) || (full_lane && no3));
+                }
                 if (coded) {
                     const T mu = F::from(mu_bits);
+                    // the dense run: 32-bit words from pos2's word on, read with
+                    // the byte shift of pos2 (the record's slack covers the last)
+                    const uint32_t *rw = reinterpret_cast<const uint32_t *>(rec);
+                    const uint32_t w2 = pos2 >> 2, a2 = (pos2 & 3u) * 8u;
+                    uint32_t cur2 = (dense2 && q >= 3) ? rw[w2] : 0u;
 #pragma unroll
                     for (int gq = 0; gq < VPL / 4; ++gq) {
                         uint32_t code8 = (codes[gq >> 2] >> (8 * (gq & 3))) & 0xFFu;
@@ -691,10 +710,16 @@ __global__ void __launch_bounds__(decompress_threads(NDW),
                             pos1 += e1 >> 16;
                             carry[1] = P[1] >> 24;
                             if (q >= 3) {
-                                const uint32_t e2 = lut[512 + code8];
-                                P[2] = dprmt(load_run(rec, pos2), carry[2], e2);
-                                pos2 += e2 >> 16;
-                                carry[2] = P[2] >> 24;
+                                if (dense2) {
+                                    const uint32_t nxt = rw[w2 + gq + 1];
+                                    P[2] = __funnelshift_r(cur2, nxt, a2);
+                                    cur2 = nxt;
+                                } else {
+                                    const uint32_t e2 = lut[512 + code8];
+                                    P[2] = dprmt(load_run(rec, pos2), carry[2], e2);
+                                    pos2 += e2 >> 16;
+                                    carry[2] = P[2] >> 24;
+                                }
                             }
                             if (q >= 4) {
                                 // dense planes: every valid value owns its byte
