@@ -1132,7 +1132,9 @@ def main():
                          "peak_kind": f"hbm_gbs of {peak_kind}", "unit": "GB/s", "frac": achieved / peak,
                          "traffic": traffic, "algorithmic_bytes_per_launch": alg_bytes},
             "cpu_baseline": cpu_base, "e2e": e2e, "e2e_serial": e2e_serial, "clocks": clocks.summary(),
-            "gpu_launches": 2 * args.steps,
+            # per step: the workspace clear and the compression kernel, the
+            # status clear and the decompression kernel
+            "gpu_launches": 4 * args.steps,
             "stream": {"bytes": nbytes, "nonconst": h.nonconst, "raw": h.raw, "escalated": h.escalated,
                        "blocks": -(-n // BLOCK)},
             "gpu": torch.cuda.get_device_name(local),

@@ -188,8 +188,8 @@ szx_status szx_header_read(const void *d_in, size_t in_bytes, szx_header *h,
  * stream's dtype; out_capacity >= n * 4 or n * 8 bytes).  *n_out and
  * *dtype_out receive the header's values (either may be NULL).  Every read
  * of the stream is bounds-checked on the device; a malformed stream returns
- * SZX_ERR_CORRUPT.  Synchronous (one 64-byte header read, the kernel, one
- * 4-byte status read).  Allocates nothing: its device status word is one of
+ * SZX_ERR_CORRUPT.  Synchronous (one 64-byte header read, the status clear
+ * and the kernel, one 4-byte status read).  Allocates nothing: its device status word is one of
  * 256 words of a fixed array inside the library, taken round-robin, so that
  * up to 256 calls in flight at once (from different host threads) get
  * distinct words.

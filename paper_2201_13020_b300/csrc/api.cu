@@ -2,7 +2,7 @@
 //
 // Host-side argument checks, the stream geometry, and the launch sequence on
 // the caller's stream.  Every device step is one of this library's kernels
-// (plus a cudaMemsetAsync of the compress scratch words); there is no host or
+// (the scratch and status words are cleared by one too); there is no host or
 // CPU fallback: if the kernels cannot run, the call returns SZX_ERR_CUDA.
 #include "szx.h"
 #include "szx_device.cuh"
@@ -208,7 +208,6 @@ szx_status szx_decompress_async(const void *d_in, size_t in_bytes, const szx_hea
     if (h->total_bytes > in_bytes || h->total_bytes < g.off_rec) return SZX_ERR_CORRUPT;
     if (out_capacity < h->n * width(h->dtype)) return SZX_ERR_TOO_SMALL;
     cudaStream_t s = (cudaStream_t)stream;
-    if (d_status && cudaMemsetAsync(d_status, 0, sizeof(uint32_t), s) != cudaSuccess) return SZX_ERR_CUDA;
     return from_cuda(launch_decompress(d_in, in_bytes, h->total_bytes, h->n, (int)h->dtype, h->block, d_out,
                                        d_status, true, s));
 }
@@ -227,7 +226,6 @@ szx_status szx_decompress_range_async(const void *d_in, size_t in_bytes, const s
     const uint64_t vals = min_u64(h->n, last * h->block) - (uint64_t)first_block * h->block;
     if (out_capacity < vals * width(h->dtype)) return SZX_ERR_TOO_SMALL;
     cudaStream_t s = (cudaStream_t)stream;
-    if (d_status && cudaMemsetAsync(d_status, 0, sizeof(uint32_t), s) != cudaSuccess) return SZX_ERR_CUDA;
     return from_cuda(launch_decompress(d_in, in_bytes, h->total_bytes, h->n, (int)h->dtype, h->block, d_out,
                                        d_status, true, s, first_block, last));
 }

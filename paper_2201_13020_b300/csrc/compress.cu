@@ -558,6 +558,9 @@ __global__ void __launch_bounds__(compress_threads(NW),
         }
     }
     __syncthreads();
+    // nothing above reads or writes memory that an earlier kernel may write
+    // (the launch may be the programmatic dependent of the workspace clear)
+    wait_prior_grids();
 
     if (warp == kProducerWarp) {
         // ---- producer: tickets and tile copies into the stage ring ---------
@@ -1111,13 +1114,28 @@ __global__ void __launch_bounds__(compress_threads(NW),
 }
 
 
+__global__ void clear_words_kernel(uint32_t *p, uint64_t n) {
+    // the kernel behind this one may start now (it waits for this one to end
+    // before its first global access)
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) p[i] = 0u;
+}
+
 // ---------------------------------------------------------------------------
 // host side
+
+cudaError_t launch_clear_words(uint32_t *p, uint64_t n, cudaStream_t stream) {
+    if (n == 0) return cudaSuccess;
+    const uint64_t ctas = min_u64((n + 255) / 256, 4 * 148);
+    clear_words_kernel<<<(unsigned)ctas, 256, 0, stream>>>(p, n);
+    return cudaGetLastError();
+}
 
 namespace {
 
 template <typename T, int LPB, int VPL, int NW>
-cudaError_t launch_t(const CField &one, const CompressLaunch &lc, int ctas_per_sm, cudaStream_t stream) {
+cudaError_t launch_t(const CField &one, const CompressLaunch &lc, int ctas_per_sm, bool pdl, cudaStream_t stream) {
     constexpr uint32_t b = (uint32_t)(LPB * VPL), w = (uint32_t)Fmt<T>::w;
     const CSmem L = compress_smem(tile_blocks(b, w), b, w, NW);
     auto kern = lc.fields ? compress_kernel<T, LPB, VPL, NW, true> : compress_kernel<T, LPB, VPL, NW, false>;
@@ -1129,8 +1147,7 @@ cudaError_t launch_t(const CField &one, const CompressLaunch &lc, int ctas_per_s
     if (err != cudaSuccess) return err;
     if (ctas_per_sm > 0 && ctas_per_sm < per_sm) per_sm = ctas_per_sm;
     const uint64_t grid = min_u64(lc.total_tiles, (uint64_t)sms * per_sm);
-    kern<<<(unsigned)grid, compress_threads(NW), L.total, stream>>>(one, lc);
-    return cudaGetLastError();
+    return launch_kernel(kern, (unsigned)grid, compress_threads(NW), L.total, pdl, stream, one, lc);
 }
 
 // The kernel instance for (dtype, block, consumer warps): 8 warps with 32
@@ -1138,41 +1155,41 @@ cudaError_t launch_t(const CField &one, const CompressLaunch &lc, int ctas_per_s
 // where a block still covers whole lanes (not for f32 with b = 32, nor f64
 // with b = 1024, whose 64 values per lane would not fit the registers).
 cudaError_t dispatch(int dtype, uint32_t block, int nw, const CField &one, const CompressLaunch &lc,
-                     int ctas_per_sm, cudaStream_t stream) {
+                     int ctas_per_sm, bool pdl, cudaStream_t stream) {
     if (nw == 0) nw = 8;
     if (dtype == 0 && nw == 8) {
         switch (block) {
-            case 32: return launch_t<float, 1, 32, 8>(one, lc, ctas_per_sm, stream);
-            case 64: return launch_t<float, 2, 32, 8>(one, lc, ctas_per_sm, stream);
-            case 128: return launch_t<float, 4, 32, 8>(one, lc, ctas_per_sm, stream);
-            case 256: return launch_t<float, 8, 32, 8>(one, lc, ctas_per_sm, stream);
-            case 512: return launch_t<float, 16, 32, 8>(one, lc, ctas_per_sm, stream);
-            case 1024: return launch_t<float, 32, 32, 8>(one, lc, ctas_per_sm, stream);
+            case 32: return launch_t<float, 1, 32, 8>(one, lc, ctas_per_sm, pdl, stream);
+            case 64: return launch_t<float, 2, 32, 8>(one, lc, ctas_per_sm, pdl, stream);
+            case 128: return launch_t<float, 4, 32, 8>(one, lc, ctas_per_sm, pdl, stream);
+            case 256: return launch_t<float, 8, 32, 8>(one, lc, ctas_per_sm, pdl, stream);
+            case 512: return launch_t<float, 16, 32, 8>(one, lc, ctas_per_sm, pdl, stream);
+            case 1024: return launch_t<float, 32, 32, 8>(one, lc, ctas_per_sm, pdl, stream);
         }
     } else if (dtype == 0 && nw == 4) {
         switch (block) {
-            case 64: return launch_t<float, 1, 64, 4>(one, lc, ctas_per_sm, stream);
-            case 128: return launch_t<float, 2, 64, 4>(one, lc, ctas_per_sm, stream);
-            case 256: return launch_t<float, 4, 64, 4>(one, lc, ctas_per_sm, stream);
-            case 512: return launch_t<float, 8, 64, 4>(one, lc, ctas_per_sm, stream);
-            case 1024: return launch_t<float, 16, 64, 4>(one, lc, ctas_per_sm, stream);
+            case 64: return launch_t<float, 1, 64, 4>(one, lc, ctas_per_sm, pdl, stream);
+            case 128: return launch_t<float, 2, 64, 4>(one, lc, ctas_per_sm, pdl, stream);
+            case 256: return launch_t<float, 4, 64, 4>(one, lc, ctas_per_sm, pdl, stream);
+            case 512: return launch_t<float, 8, 64, 4>(one, lc, ctas_per_sm, pdl, stream);
+            case 1024: return launch_t<float, 16, 64, 4>(one, lc, ctas_per_sm, pdl, stream);
         }
     } else if (dtype == 1 && nw == 8) {
         switch (block) {
-            case 32: return launch_t<double, 2, 16, 8>(one, lc, ctas_per_sm, stream);
-            case 64: return launch_t<double, 4, 16, 8>(one, lc, ctas_per_sm, stream);
-            case 128: return launch_t<double, 8, 16, 8>(one, lc, ctas_per_sm, stream);
-            case 256: return launch_t<double, 16, 16, 8>(one, lc, ctas_per_sm, stream);
-            case 512: return launch_t<double, 32, 16, 8>(one, lc, ctas_per_sm, stream);
-            case 1024: return launch_t<double, 32, 32, 8>(one, lc, ctas_per_sm, stream);
+            case 32: return launch_t<double, 2, 16, 8>(one, lc, ctas_per_sm, pdl, stream);
+            case 64: return launch_t<double, 4, 16, 8>(one, lc, ctas_per_sm, pdl, stream);
+            case 128: return launch_t<double, 8, 16, 8>(one, lc, ctas_per_sm, pdl, stream);
+            case 256: return launch_t<double, 16, 16, 8>(one, lc, ctas_per_sm, pdl, stream);
+            case 512: return launch_t<double, 32, 16, 8>(one, lc, ctas_per_sm, pdl, stream);
+            case 1024: return launch_t<double, 32, 32, 8>(one, lc, ctas_per_sm, pdl, stream);
         }
     } else if (dtype == 1 && nw == 4) {
         switch (block) {
-            case 32: return launch_t<double, 1, 32, 4>(one, lc, ctas_per_sm, stream);
-            case 64: return launch_t<double, 2, 32, 4>(one, lc, ctas_per_sm, stream);
-            case 128: return launch_t<double, 4, 32, 4>(one, lc, ctas_per_sm, stream);
-            case 256: return launch_t<double, 8, 32, 4>(one, lc, ctas_per_sm, stream);
-            case 512: return launch_t<double, 16, 32, 4>(one, lc, ctas_per_sm, stream);
+            case 32: return launch_t<double, 1, 32, 4>(one, lc, ctas_per_sm, pdl, stream);
+            case 64: return launch_t<double, 2, 32, 4>(one, lc, ctas_per_sm, pdl, stream);
+            case 128: return launch_t<double, 4, 32, 4>(one, lc, ctas_per_sm, pdl, stream);
+            case 256: return launch_t<double, 8, 32, 4>(one, lc, ctas_per_sm, pdl, stream);
+            case 512: return launch_t<double, 16, 32, 4>(one, lc, ctas_per_sm, pdl, stream);
         }
     }
     return cudaErrorInvalidValue;
@@ -1218,9 +1235,11 @@ cudaError_t launch_compress_ws(const void *in, uint64_t n, int dtype, uint64_t e
     lc.err = &w->err;
     lc.lookback_ns = 1000ull * wait_limit_from_env("SZX_LOOKBACK_US", 1000000u);
     lc.copy_ns = 1000ull * wait_limit_from_env("SZX_COPY_US", 1000000u);
-    cudaError_t err = cudaMemsetAsync(ws, 0, workspace_bytes(one.g.ntiles), stream);
+    // the counters and look-back flags start at zero (workspace_bytes is a
+    // multiple of 8); the kernel starts behind the clear
+    cudaError_t err = launch_clear_words(static_cast<uint32_t *>(ws), workspace_bytes(one.g.ntiles) / 4, stream);
     if (err != cudaSuccess) return err;
-    return dispatch(dtype, block, 8, one, lc, 0, stream);
+    return dispatch(dtype, block, 8, one, lc, 0, true, stream);
 }
 
 cudaError_t launch_compress_batch(const void *d_fields, uint32_t nfields, uint64_t total_tiles, uint32_t *d_counters,
@@ -1236,7 +1255,7 @@ cudaError_t launch_compress_batch(const void *d_fields, uint32_t nfields, uint64
     lc.err = d_counters + 2;
     lc.lookback_ns = 1000ull * wait_limit_from_env("SZX_LOOKBACK_US", 1000000u);
     lc.copy_ns = 1000ull * wait_limit_from_env("SZX_COPY_US", 1000000u);
-    return dispatch(dtype, block, nw, one, lc, ctas_per_sm, stream);
+    return dispatch(dtype, block, nw, one, lc, ctas_per_sm, false, stream);
 }
 
 // ---------------------------------------------------------------------------

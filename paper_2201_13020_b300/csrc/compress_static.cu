@@ -17,7 +17,7 @@
 // first call made with that device current; later calls reuse it.  So a
 // cudaDeviceReset between calls (which reloads the module, possibly at
 // another address) is not supported, as szx.h states.  Every
-// call clears the part of the array it uses (cudaMemsetAsync on the caller's
+// call clears the part of the array it uses (a clear kernel on the caller's
 // stream) before the kernel starts, because the tile counters and look-back
 // flags must start at zero.  All calls on one device share the array, so two
 // calls that can overlap in time (different streams, or different host

@@ -251,6 +251,9 @@ __global__ void __launch_bounds__(decompress_threads(NDW),
         fence_mbar_init();
     }
     __syncthreads();
+    // nothing above reads or writes memory that an earlier kernel may write
+    // (the launch may be the programmatic dependent of the status clear)
+    wait_prior_grids();
 
     if (warp == kDProducerWarp) {
         // ---- producer: record copies into the ring, mu and state bits into the slots
@@ -855,7 +858,7 @@ __global__ void __launch_bounds__(decompress_threads(NDW),
 namespace {
 
 template <typename T, int LPB, int VPL, int NDW>
-cudaError_t launch_t(const DField &one, const DecompressLaunch &lc, int ctas_per_sm, cudaStream_t stream) {
+cudaError_t launch_t(const DField &one, const DecompressLaunch &lc, int ctas_per_sm, bool pdl, cudaStream_t stream) {
     constexpr uint32_t b = (uint32_t)(LPB * VPL), w = (uint32_t)Fmt<T>::w;
     const DSmem L = decompress_smem(tile_blocks(b, w), b, w, NDW);
     if (L.ring_bytes < record_max_bytes(tile_blocks(b, w), b, w) + 16) return cudaErrorInvalidValue;
@@ -869,48 +872,47 @@ cudaError_t launch_t(const DField &one, const DecompressLaunch &lc, int ctas_per
     if (err != cudaSuccess) return err;
     if (ctas_per_sm > 0 && ctas_per_sm < per_sm) per_sm = ctas_per_sm;
     const uint64_t grid = min_u64(lc.total_tiles, (uint64_t)sms * per_sm);
-    kern<<<(unsigned)grid, decompress_threads(NDW), L.total, stream>>>(one, lc);
-    return cudaGetLastError();
+    return launch_kernel(kern, (unsigned)grid, decompress_threads(NDW), L.total, pdl, stream, one, lc);
 }
 
 // The kernel instance for (dtype, block, decoding warps); the same pairs as
 // the compressor's.
 cudaError_t ddispatch(int dtype, uint32_t block, int nw, const DField &one, const DecompressLaunch &lc,
-                      int ctas_per_sm, cudaStream_t stream) {
+                      int ctas_per_sm, bool pdl, cudaStream_t stream) {
     if (nw == 0) nw = 8;
     if (dtype == 0 && nw == 8) {
         switch (block) {
-            case 32: return launch_t<float, 1, 32, 8>(one, lc, ctas_per_sm, stream);
-            case 64: return launch_t<float, 2, 32, 8>(one, lc, ctas_per_sm, stream);
-            case 128: return launch_t<float, 4, 32, 8>(one, lc, ctas_per_sm, stream);
-            case 256: return launch_t<float, 8, 32, 8>(one, lc, ctas_per_sm, stream);
-            case 512: return launch_t<float, 16, 32, 8>(one, lc, ctas_per_sm, stream);
-            case 1024: return launch_t<float, 32, 32, 8>(one, lc, ctas_per_sm, stream);
+            case 32: return launch_t<float, 1, 32, 8>(one, lc, ctas_per_sm, pdl, stream);
+            case 64: return launch_t<float, 2, 32, 8>(one, lc, ctas_per_sm, pdl, stream);
+            case 128: return launch_t<float, 4, 32, 8>(one, lc, ctas_per_sm, pdl, stream);
+            case 256: return launch_t<float, 8, 32, 8>(one, lc, ctas_per_sm, pdl, stream);
+            case 512: return launch_t<float, 16, 32, 8>(one, lc, ctas_per_sm, pdl, stream);
+            case 1024: return launch_t<float, 32, 32, 8>(one, lc, ctas_per_sm, pdl, stream);
         }
     } else if (dtype == 0 && nw == 4) {
         switch (block) {
-            case 64: return launch_t<float, 1, 64, 4>(one, lc, ctas_per_sm, stream);
-            case 128: return launch_t<float, 2, 64, 4>(one, lc, ctas_per_sm, stream);
-            case 256: return launch_t<float, 4, 64, 4>(one, lc, ctas_per_sm, stream);
-            case 512: return launch_t<float, 8, 64, 4>(one, lc, ctas_per_sm, stream);
-            case 1024: return launch_t<float, 16, 64, 4>(one, lc, ctas_per_sm, stream);
+            case 64: return launch_t<float, 1, 64, 4>(one, lc, ctas_per_sm, pdl, stream);
+            case 128: return launch_t<float, 2, 64, 4>(one, lc, ctas_per_sm, pdl, stream);
+            case 256: return launch_t<float, 4, 64, 4>(one, lc, ctas_per_sm, pdl, stream);
+            case 512: return launch_t<float, 8, 64, 4>(one, lc, ctas_per_sm, pdl, stream);
+            case 1024: return launch_t<float, 16, 64, 4>(one, lc, ctas_per_sm, pdl, stream);
         }
     } else if (dtype == 1 && nw == 8) {
         switch (block) {
-            case 32: return launch_t<double, 2, 16, 8>(one, lc, ctas_per_sm, stream);
-            case 64: return launch_t<double, 4, 16, 8>(one, lc, ctas_per_sm, stream);
-            case 128: return launch_t<double, 8, 16, 8>(one, lc, ctas_per_sm, stream);
-            case 256: return launch_t<double, 16, 16, 8>(one, lc, ctas_per_sm, stream);
-            case 512: return launch_t<double, 32, 16, 8>(one, lc, ctas_per_sm, stream);
-            case 1024: return launch_t<double, 32, 32, 8>(one, lc, ctas_per_sm, stream);
+            case 32: return launch_t<double, 2, 16, 8>(one, lc, ctas_per_sm, pdl, stream);
+            case 64: return launch_t<double, 4, 16, 8>(one, lc, ctas_per_sm, pdl, stream);
+            case 128: return launch_t<double, 8, 16, 8>(one, lc, ctas_per_sm, pdl, stream);
+            case 256: return launch_t<double, 16, 16, 8>(one, lc, ctas_per_sm, pdl, stream);
+            case 512: return launch_t<double, 32, 16, 8>(one, lc, ctas_per_sm, pdl, stream);
+            case 1024: return launch_t<double, 32, 32, 8>(one, lc, ctas_per_sm, pdl, stream);
         }
     } else if (dtype == 1 && nw == 4) {
         switch (block) {
-            case 32: return launch_t<double, 1, 32, 4>(one, lc, ctas_per_sm, stream);
-            case 64: return launch_t<double, 2, 32, 4>(one, lc, ctas_per_sm, stream);
-            case 128: return launch_t<double, 4, 32, 4>(one, lc, ctas_per_sm, stream);
-            case 256: return launch_t<double, 8, 32, 4>(one, lc, ctas_per_sm, stream);
-            case 512: return launch_t<double, 16, 32, 4>(one, lc, ctas_per_sm, stream);
+            case 32: return launch_t<double, 1, 32, 4>(one, lc, ctas_per_sm, pdl, stream);
+            case 64: return launch_t<double, 2, 32, 4>(one, lc, ctas_per_sm, pdl, stream);
+            case 128: return launch_t<double, 4, 32, 4>(one, lc, ctas_per_sm, pdl, stream);
+            case 256: return launch_t<double, 8, 32, 4>(one, lc, ctas_per_sm, pdl, stream);
+            case 512: return launch_t<double, 16, 32, 4>(one, lc, ctas_per_sm, pdl, stream);
         }
     }
     return cudaErrorInvalidValue;
@@ -962,10 +964,15 @@ cudaError_t launch_decompress(const void *in, uint64_t in_bytes, uint64_t total_
     lc.fields = nullptr;
     lc.nfields = 1;
     lc.total_tiles = decompress_field_tiles(&one);
+    // the status starts at zero; the kernel starts behind the clear
+    if (d_status) {
+        const cudaError_t err = launch_clear_words(d_status, 1, stream);
+        if (err != cudaSuccess) return err;
+    }
     if (!lc.total_tiles) return cudaSuccess;
     lc.copy_ns = copy_limit_ns();
     lc.ticket = nullptr;  // no device workspace here: the static split
-    return ddispatch(dtype, block, 8, one, lc, 0, stream);
+    return ddispatch(dtype, block, 8, one, lc, 0, d_status != nullptr, stream);
 }
 
 cudaError_t launch_decompress_batch(const void *d_fields, uint32_t nfields, uint64_t total_tiles, uint32_t *d_ticket,
@@ -978,7 +985,7 @@ cudaError_t launch_decompress_batch(const void *d_fields, uint32_t nfields, uint
     lc.total_tiles = total_tiles;
     lc.copy_ns = copy_limit_ns();
     lc.ticket = d_ticket;
-    return ddispatch(dtype, block, nw, one, lc, ctas_per_sm, stream);
+    return ddispatch(dtype, block, nw, one, lc, ctas_per_sm, false, stream);
 }
 
 }  // namespace szx

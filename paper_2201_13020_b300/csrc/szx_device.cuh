@@ -150,6 +150,12 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t by
         : "memory");
 }
 
+// A kernel launched as the programmatic dependent of the one before it on the
+// stream may start while that one still runs: every thread calls this before
+// its first global-memory access, and it returns once the earlier kernels have
+// finished and their writes are visible (at once for a plain launch).
+__device__ __forceinline__ void wait_prior_grids() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 __device__ __forceinline__ uint64_t globaltimer_ns() {
     uint64_t t;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));

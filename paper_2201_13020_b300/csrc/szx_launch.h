@@ -2,10 +2,38 @@
 #pragma once
 
 #include <cstdint>
+#include <cstring>
 #include <cuda.h>
 #include <cuda_runtime.h>
 
 namespace szx {
+
+// Zero n 4-byte words at p (device memory) on `stream`, with a small kernel
+// (not a memset node) so that the kernel enqueued right after it can be
+// launched as its programmatic dependent (launch_kernel with pdl).
+cudaError_t launch_clear_words(uint32_t *p, uint64_t n, cudaStream_t stream);
+
+// kern<<<grid, threads, smem, stream>>>(args...).  With pdl, as the
+// programmatic dependent of the kernel before it on the stream: its CTAs may
+// start, and run what precedes their wait_prior_grids(), while that kernel
+// still runs.  Only kernels that call wait_prior_grids() before their first
+// global-memory access may be launched so.
+template <typename... P, typename... A>
+cudaError_t launch_kernel(void (*kern)(P...), unsigned grid, unsigned threads, size_t smem, bool pdl,
+                          cudaStream_t stream, A &&...args) {
+    cudaLaunchConfig_t cfg;
+    std::memset(&cfg, 0, sizeof(cfg));
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(threads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = stream;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = pdl ? at : nullptr;
+    cfg.numAttrs = pdl ? 1u : 0u;
+    return cudaLaunchKernelEx(&cfg, kern, static_cast<A &&>(args)...);
+}
 
 // Limit (microseconds) of a bounded device-side wait: the environment variable
 // `name` (a positive integer) if set, else `fallback`.  Read on every launch.
@@ -31,7 +59,8 @@ cudaError_t launch_compress(const void *in, uint64_t n, int dtype, uint64_t e_bi
 
 // Same, with the workspace (workspace_bytes(ntiles) bytes, 256-byte aligned)
 // at an arbitrary device address instead of the tail of out.  Clears it on
-// `stream` before the kernel runs.
+// `stream` (launch_clear_words) and launches the kernel as the clear's
+// programmatic dependent.
 cudaError_t launch_compress_ws(const void *in, uint64_t n, int dtype, uint64_t e_bits, uint32_t block,
                                void *out, void *ws, uint64_t *d_result, cudaStream_t stream);
 
@@ -82,8 +111,10 @@ cudaError_t launch_decompress_batch(const void *d_fields, uint32_t nfields, uint
                                     int dtype, uint32_t block, int ctas_per_sm, int nw, cudaStream_t stream);
 
 // Enqueue the decompression of a stream of total_bytes whose header says
-// (n, dtype, block).  Errors are folded into *d_status with atomicMax as
-// szx_status codes (d_status may be null).
+// (n, dtype, block).  *d_status is zeroed on `stream` first (launch_clear_words;
+// the kernel is then launched as the clear's programmatic dependent), and
+// errors are folded into it with atomicMax as szx_status codes (d_status may
+// be null).
 cudaError_t launch_decompress(const void *in, uint64_t in_bytes, uint64_t total_bytes, uint64_t n, int dtype,
                               uint32_t block, void *out, uint32_t *d_status, bool check_header,
                               cudaStream_t stream, uint64_t blk_lo = 0, uint64_t blk_hi = ~0ull);
