@@ -29,7 +29,9 @@
 //      the record), then encodes in registers -- block statistics
 //      (Algorithm 1): NaN-propagating min/max per lane, reduced over the
 //      block's lanes with shuffles; mu, r, the exact constant test, reqBits
-//      (Eq. 4), the Eq. 5 shift and truncation.  The per-value bound check is
+//      (Eq. 4) -- for f64 with 128 <= b <= 512 computed by warp 0 for every
+//      block of the tile from the keys the warps hand in through shared
+//      memory -- then the Eq. 5 shift and truncation.  The per-value bound check is
 //      skipped when a block-level bound proves it passes (see
 //      bound_check_needed); otherwise a fast test runs and an exact slow path
 //      re-checks a block that fails it, raising reqBits while a value exceeds
@@ -239,11 +241,53 @@ __device__ __forceinline__ bool bound_check_needed(T mn, T mx, T mu, int R, type
 // ---------------------------------------------------------------------------
 // per-lane encoding (step 1); FULL: every value of the lane is valid
 
-template <typename T, int LPB, int VPL, bool FULL>
-__device__ __forceinline__ void encode_lane(typename Fmt<T>::U (&x)[VPL], uint32_t (&codes)[(2 * VPL + 31) / 32],
+// One block's statistics from its min / max keys (Algorithm 1): r =
+// RN(RN(mx - mn) / 2), mu = RN(mn + r), the class (raw when a value or r or mu
+// is not finite; constant by the exact test |d - mu| <= e at both extremes),
+// R of Eq. 4 and reqBits = 1 + E + R before any escalation.
+template <typename T>
+struct BlockStats {
+    T mn, mx, mu;
+    int kind, R, req0;
+};
+template <typename T>
+__device__ __forceinline__ BlockStats<T> block_stats(typename Fmt<T>::S kmn, typename Fmt<T>::S kmx, bool exists,
+                                                     T e) {
+    using F = Fmt<T>;
+    BlockStats<T> o;
+    // a NaN's key lies above +inf (or, for f64 negative NaNs, below -inf)
+    const bool all_finite = kmn > F::kKeyNegInf && kmn < F::kKeyPosInf && kmx > F::kKeyNegInf &&
+                            kmx < F::kKeyPosInf;
+    o.mn = F::from(F::unkey(kmn));
+    o.mx = F::from(F::unkey(kmx));
+    const T r = F::half(F::sub(o.mx, o.mn));
+    o.mu = F::add(o.mn, r);
+    o.kind = kConst;
+    if (!exists) o.kind = 0xFF;
+    else if (!all_finite || !F::finite(F::bits(r)) || !F::finite(F::bits(o.mu))) o.kind = kRaw;
+    else if (!(within(o.mx, o.mu, e) && within(o.mn, o.mu, e))) o.kind = kNonConst;
+    int R = F::expo(F::bits(r)) - F::expo(F::bits(e));
+    o.R = R < 0 ? 0 : (R > F::M ? F::M : R);
+    o.req0 = 1 + F::E + o.R;
+    return o;
+}
+
+// A block's statistics as the tile's statistics warp hands them out (XS).
+template <typename T>
+struct XOut {
+    T mu;
+    int kind, req0;
+    bool check;
+};
+
+// XS: the block statistics come from xchg(kmn, kmx, XOut&) -- one warp
+// computes them for every block of the tile -- instead of from this lane;
+// false when that exchange ran out of time.
+template <typename T, int LPB, int VPL, bool FULL, bool XS, typename Xchg>
+__device__ __forceinline__ bool encode_lane(typename Fmt<T>::U (&x)[VPL], uint32_t (&codes)[(2 * VPL + 31) / 32],
                                             int &kind, int &req, int &req0, T &mu_out, uint32_t &mk_out,
                                             const typename Fmt<T>::U *src, int nvalid, bool exists, T e,
-                                            uint64_t e_bits, Workspace *ws, uint32_t tile) {
+                                            uint64_t e_bits, Workspace *ws, uint32_t tile, Xchg &&xchg) {
     using F = Fmt<T>;
     using U = typename F::U;
     using S = typename F::S;
@@ -294,22 +338,27 @@ __device__ __forceinline__ void encode_lane(typename Fmt<T>::U (&x)[VPL], uint32
         kmn = omn < kmn ? omn : kmn;
         kmx = omx > kmx ? omx : kmx;
     }
-    // a NaN's key lies above +inf (or, for f64 negative NaNs, below -inf)
-    const bool all_finite = kmn > F::kKeyNegInf && kmn < F::kKeyPosInf && kmx > F::kKeyNegInf &&
-                            kmx < F::kKeyPosInf;
-    const T mn = F::from(F::unkey(kmn)), mx = F::from(F::unkey(kmx));
-    const T r = F::half(F::sub(mx, mn));
-    const T mu = F::add(mn, r);
+    T mn, mx, mu;
+    int R = 0;
+    bool check_x = false;
+    if constexpr (XS) {
+        XOut<T> o;
+        if (!xchg(kmn, kmx, o)) return false;
+        mu = o.mu;
+        mn = mx = mu;  // used only by the block-level bound, already decided
+        kind = o.kind;
+        req0 = o.req0;
+        check_x = o.check;
+    } else {
+        const BlockStats<T> bs = block_stats<T>(kmn, kmx, exists, e);
+        mn = bs.mn;
+        mx = bs.mx;
+        mu = bs.mu;
+        kind = bs.kind;
+        R = bs.R;
+        req0 = bs.req0;
+    }
     mu_out = mu;
-
-    kind = kConst;
-    if (!exists) kind = 0xFF;
-    else if (!all_finite || !F::finite(F::bits(r)) || !F::finite(F::bits(mu))) kind = kRaw;
-    else if (!(within(mx, mu, e) && within(mn, mu, e))) kind = kNonConst;
-
-    int R = F::expo(F::bits(r)) - F::expo(F::bits(e));
-    R = R < 0 ? 0 : (R > F::M ? F::M : R);
-    req0 = 1 + F::E + R;
     req = req0;
     if (__all_sync(kFull, kind != kNonConst)) {
         // no block of the warp keeps truncated values (all constant, raw or
@@ -317,9 +366,9 @@ __device__ __forceinline__ void encode_lane(typename Fmt<T>::U (&x)[VPL], uint32
 #pragma unroll
         for (int i = 0; i < NCODE; ++i) codes[i] = 0;
         mk_out = kind == kRaw ? (uint32_t)nvalid * w : 0u;
-        return;
+        return true;
     }
-    const bool check = kind == kNonConst && bound_check_needed<T>(mn, mx, mu, R, (U)e_bits);
+    const bool check = XS ? check_x : kind == kNonConst && bound_check_needed<T>(mn, mx, mu, R, (U)e_bits);
 
     // truncation; with `check`, a fast test of every value (one rounding)
     bool ok = true;
@@ -453,6 +502,7 @@ __device__ __forceinline__ void encode_lane(typename Fmt<T>::U (&x)[VPL], uint32
     for (int i = 0; i < NCODE; ++i) suml += __popc(codes[i] & 0x55555555u) + 2 * __popc(codes[i] & 0xAAAAAAAAu);
     // this lane's mid bytes (raw: its verbatim bytes)
     mk_out = kind == kNonConst ? (uint32_t)(nvalid * q) - suml : (kind == kRaw ? (uint32_t)nvalid * w : 0u);
+    return true;
 }
 
 // Shared-memory layout of the compress kernel: kStages tile buffers (each
@@ -468,7 +518,7 @@ struct CSmem {
     uint32_t buf_stride, buf_bytes;  // tile buffer st at st * buf_stride (1024-aligned)
     uint32_t meta0, meta_stride;     // metadata block st at meta0 + st * meta_stride
     uint32_t m_kind, m_w;  // offsets inside a metadata block: block kinds, per-warp totals
-    uint32_t lut, total;
+    uint32_t lut, xs, total;
 };
 __host__ __device__ inline CSmem compress_smem(uint32_t G, uint32_t b, uint32_t w, uint32_t nw) {
     CSmem s;
@@ -489,7 +539,13 @@ __host__ __device__ inline CSmem compress_smem(uint32_t G, uint32_t b, uint32_t 
     s.meta_stride = (m + 15) & ~15u;
     s.meta0 = (kStages - 1) * s.buf_stride + s.buf_bytes;  // after the last buffer (16-aligned)
     s.lut = s.meta0 + kStages * s.meta_stride;
-    const uint32_t o = s.lut + 256 * 16;
+    uint32_t o = s.lut + 256 * 16;
+    // f64: the tile's block statistics exchange, 16 bytes a block
+    s.xs = 0;
+    if (w == 8) {
+        s.xs = (o + 15) & ~15u;
+        o = s.xs + 16 * G;
+    }
     s.total = ((o + 1023) & ~1023u) + 1024;  // + slack to realign the dynamic base
     return s;
 }
@@ -524,6 +580,9 @@ __global__ void __launch_bounds__(compress_threads(NW),
     // full: tile copied in; encoded: every consumer warp has its blocks'
     // totals in place; ready: record written; empty: record stored
     __shared__ __align__(8) uint64_t full[kStages], encoded[kStages], ready[kStages], empty[kStages];
+    // f64 (XS): the warps' block keys are in the exchange table; the block
+    // statistics are in it (per tile, in tile order)
+    __shared__ __align__(8) uint64_t keys_in, stats_out;
     // per stage: the field and its local tile (0xFFFFFFFF: no more tiles)
     __shared__ uint32_t st_field[kStages], st_tile[kStages], st_rec[kStages];
 
@@ -550,6 +609,8 @@ __global__ void __launch_bounds__(compress_threads(NW),
             mbar_init(&ready[i], kConsumerWarps);
             mbar_init(&empty[i], 1);
         }
+        mbar_init(&keys_in, kConsumerWarps);
+        mbar_init(&stats_out, 1);
         fence_mbar_init();
         for (int i = 0; i < kStages; ++i) {
             st_tile[i] = 0xFFFFFFFFu;
@@ -882,12 +943,59 @@ __global__ void __launch_bounds__(compress_threads(NW),
             int kind, req, req0;
             T mu;
             uint32_t mk_lane;
+            // f64 with 128 <= b <= 512: the block statistics of the whole tile
+            // on warp 0, in one pass over its blocks (an FP64 instruction
+            // costs a warp's issue whatever lanes it runs on, and a warp holds
+            // only 4 blocks or fewer); the other warps wait for them.  At b =
+            // 64 warp 0 needs two passes, and at b = 1024 (one CTA per SM)
+            // nothing hides the wait: both are slower that way.
+            constexpr bool XS = sizeof(T) == 8 && LPB * VPL >= 128 && LPB * VPL <= 512;
+            const uint32_t xpar = it & 1u;  // the exchange barriers' phase: one per tile
+            auto xchg = [&](typename F::S kmn, typename F::S kmx, XOut<T> &o) -> bool {
+                longlong2 *xt = reinterpret_cast<longlong2 *>(smem + L.xs);
+                if (exists && sub == 0) xt[blk] = make_longlong2((long long)kmn, (long long)kmx);
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&keys_in);
+                if (warp == 0) {
+                    if (!mbar_wait_bounded(&keys_in, xpar, lc.copy_ns)) return false;
+                    for (uint32_t i = (uint32_t)lane; i < G; i += 32) {
+                        const longlong2 v = xt[i];
+                        const BlockStats<T> bs =
+                            block_stats<T>((typename F::S)v.x, (typename F::S)v.y, FT || i < Gt, e);
+                        const bool chk = bs.kind == kNonConst &&
+                                         bound_check_needed<T>(bs.mn, bs.mx, bs.mu, bs.R, (U)Fd->e_bits);
+                        xt[i] = make_longlong2((long long)F::bits(bs.mu),
+                                               (long long)((uint32_t)bs.kind | ((uint32_t)bs.req0 << 8) |
+                                                           ((uint32_t)chk << 16)));
+                    }
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&stats_out);
+                }
+                if (!mbar_wait_bounded(&stats_out, xpar, lc.copy_ns)) return false;
+                const longlong2 v = xt[blk];
+                const uint32_t m = (uint32_t)v.y;
+                o.mu = F::from((U)v.x);
+                o.kind = exists ? (int)(m & 0xFFu) : 0xFF;
+                o.req0 = (int)((m >> 8) & 0xFFu);
+                o.check = ((m >> 16) & 1u) != 0u;
+                return true;
+            };
+            bool encoded_ok;
             if (FT || __all_sync(kFull, full_lane)) {
-                encode_lane<T, LPB, VPL, true>(x, codes, kind, req, req0, mu, mk_lane, src, nvalid, exists, e,
-                                               Fd->e_bits, Fd->ws, tile);
+                encoded_ok = encode_lane<T, LPB, VPL, true, XS>(x, codes, kind, req, req0, mu, mk_lane, src, nvalid,
+                                                                exists, e, Fd->e_bits, Fd->ws, tile, xchg);
             } else {
-                encode_lane<T, LPB, VPL, false>(x, codes, kind, req, req0, mu, mk_lane, src, nvalid, exists, e,
-                                                Fd->e_bits, Fd->ws, tile);
+                encoded_ok = encode_lane<T, LPB, VPL, false, XS>(x, codes, kind, req, req0, mu, mk_lane, src,
+                                                                 nvalid, exists, e, Fd->e_bits, Fd->ws, tile, xchg);
+            }
+            if (!encoded_ok) {
+                // the statistics exchange ran out of time: give up on the tile
+                if (lane == 0) {
+                    atomicOr(lc.err, kErrTimeout);
+                    st_tile[st] = 0xFFFFFFFFu;
+                    mbar_arrive(&ready[st]);
+                }
+                return false;
             }
             const bool lead = exists && sub == 0;  // the block's first lane
             if (lead) {
