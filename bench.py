@@ -19,6 +19,10 @@ arm time the CPU oracle on the same fixed slice of the field, one process per
 host core on disjoint block ranges (and one thread beside it).  With N > 1
 (torchrun) every rank codes its own field (independent problems: weak
 scaling, no collective on the data path).
+
+Other workloads (--workload): batch96, serve, dump, grf384f64, blocksweep (b =
+32 ... 1024 on the headline field) and relsweep (the headline field at rel
+1e-2, 1e-3 and 1e-4, and its lognormal variant at 1e-3).
 """
 import argparse
 import json
@@ -742,6 +746,58 @@ def run_dump(args, world, rank, local):
     return 0
 
 
+def _sweep_row(x, eb, b, args):
+    """Time compress_async / decompress_async of x at bound eb and block b
+    (warm-up, then the median of the steps, queued as in the headline loop),
+    check the decode against the bound, and return the row's rates, ratio,
+    PSNR and block counts."""
+    import torch
+
+    import paper_2201_13020_b300 as szx
+    from paper_2201_13020_b300 import metrics
+    n = x.numel()
+    stream = torch.cuda.current_stream()
+    out = torch.empty(szx.compress_bound(n, szx.SZX_F32, b), dtype=torch.uint8, device="cuda")
+    res = torch.zeros(2, dtype=torch.int64, device="cuda")
+    s0 = szx.compress(x, eb, b, out=out)
+    nbytes = s0.numel()
+    h = szx.header(out[:nbytes])
+    y = torch.empty_like(x)
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    for _ in range(args.warmup):
+        szx.compress_async(x, eb, b, out, res)
+        szx.decompress_async(out[:nbytes], h, y, st)
+    torch.cuda.synchronize()
+    # as in the headline loop: every timed step queued behind the clock-bounded
+    # sleep, so that no host launch gap falls between a step's events
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    queue_ahead(stream, args.steps)
+    for e in ev:
+        e[0].record(stream)
+        szx.compress_async(x, eb, b, out, res)
+        e[1].record(stream)
+        szx.decompress_async(out[:nbytes], h, y, st)
+        e[2].record(stream)
+    torch.cuda.synchronize()
+    tc = [e[0].elapsed_time(e[1]) for e in ev]
+    td = [e[1].elapsed_time(e[2]) for e in ev]
+    if int(st.item()) or int(res[1].item()):
+        raise RuntimeError(f"block {b}: status {int(res[1].item())}/{int(st.item())}")
+    err = float((y.double() - x.double()).abs().max())
+    if err > eb:
+        raise RuntimeError(f"block {b}: error {err} > {eb}")
+    nb = -(-n // b)
+    peak, _ = peaks()
+    alg = n * 4 + nbytes
+    tcm, tdm = statistics.median(tc) * 1e-3, statistics.median(td) * 1e-3
+    return {"compress_gbs": n * 4 / tcm / 1e9, "decompress_gbs": n * 4 / tdm / 1e9,
+            "compress_us": tcm * 1e6, "decompress_us": tdm * 1e6,
+            "hbm_frac_algorithmic": {"compress": alg / tcm / 1e9 / peak, "decompress": alg / tdm / 1e9 / peak},
+            "cr": n * 4 / nbytes, "psnr_db": metrics.psnr(x, y),
+            "constant_fraction": 1.0 - h.nonconst / nb, "raw_blocks": h.raw,
+            "escalated_blocks": h.escalated}
+
+
 def run_blocksweep(args, world, rank, local):
     """Block length sweep on the 512^3 f32 field at rel 1e-3 (Sec. V-A.2's
     study, Fig. 7, on synthetic data): per b, compress and decompress rates,
@@ -749,46 +805,11 @@ def run_blocksweep(args, world, rank, local):
     block length that block=0 picks."""
     import torch
 
-    import paper_2201_13020_b300 as szx
     from paper_2201_13020_b300 import inputs, metrics
     torch.cuda.set_device(local)
     x = make_field("cuda", seed=2 + rank)
     eb = inputs.rel_to_abs(x, REL)
-    n = x.numel()
-    stream = torch.cuda.current_stream()
-    rows = {}
-    for b in (32, 64, 128, 256, 512, 1024):
-        out = torch.empty(szx.compress_bound(n, szx.SZX_F32, b), dtype=torch.uint8, device="cuda")
-        res = torch.zeros(2, dtype=torch.int64, device="cuda")
-        s0 = szx.compress(x, eb, b, out=out)
-        nbytes = s0.numel()
-        h = szx.header(out[:nbytes])
-        y = torch.empty_like(x)
-        st = torch.zeros(1, dtype=torch.int32, device="cuda")
-        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
-        tc, td = [], []
-        for i in range(args.warmup + args.steps):
-            ev[0].record(stream)
-            szx.compress_async(x, eb, b, out, res)
-            ev[1].record(stream)
-            szx.decompress_async(out[:nbytes], h, y, st)
-            ev[2].record(stream)
-            torch.cuda.synchronize()
-            if i >= args.warmup:
-                tc.append(ev[0].elapsed_time(ev[1]))
-                td.append(ev[1].elapsed_time(ev[2]))
-        if int(st.item()) or int(res[1].item()):
-            raise RuntimeError(f"block {b}: status {int(res[1].item())}/{int(st.item())}")
-        err = float((y.double() - x.double()).abs().max())
-        if err > eb:
-            raise RuntimeError(f"block {b}: error {err} > {eb}")
-        nb = -(-n // b)
-        rows[b] = {"compress_gbs": n * 4 / (statistics.median(tc) * 1e-3) / 1e9,
-                   "decompress_gbs": n * 4 / (statistics.median(td) * 1e-3) / 1e9,
-                   "cr": n * 4 / nbytes, "psnr_db": metrics.psnr(x, y),
-                   "constant_fraction": 1.0 - h.nonconst / nb, "raw_blocks": h.raw,
-                   "escalated_blocks": h.escalated}
-        del out, y
+    rows = {b: _sweep_row(x, eb, b, args) for b in (32, 64, 128, 256, 512, 1024)}
     pick, sample_cr = metrics.choose_block(x, eb)
     if rank == 0:
         line = {"metric": METRIC, "value": rows[128]["compress_gbs"], "unit": "GB/s", "n_gpus": world,
@@ -796,6 +817,36 @@ def run_blocksweep(args, world, rank, local):
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": {"workload": "blocksweep_grf512_f32_rel1e-3", "parallelism": f"replicas{world}"},
                 "blocks": rows, "block0_choice": pick, "block0_sample_cr": sample_cr,
+                "gpu": torch.cuda.get_device_name(local)}
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_relsweep(args, world, rank, local):
+    """The 512^3 f32 field at value-range bounds 1e-2, 1e-3 and 1e-4, and its
+    lognormal variant (exp(1.5 g), the same zero slabs) at 1e-3, all at b =
+    128: per case compress and decompress rates, the algorithmic HBM
+    fractions, compression ratio, Eq. 7 PSNR and the block counts."""
+    import torch
+
+    from paper_2201_13020_b300 import inputs
+    torch.cuda.set_device(local)
+    rows = {}
+    x = make_field("cuda", seed=2 + rank)
+    for rel in (1e-2, 1e-3, 1e-4):
+        rows[f"grf_rel{rel:g}"] = _sweep_row(x, inputs.rel_to_abs(x, rel), BLOCK, args)
+    del x
+    g = inputs.grf_3d(tuple(SHAPE_RUN), -5.0 / 3.0, seed=2 + rank, device="cuda")
+    g = inputs.zero_slabs(inputs.lognormal(g), 0.25, 32, seed=2 + rank)
+    x = g.reshape(-1).contiguous()
+    del g
+    rows["lognormal_rel0.001"] = _sweep_row(x, inputs.rel_to_abs(x, 1e-3), BLOCK, args)
+    if rank == 0:
+        line = {"metric": METRIC, "value": rows["grf_rel0.001"]["compress_gbs"], "unit": "GB/s",
+                "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": "relsweep_grf512_f32_block128", "parallelism": f"replicas{world}"},
+                "peak": "hbm_gbs %s of %s" % peaks(), "rows": rows,
                 "gpu": torch.cuda.get_device_name(local)}
         print(json.dumps(line), flush=True)
     return 0
@@ -898,7 +949,7 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=600, help="requests of the serve sub-object")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--size", type=int, default=512, help="cube edge (default 512; smaller only for captures)")
-    ap.add_argument("--workload", default="grf512", choices=["grf512", "batch96", "serve", "dump", "blocksweep", "grf384f64"],
+    ap.add_argument("--workload", default="grf512", choices=["grf512", "batch96", "serve", "dump", "blocksweep", "relsweep", "grf384f64"],
                     help="grf512: the 512^3 f32 field (default); batch96: 96 mixed fields, batched vs plain; "
                          "serve: Poisson request mix through the serving loop; dump: compressed dump to a file")
     ap.add_argument("--dump-dir", default=None, help="dump: directory of the dump file (default: the temp dir)")
@@ -921,6 +972,8 @@ def main():
         return run_blocksweep(args, world, rank, local)
     if args.workload == "grf384f64":
         return run_grf384f64(args, world, rank, local)
+    if args.workload == "relsweep":
+        return run_relsweep(args, world, rank, local)
 
     import numpy as np
     import torch
