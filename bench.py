@@ -523,7 +523,9 @@ def measure_batch96(args, rank, count=96):
                                     "decompress": alg / (best["decompress_ms"] * 1e-3) / 1e9 / peak,
                                     "peak": f"hbm_gbs {peak} of {peak_kind}"},
            "autotune": {"compress": tuned_c, "decompress": tuned_d},
-           "steps": args.steps, "gpu_launches": args.steps * (len(tuned_c) + len(tuned_d)),
+           "steps": args.steps,
+           # per step and plan: the run's clear kernel and one launch per group
+           "gpu_launches": args.steps * (2 + len(tuned_c) + len(tuned_d)),
            "wall_s": time.perf_counter() - t_start}
     del graphs, batch, dbatch, b_out, d_ys, p_out, ys, xs, fields
     torch.cuda.empty_cache()

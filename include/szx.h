@@ -228,9 +228,10 @@ szx_status szx_decompress_async(const void *d_in, size_t in_bytes,
  * Life cycle: plan (host only) -> szx_batch_workspace_bytes -> szx_batch_upload
  * (writes the plan's descriptor tables into the caller's device workspace;
  * synchronous on `stream`) -> szx_batch_run any number of times (enqueues one
- * memset of the plan's counters, for decompression one more per stream status
- * word, and one persistent kernel launch per (dtype, block) group, no host
- * synchronisation; the same sequence can be captured in a CUDA graph) ->
+ * small kernel that clears the plan's counters and, for decompression, every
+ * stream's status word, then one persistent kernel launch per (dtype, block)
+ * group, no host synchronisation; the same sequence can be captured in a CUDA
+ * graph) ->
  * szx_batch_destroy.  A plan remembers the workspace it was uploaded to;
  * running it with another one returns SZX_ERR_INVALID.  Buffers named in the
  * fields must stay valid while the plan is run; runs of one plan must not

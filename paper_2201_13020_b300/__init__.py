@@ -149,7 +149,7 @@ def decompress_range(buf, first_block, nblocks, h=None, out=None, status=None, s
 class Batch:
     """A planned batch (see szx_batch_* in include/szx.h) with its device workspace.
 
-    run() enqueues one run (one memset and one persistent launch per
+    run() enqueues one run (one clear kernel and one persistent launch per
     (dtype, block) group) on the stream; it can be captured in a CUDA graph.
     """
 

@@ -10,9 +10,10 @@
 //   uses the ticket only),
 //   per-field compression workspaces (counters + look-back words, 256-byte
 //   aligned; compression only).
-// Running a plan is one cudaMemsetAsync (counters and workspaces) plus one
-// kernel launch per group, so it can be captured in a CUDA graph once the
-// tables are uploaded.  The autotuner times each group alone on the plan's own
+// Running a plan is one clear kernel (counters, workspaces and, for
+// decompression, every stream's status word) plus one kernel launch per group,
+// each the programmatic dependent of the kernel before it, so it can be
+// captured in a CUDA graph once the tables are uploaded.  The autotuner times each group alone on the plan's own
 // data in every shape the kernels have -- consumer warps per CTA (8, or 4 with
 // twice the values per lane and blocks per warp) times CTAs per SM (2 or 1) --
 // and keeps the fastest; the stream is the same in every shape.  For a group
@@ -34,6 +35,22 @@
 using namespace szx;
 
 namespace {
+
+// A run's state cleared in one kernel: n words at `words` (the plan's counters
+// and, for compression, the fields' workspaces) and, for decompression, the
+// status word of each of the nfields descriptors at `fields` (device memory).
+// The first group's launch follows it as its programmatic dependent.
+__global__ void clear_run_kernel(uint32_t *words, uint64_t n, const DField *fields, uint32_t nfields) {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    const uint64_t i0 = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    for (uint64_t i = i0; i < n; i += stride) words[i] = 0u;
+    if (fields)
+        for (uint64_t i = i0; i < nfields; i += stride) {
+            uint32_t *st = fields[i].status;
+            if (st) *st = 0u;
+        }
+}
 
 struct Group {
     int dtype;
@@ -242,13 +259,18 @@ szx_status szx_batch_run(const szx_batch_plan *p, void *d_ws, szx_stream_t strea
     if (d_ws != p->uploaded_ws) return SZX_ERR_INVALID;  // the tables point into that workspace
     cudaStream_t s = (cudaStream_t)stream;
     uint8_t *base = static_cast<uint8_t *>(d_ws);
-    // counters (and, for compression, the fields' workspaces) start at zero
-    if (cudaMemsetAsync(base + p->zero_off, 0, p->total_bytes - p->zero_off, s) != cudaSuccess) return SZX_ERR_CUDA;
-    if (!p->compress) {
-        // every stream's status word starts at SZX_OK
-        for (const szx_stream_field &sf : p->streams)
-            if (sf.d_status && cudaMemsetAsync(sf.d_status, 0, sizeof(uint32_t), s) != cudaSuccess)
-                return SZX_ERR_CUDA;
+    // counters (and, for compression, the fields' workspaces) start at zero,
+    // and so does every stream's status word (SZX_OK); the region is a whole
+    // number of 256-byte units
+    {
+        const uint64_t nwords = (p->total_bytes - p->zero_off) / 4;
+        const uint32_t nst = p->compress ? 0u : (uint32_t)p->streams.size();
+        const uint64_t items = nwords > nst ? nwords : nst;
+        const uint64_t ctas = std::min<uint64_t>((items + 255) / 256, 4 * 148);
+        clear_run_kernel<<<(unsigned)(ctas ? ctas : 1), 256, 0, s>>>(
+            reinterpret_cast<uint32_t *>(base + p->zero_off), nwords,
+            p->compress ? nullptr : reinterpret_cast<const DField *>(base), nst);
+        if (cudaGetLastError() != cudaSuccess) return SZX_ERR_CUDA;
     }
     for (size_t gi = 0; gi < p->groups.size(); ++gi) {
         const Group &g = p->groups[gi];
@@ -256,11 +278,12 @@ szx_status szx_batch_run(const szx_batch_plan *p, void *d_ws, szx_stream_t strea
         if (p->compress) {
             const CField *tbl = reinterpret_cast<const CField *>(base) + g.first;
             uint32_t *ctr = reinterpret_cast<uint32_t *>(base + p->counters_off + 16 * gi);
-            e = launch_compress_batch(tbl, g.count, g.tiles, ctr, g.dtype, g.block, g.ctas_per_sm, g.nw, s);
+            e = launch_compress_batch(tbl, g.count, g.tiles, ctr, g.dtype, g.block, g.ctas_per_sm, g.nw, true, s);
         } else {
             const DField *tbl = reinterpret_cast<const DField *>(base) + g.first;
             uint32_t *ticket = reinterpret_cast<uint32_t *>(base + p->counters_off + 16 * gi);
-            e = launch_decompress_batch(tbl, g.count, g.tiles, ticket, g.dtype, g.block, g.ctas_per_sm, g.nw, s);
+            e = launch_decompress_batch(tbl, g.count, g.tiles, ticket, g.dtype, g.block, g.ctas_per_sm, g.nw, true,
+                                        s);
         }
         if (e != cudaSuccess) return SZX_ERR_CUDA;
     }

@@ -1351,7 +1351,7 @@ cudaError_t launch_compress_ws(const void *in, uint64_t n, int dtype, uint64_t e
 }
 
 cudaError_t launch_compress_batch(const void *d_fields, uint32_t nfields, uint64_t total_tiles, uint32_t *d_counters,
-                                  int dtype, uint32_t block, int ctas_per_sm, int nw, cudaStream_t stream) {
+                                  int dtype, uint32_t block, int ctas_per_sm, int nw, bool pdl, cudaStream_t stream) {
     CField one;
     std::memset(&one, 0, sizeof(one));
     CompressLaunch lc;
@@ -1363,7 +1363,7 @@ cudaError_t launch_compress_batch(const void *d_fields, uint32_t nfields, uint64
     lc.err = d_counters + 2;
     lc.lookback_ns = 1000ull * wait_limit_from_env("SZX_LOOKBACK_US", 1000000u);
     lc.copy_ns = 1000ull * wait_limit_from_env("SZX_COPY_US", 1000000u);
-    return dispatch(dtype, block, nw, one, lc, ctas_per_sm, false, stream);
+    return dispatch(dtype, block, nw, one, lc, ctas_per_sm, pdl, stream);
 }
 
 // ---------------------------------------------------------------------------

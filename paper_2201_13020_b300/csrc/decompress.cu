@@ -976,7 +976,8 @@ cudaError_t launch_decompress(const void *in, uint64_t in_bytes, uint64_t total_
 }
 
 cudaError_t launch_decompress_batch(const void *d_fields, uint32_t nfields, uint64_t total_tiles, uint32_t *d_ticket,
-                                    int dtype, uint32_t block, int ctas_per_sm, int nw, cudaStream_t stream) {
+                                    int dtype, uint32_t block, int ctas_per_sm, int nw, bool pdl,
+                                    cudaStream_t stream) {
     DField one;
     std::memset(&one, 0, sizeof(one));
     DecompressLaunch lc;
@@ -985,7 +986,7 @@ cudaError_t launch_decompress_batch(const void *d_fields, uint32_t nfields, uint
     lc.total_tiles = total_tiles;
     lc.copy_ns = copy_limit_ns();
     lc.ticket = d_ticket;
-    return ddispatch(dtype, block, nw, one, lc, ctas_per_sm, false, stream);
+    return ddispatch(dtype, block, nw, one, lc, ctas_per_sm, pdl, stream);
 }
 
 }  // namespace szx

@@ -77,9 +77,10 @@ void fill_compress_field(CField *f, const void *in, uint64_t n, int dtype, uint6
 // d_fields (device memory, 64-byte aligned; all of dtype and block), whose
 // tiles number total_tiles.  d_counters: 3 zeroed words (ticket, done, error
 // bits).  ctas_per_sm: 0 = as many as fit, else at most that many.  nw: the
-// consumer warps per CTA, 8 or 4 (0 = 8; see kernel_shape_ok).
+// consumer warps per CTA, 8 or 4 (0 = 8; see kernel_shape_ok).  pdl: launch
+// as the programmatic dependent of the kernel before it (launch_kernel).
 cudaError_t launch_compress_batch(const void *d_fields, uint32_t nfields, uint64_t total_tiles, uint32_t *d_counters,
-                                  int dtype, uint32_t block, int ctas_per_sm, int nw, cudaStream_t stream);
+                                  int dtype, uint32_t block, int ctas_per_sm, int nw, bool pdl, cudaStream_t stream);
 
 // Whether the kernels have an instance with nw consumer (decoding) warps for
 // this dtype and block: 8 always; 4 where a block covers whole lanes of 64
@@ -108,7 +109,8 @@ uint64_t decompress_field_tiles(const DField *f);
 // take tiles by ticket from *d_ticket (device memory, zero before the launch),
 // or, if d_ticket is null, by a static split.
 cudaError_t launch_decompress_batch(const void *d_fields, uint32_t nfields, uint64_t total_tiles, uint32_t *d_ticket,
-                                    int dtype, uint32_t block, int ctas_per_sm, int nw, cudaStream_t stream);
+                                    int dtype, uint32_t block, int ctas_per_sm, int nw, bool pdl,
+                                    cudaStream_t stream);
 
 // Enqueue the decompression of a stream of total_bytes whose header says
 // (n, dtype, block).  *d_status is zeroed on `stream` first (launch_clear_words;
