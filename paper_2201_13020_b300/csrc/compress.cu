@@ -29,7 +29,7 @@
 //      the record), then encodes in registers -- block statistics
 //      (Algorithm 1): NaN-propagating min/max per lane, reduced over the
 //      block's lanes with shuffles; mu, r, the exact constant test, reqBits
-//      (Eq. 4) -- for f64 with 128 <= b <= 512 computed by warp 0 for every
+//      (Eq. 4) -- for one f64 field with 128 <= b <= 512 computed by warp 0 for every
 //      block of the tile from the keys the warps hand in through shared
 //      memory -- then the Eq. 5 shift and truncation.  The per-value bound check is
 //      skipped when a block-level bound proves it passes (see
@@ -943,13 +943,14 @@ __global__ void __launch_bounds__(compress_threads(NW),
             int kind, req, req0;
             T mu;
             uint32_t mk_lane;
-            // f64 with 128 <= b <= 512: the block statistics of the whole tile
-            // on warp 0, in one pass over its blocks (an FP64 instruction
-            // costs a warp's issue whatever lanes it runs on, and a warp holds
-            // only 4 blocks or fewer); the other warps wait for them.  At b =
-            // 64 warp 0 needs two passes, and at b = 1024 (one CTA per SM)
-            // nothing hides the wait: both are slower that way.
-            constexpr bool XS = sizeof(T) == 8 && LPB * VPL >= 128 && LPB * VPL <= 512;
+            // f64 with 128 <= b <= 512, one field: the block statistics of the
+            // whole tile on warp 0, in one pass over its blocks (an FP64
+            // instruction costs a warp's issue whatever lanes it runs on, and a
+            // warp holds only 4 blocks or fewer); the other warps wait for
+            // them.  At b = 64 warp 0 needs two passes, at b = 1024 (one CTA
+            // per SM) nothing hides the wait, and the batch instances spill
+            // registers with it: all three are slower that way.
+            constexpr bool XS = !BATCH && sizeof(T) == 8 && LPB * VPL >= 128 && LPB * VPL <= 512;
             const uint32_t xpar = it & 1u;  // the exchange barriers' phase: one per tile
             auto xchg = [&](typename F::S kmn, typename F::S kmx, XOut<T> &o) -> bool {
                 longlong2 *xt = reinterpret_cast<longlong2 *>(smem + L.xs);
