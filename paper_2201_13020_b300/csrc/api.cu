@@ -148,6 +148,33 @@ uint32_t szx::wait_limit_from_env(const char *name, uint32_t fallback) {
     return (uint32_t)x;
 }
 
+namespace szx {
+
+szx_status compress_async_with(const void *d_in, size_t n, szx_dtype dtype, double eb, uint32_t block, void *d_out,
+                               size_t out_capacity, uint64_t *d_result, szx_stream_t stream, Clear clear) {
+    szx_status st = check_compress_args(d_in, n, dtype, eb, block, d_out, out_capacity);
+    if (st != SZX_OK) return st;
+    const uint64_t ws = align256(stream_max(n, block, width(dtype)));
+    return from_cuda(launch_compress(d_in, n, (int)dtype, bound_bits(eb, dtype), block, d_out, ws, d_result,
+                                     (cudaStream_t)stream, clear));
+}
+
+szx_status decompress_async_with(const void *d_in, size_t in_bytes, const szx_header *h, void *d_out,
+                                 size_t out_capacity, uint32_t *d_status, szx_stream_t stream, Clear clear) {
+    if (!d_in || !h || !d_out) return SZX_ERR_INVALID;
+    if (!aligned16(d_in) || !aligned16(d_out)) return SZX_ERR_INVALID;
+    if (!dtype_ok(h->dtype) || !block_ok(h->block) || h->n == 0 || h->n > kMaxValues) return SZX_ERR_INVALID;
+    if (h->tile_blocks != tile_blocks(h->block, width(h->dtype))) return SZX_ERR_INVALID;
+    const Geometry g = make_geometry(h->n, h->block, width(h->dtype));
+    if (h->total_bytes > in_bytes || h->total_bytes < g.off_rec) return SZX_ERR_CORRUPT;
+    if (out_capacity < h->n * width(h->dtype)) return SZX_ERR_TOO_SMALL;
+    cudaStream_t s = (cudaStream_t)stream;
+    return from_cuda(launch_decompress(d_in, in_bytes, h->total_bytes, h->n, (int)h->dtype, h->block, d_out,
+                                       d_status, true, s, 0, ~0ull, clear));
+}
+
+}  // namespace szx
+
 extern "C" {
 
 size_t szx_stream_max_bytes(size_t n, szx_dtype dtype, uint32_t block) {
@@ -164,11 +191,7 @@ size_t szx_compress_bound(size_t n, szx_dtype dtype, uint32_t block) {
 
 szx_status szx_compress_async(const void *d_in, size_t n, szx_dtype dtype, double eb, uint32_t block,
                               void *d_out, size_t out_capacity, uint64_t *d_result, szx_stream_t stream) {
-    szx_status st = check_compress_args(d_in, n, dtype, eb, block, d_out, out_capacity);
-    if (st != SZX_OK) return st;
-    const uint64_t ws = align256(stream_max(n, block, width(dtype)));
-    return from_cuda(launch_compress(d_in, n, (int)dtype, bound_bits(eb, dtype), block, d_out, ws, d_result,
-                                     (cudaStream_t)stream));
+    return compress_async_with(d_in, n, dtype, eb, block, d_out, out_capacity, d_result, stream, Clear::kernel);
 }
 
 szx_status szx_compress(const void *d_in, size_t n, szx_dtype dtype, double eb, uint32_t block, void *d_out,
@@ -200,16 +223,7 @@ szx_status szx_header_read(const void *d_in, size_t in_bytes, szx_header *h, szx
 
 szx_status szx_decompress_async(const void *d_in, size_t in_bytes, const szx_header *h, void *d_out,
                                 size_t out_capacity, uint32_t *d_status, szx_stream_t stream) {
-    if (!d_in || !h || !d_out) return SZX_ERR_INVALID;
-    if (!aligned16(d_in) || !aligned16(d_out)) return SZX_ERR_INVALID;
-    if (!dtype_ok(h->dtype) || !block_ok(h->block) || h->n == 0 || h->n > kMaxValues) return SZX_ERR_INVALID;
-    if (h->tile_blocks != tile_blocks(h->block, width(h->dtype))) return SZX_ERR_INVALID;
-    const Geometry g = make_geometry(h->n, h->block, width(h->dtype));
-    if (h->total_bytes > in_bytes || h->total_bytes < g.off_rec) return SZX_ERR_CORRUPT;
-    if (out_capacity < h->n * width(h->dtype)) return SZX_ERR_TOO_SMALL;
-    cudaStream_t s = (cudaStream_t)stream;
-    return from_cuda(launch_decompress(d_in, in_bytes, h->total_bytes, h->n, (int)h->dtype, h->block, d_out,
-                                       d_status, true, s));
+    return decompress_async_with(d_in, in_bytes, h, d_out, out_capacity, d_status, stream, Clear::kernel);
 }
 
 szx_status szx_decompress_range_async(const void *d_in, size_t in_bytes, const szx_header *h, size_t first_block,

@@ -1307,9 +1307,9 @@ cudaError_t dispatch(int dtype, uint32_t block, int nw, const CField &one, const
 }  // namespace
 
 cudaError_t launch_compress(const void *in, uint64_t n, int dtype, uint64_t e_bits, uint32_t block,
-                            void *out, uint64_t ws_offset, uint64_t *d_result, cudaStream_t stream) {
+                            void *out, uint64_t ws_offset, uint64_t *d_result, cudaStream_t stream, Clear clear) {
     return launch_compress_ws(in, n, dtype, e_bits, block, out, static_cast<uint8_t *>(out) + ws_offset,
-                              d_result, stream);
+                              d_result, stream, clear);
 }
 
 void fill_compress_field(CField *f, const void *in, uint64_t n, int dtype, uint64_t e_bits, uint32_t block,
@@ -1331,7 +1331,7 @@ void fill_compress_field(CField *f, const void *in, uint64_t n, int dtype, uint6
 }
 
 cudaError_t launch_compress_ws(const void *in, uint64_t n, int dtype, uint64_t e_bits, uint32_t block,
-                               void *out, void *ws, uint64_t *d_result, cudaStream_t stream) {
+                               void *out, void *ws, uint64_t *d_result, cudaStream_t stream, Clear clear) {
     CField one;
     fill_compress_field(&one, in, n, dtype, e_bits, block, out, ws, d_result, 0);
     Workspace *w = reinterpret_cast<Workspace *>(ws);
@@ -1345,7 +1345,13 @@ cudaError_t launch_compress_ws(const void *in, uint64_t n, int dtype, uint64_t e
     lc.lookback_ns = 1000ull * wait_limit_from_env("SZX_LOOKBACK_US", 1000000u);
     lc.copy_ns = 1000ull * wait_limit_from_env("SZX_COPY_US", 1000000u);
     // the counters and look-back flags start at zero (workspace_bytes is a
-    // multiple of 8); the kernel starts behind the clear
+    // multiple of 8)
+    if (clear == Clear::memset) {
+        const cudaError_t err = cudaMemsetAsync(ws, 0, workspace_bytes(one.g.ntiles), stream);
+        if (err != cudaSuccess) return err;
+        return dispatch(dtype, block, 8, one, lc, 0, false, stream);
+    }
+    // the kernel starts behind the clear
     cudaError_t err = launch_clear_words(static_cast<uint32_t *>(ws), workspace_bytes(one.g.ntiles) / 4, stream);
     if (err != cudaSuccess) return err;
     return dispatch(dtype, block, 8, one, lc, 0, true, stream);

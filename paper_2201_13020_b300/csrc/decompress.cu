@@ -956,7 +956,7 @@ uint64_t decompress_field_tiles(const DField *f) {
 
 cudaError_t launch_decompress(const void *in, uint64_t in_bytes, uint64_t total_bytes, uint64_t n, int dtype,
                               uint32_t block, void *out, uint32_t *d_status, bool check_header,
-                              cudaStream_t stream, uint64_t blk_lo, uint64_t blk_hi) {
+                              cudaStream_t stream, uint64_t blk_lo, uint64_t blk_hi, Clear clear) {
     (void)in_bytes;
     DField one;
     fill_decompress_field(&one, in, total_bytes, n, dtype, block, out, d_status, check_header, 0, blk_lo, blk_hi);
@@ -964,15 +964,17 @@ cudaError_t launch_decompress(const void *in, uint64_t in_bytes, uint64_t total_
     lc.fields = nullptr;
     lc.nfields = 1;
     lc.total_tiles = decompress_field_tiles(&one);
-    // the status starts at zero; the kernel starts behind the clear
+    // the status starts at zero; with the clear kernel, the decoder starts
+    // behind it
     if (d_status) {
-        const cudaError_t err = launch_clear_words(d_status, 1, stream);
+        const cudaError_t err = clear == Clear::memset ? cudaMemsetAsync(d_status, 0, sizeof(uint32_t), stream)
+                                                       : launch_clear_words(d_status, 1, stream);
         if (err != cudaSuccess) return err;
     }
     if (!lc.total_tiles) return cudaSuccess;
     lc.copy_ns = copy_limit_ns();
     lc.ticket = nullptr;  // no device workspace here: the static split
-    return ddispatch(dtype, block, 8, one, lc, 0, d_status != nullptr, stream);
+    return ddispatch(dtype, block, 8, one, lc, 0, d_status != nullptr && clear == Clear::kernel, stream);
 }
 
 cudaError_t launch_decompress_batch(const void *d_fields, uint32_t nfields, uint64_t total_tiles, uint32_t *d_ticket,

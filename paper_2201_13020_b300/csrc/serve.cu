@@ -17,6 +17,7 @@
 // bookkeeping of its free ranges (first fit, 256-byte granules, coalescing).
 #include "szx.h"
 #include "szx_device.cuh"
+#include "szx_launch.h"
 
 #include <algorithm>
 #include <chrono>
@@ -266,12 +267,14 @@ szx_status szx_server_run(szx_server *s, szx_request *reqs, int count, int *max_
             if (r.kind == SZX_REQ_COMPRESS) {
                 s->h_results[2 * slot] = 0;
                 s->h_results[2 * slot + 1] = (uint64_t)SZX_ERR_CUDA;
-                ls = szx_compress_async(r.d_in, r.n, r.dtype, r.eb, r.block, s->pool + off, granules(need),
-                                        s->d_results + 2 * slot, (szx_stream_t)st);
+                // the slots' streams run at once: each call clears its words
+                // with a memset node rather than a kernel (Clear::memset)
+                ls = compress_async_with(r.d_in, r.n, r.dtype, r.eb, r.block, s->pool + off, granules(need),
+                                         s->d_results + 2 * slot, (szx_stream_t)st, Clear::memset);
             } else {
                 const szx_request &src = reqs[r.source];
-                ls = szx_decompress_async(s->pool + src.offset, src.bytes, &h, s->pool + off, need,
-                                          s->d_status + slot, (szx_stream_t)st);
+                ls = decompress_async_with(s->pool + src.offset, src.bytes, &h, s->pool + off, need,
+                                           s->d_status + slot, (szx_stream_t)st, Clear::memset);
                 if (ls == SZX_OK &&
                     cudaMemcpyAsync(s->h_status + slot, s->d_status + slot, sizeof(uint32_t),
                                     cudaMemcpyDeviceToHost, st) != cudaSuccess)

@@ -6,7 +6,25 @@
 #include <cuda.h>
 #include <cuda_runtime.h>
 
+#include "szx.h"
+
 namespace szx {
+
+// How a single-field launch zeroes its scratch or status words first:
+//   kernel -- a clear kernel (launch_clear_words), with the codec kernel as
+//             its programmatic dependent: the faster for calls back to back
+//             on one stream;
+//   memset -- a cudaMemsetAsync and a plain launch: the faster when many
+//             streams run such calls at once (the serving loop's slots),
+//             where a small kernel has to wait for room on an SM.
+enum class Clear { kernel, memset };
+
+// szx_compress_async and szx_decompress_async with the clear mode chosen (the
+// public calls use Clear::kernel; the serving loop, Clear::memset).
+szx_status compress_async_with(const void *d_in, size_t n, szx_dtype dtype, double eb, uint32_t block, void *d_out,
+                               size_t out_capacity, uint64_t *d_result, szx_stream_t stream, Clear clear);
+szx_status decompress_async_with(const void *d_in, size_t in_bytes, const szx_header *h, void *d_out,
+                                 size_t out_capacity, uint32_t *d_status, szx_stream_t stream, Clear clear);
 
 // Zero n 4-byte words at p (device memory) on `stream`, with a small kernel
 // (not a memset node) so that the kernel enqueued right after it can be
@@ -55,14 +73,15 @@ bool encode_row_map(CUtensorMap *tm, const void *base, uint64_t rows, uint32_t b
 // e_bits into the stream at out; the workspace starts ws_offset bytes into
 // out.  Optionally writes {stream bytes, status} to d_result on completion.
 cudaError_t launch_compress(const void *in, uint64_t n, int dtype, uint64_t e_bits, uint32_t block,
-                            void *out, uint64_t ws_offset, uint64_t *d_result, cudaStream_t stream);
+                            void *out, uint64_t ws_offset, uint64_t *d_result, cudaStream_t stream,
+                            Clear clear = Clear::kernel);
 
 // Same, with the workspace (workspace_bytes(ntiles) bytes, 256-byte aligned)
 // at an arbitrary device address instead of the tail of out.  Clears it on
-// `stream` (launch_clear_words) and launches the kernel as the clear's
-// programmatic dependent.
+// `stream` first, as `clear` says.
 cudaError_t launch_compress_ws(const void *in, uint64_t n, int dtype, uint64_t e_bits, uint32_t block,
-                               void *out, void *ws, uint64_t *d_result, cudaStream_t stream);
+                               void *out, void *ws, uint64_t *d_result, cudaStream_t stream,
+                               Clear clear = Clear::kernel);
 
 struct CField;
 
@@ -113,12 +132,12 @@ cudaError_t launch_decompress_batch(const void *d_fields, uint32_t nfields, uint
                                     cudaStream_t stream);
 
 // Enqueue the decompression of a stream of total_bytes whose header says
-// (n, dtype, block).  *d_status is zeroed on `stream` first (launch_clear_words;
-// the kernel is then launched as the clear's programmatic dependent), and
-// errors are folded into it with atomicMax as szx_status codes (d_status may
-// be null).
+// (n, dtype, block).  *d_status is zeroed on `stream` first, as `clear` says,
+// and errors are folded into it with atomicMax as szx_status codes (d_status
+// may be null).
 cudaError_t launch_decompress(const void *in, uint64_t in_bytes, uint64_t total_bytes, uint64_t n, int dtype,
                               uint32_t block, void *out, uint32_t *d_status, bool check_header,
-                              cudaStream_t stream, uint64_t blk_lo = 0, uint64_t blk_hi = ~0ull);
+                              cudaStream_t stream, uint64_t blk_lo = 0, uint64_t blk_hi = ~0ull,
+                              Clear clear = Clear::kernel);
 
 }  // namespace szx
