@@ -191,7 +191,7 @@ size_t szx_compress_bound(size_t n, szx_dtype dtype, uint32_t block) {
 
 szx_status szx_compress_async(const void *d_in, size_t n, szx_dtype dtype, double eb, uint32_t block,
                               void *d_out, size_t out_capacity, uint64_t *d_result, szx_stream_t stream) {
-    return compress_async_with(d_in, n, dtype, eb, block, d_out, out_capacity, d_result, stream, Clear::kernel);
+    return compress_async_with(d_in, n, dtype, eb, block, d_out, out_capacity, d_result, stream, Clear::automatic);
 }
 
 szx_status szx_compress(const void *d_in, size_t n, szx_dtype dtype, double eb, uint32_t block, void *d_out,
@@ -223,7 +223,7 @@ szx_status szx_header_read(const void *d_in, size_t in_bytes, szx_header *h, szx
 
 szx_status szx_decompress_async(const void *d_in, size_t in_bytes, const szx_header *h, void *d_out,
                                 size_t out_capacity, uint32_t *d_status, szx_stream_t stream) {
-    return decompress_async_with(d_in, in_bytes, h, d_out, out_capacity, d_status, stream, Clear::kernel);
+    return decompress_async_with(d_in, in_bytes, h, d_out, out_capacity, d_status, stream, Clear::automatic);
 }
 
 szx_status szx_decompress_range_async(const void *d_in, size_t in_bytes, const szx_header *h, size_t first_block,

@@ -1346,6 +1346,7 @@ cudaError_t launch_compress_ws(const void *in, uint64_t n, int dtype, uint64_t e
     lc.copy_ns = 1000ull * wait_limit_from_env("SZX_COPY_US", 1000000u);
     // the counters and look-back flags start at zero (workspace_bytes is a
     // multiple of 8)
+    if (clear == Clear::automatic) clear = one.g.ntiles >= kClearKernelMinTiles ? Clear::kernel : Clear::memset;
     if (clear == Clear::memset) {
         const cudaError_t err = cudaMemsetAsync(ws, 0, workspace_bytes(one.g.ntiles), stream);
         if (err != cudaSuccess) return err;

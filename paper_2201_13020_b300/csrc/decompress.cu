@@ -966,6 +966,7 @@ cudaError_t launch_decompress(const void *in, uint64_t in_bytes, uint64_t total_
     lc.total_tiles = decompress_field_tiles(&one);
     // the status starts at zero; with the clear kernel, the decoder starts
     // behind it
+    if (clear == Clear::automatic) clear = lc.total_tiles >= kClearKernelMinTiles ? Clear::kernel : Clear::memset;
     if (d_status) {
         const cudaError_t err = clear == Clear::memset ? cudaMemsetAsync(d_status, 0, sizeof(uint32_t), stream)
                                                        : launch_clear_words(d_status, 1, stream);

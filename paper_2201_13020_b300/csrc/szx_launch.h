@@ -11,16 +11,21 @@
 namespace szx {
 
 // How a single-field launch zeroes its scratch or status words first:
-//   kernel -- a clear kernel (launch_clear_words), with the codec kernel as
-//             its programmatic dependent: the faster for calls back to back
-//             on one stream;
-//   memset -- a cudaMemsetAsync and a plain launch: the faster when many
-//             streams run such calls at once (the serving loop's slots),
-//             where a small kernel has to wait for room on an SM.
-enum class Clear { kernel, memset };
+//   kernel    -- a clear kernel (launch_clear_words), with the codec kernel as
+//                its programmatic dependent: the shorter on the GPU, for
+//                calls back to back on one stream;
+//   memset    -- a cudaMemsetAsync and a plain launch: about 1.7 us less host
+//                time per call, and the faster when many streams run such
+//                calls at once (the serving loop's slots), where a small
+//                kernel has to wait for room on an SM;
+//   automatic -- kernel for launches of at least kClearKernelMinTiles tiles,
+//                memset below, where a call back to back with others is
+//                bound by the host's launch time rather than the GPU.
+enum class Clear { kernel, memset, automatic };
+constexpr uint64_t kClearKernelMinTiles = 256;
 
 // szx_compress_async and szx_decompress_async with the clear mode chosen (the
-// public calls use Clear::kernel; the serving loop, Clear::memset).
+// public calls use Clear::automatic; the serving loop, Clear::memset).
 szx_status compress_async_with(const void *d_in, size_t n, szx_dtype dtype, double eb, uint32_t block, void *d_out,
                                size_t out_capacity, uint64_t *d_result, szx_stream_t stream, Clear clear);
 szx_status decompress_async_with(const void *d_in, size_t in_bytes, const szx_header *h, void *d_out,
@@ -74,14 +79,14 @@ bool encode_row_map(CUtensorMap *tm, const void *base, uint64_t rows, uint32_t b
 // out.  Optionally writes {stream bytes, status} to d_result on completion.
 cudaError_t launch_compress(const void *in, uint64_t n, int dtype, uint64_t e_bits, uint32_t block,
                             void *out, uint64_t ws_offset, uint64_t *d_result, cudaStream_t stream,
-                            Clear clear = Clear::kernel);
+                            Clear clear = Clear::automatic);
 
 // Same, with the workspace (workspace_bytes(ntiles) bytes, 256-byte aligned)
 // at an arbitrary device address instead of the tail of out.  Clears it on
 // `stream` first, as `clear` says.
 cudaError_t launch_compress_ws(const void *in, uint64_t n, int dtype, uint64_t e_bits, uint32_t block,
                                void *out, void *ws, uint64_t *d_result, cudaStream_t stream,
-                               Clear clear = Clear::kernel);
+                               Clear clear = Clear::automatic);
 
 struct CField;
 
@@ -138,6 +143,6 @@ cudaError_t launch_decompress_batch(const void *d_fields, uint32_t nfields, uint
 cudaError_t launch_decompress(const void *in, uint64_t in_bytes, uint64_t total_bytes, uint64_t n, int dtype,
                               uint32_t block, void *out, uint32_t *d_status, bool check_header,
                               cudaStream_t stream, uint64_t blk_lo = 0, uint64_t blk_hi = ~0ull,
-                              Clear clear = Clear::kernel);
+                              Clear clear = Clear::automatic);
 
 }  // namespace szx

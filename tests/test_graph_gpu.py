@@ -1,11 +1,12 @@
 """Single-field calls on one stream, back to back and inside a CUDA graph.
 
-Each call clears its scratch or status words with a small kernel and launches
-the codec kernel as that kernel's programmatic dependent, which waits for
-every earlier kernel on the stream before touching memory.  These tests put
-other kernels right before and after the calls, with no synchronisation in
-between, and capture the calls in a graph; every stream must stay byte-identical
-to the oracle's and every decode bit-identical."""
+A call of at least 256 tiles clears its scratch or status words with a small
+kernel and launches the codec kernel as that kernel's programmatic dependent,
+which waits for every earlier kernel on the stream before touching memory; a
+smaller one clears with a memset and launches plainly.  These tests put other
+kernels right before and after the calls, with no synchronisation in between,
+and capture the calls in a graph, on both sides of that size; every stream
+must stay byte-identical to the oracle's and every decode bit-identical."""
 import numpy as np
 import pytest
 
@@ -23,10 +24,11 @@ def _case(dtype, n, seed):
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("dtype,block", [(np.float32, 128), (np.float64, 256), (np.float32, 32)])
-def test_back_to_back_calls_see_the_kernels_before_them(dtype, block):
-    # 3 tiles and a ragged tail at every block length here
-    n = 3 * max(8, 32768 // (block * np.dtype(dtype).itemsize)) * block + 77
+@pytest.mark.parametrize("dtype,block,tiles", [(np.float32, 128, 3), (np.float64, 256, 3), (np.float32, 32, 3),
+                                               (np.float32, 128, 300), (np.float64, 128, 260)])
+def test_back_to_back_calls_see_the_kernels_before_them(dtype, block, tiles):
+    # whole tiles and a ragged tail at every block length here
+    n = tiles * max(8, 32768 // (block * np.dtype(dtype).itemsize)) * block + 77
     x, eb = _case(dtype, n, 5)
     ref = oracle.compress(x, eb, block)
     xd = torch.from_numpy(x).cuda()
@@ -56,9 +58,10 @@ def test_back_to_back_calls_see_the_kernels_before_them(dtype, block):
 
 
 @pytest.mark.gpu
-def test_single_calls_replay_in_a_cuda_graph():
+@pytest.mark.parametrize("tiles", [5, 300])
+def test_single_calls_replay_in_a_cuda_graph(tiles):
     block = 128
-    n = 5 * 64 * block + 301
+    n = tiles * 64 * block + 301
     x, eb = _case(np.float32, n, 9)
     ref = oracle.compress(x, eb, block)
     dref = oracle.decompress(ref)
