@@ -13,7 +13,8 @@
 // Running a plan is one clear kernel (counters, workspaces and, for
 // decompression, every stream's status word) plus one kernel launch per group,
 // each the programmatic dependent of the kernel before it, so it can be
-// captured in a CUDA graph once the tables are uploaded.  The autotuner times each group alone on the plan's own
+// captured in a CUDA graph once the tables are uploaded.  The autotuner times
+// each group alone on the plan's own
 // data in every shape the kernels have -- consumer warps per CTA (8, or 4 with
 // twice the values per lane and blocks per warp) times CTAs per SM (2 or 1) --
 // and keeps the fastest; the stream is the same in every shape.  For a group

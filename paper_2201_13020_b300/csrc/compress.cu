@@ -933,7 +933,8 @@ __global__ void __launch_bounds__(compress_threads(NW),
                 for (int rr = 0; rr < RPL; ++rr) {
                     const uint32_t rowi = lane_row0 + rr;
 #pragma unroll
-                    for (int c = 0; c < 8; ++c) *reinterpret_cast<uint4 *>(buf + (rowi << 7) + ((c ^ (rowi & 7u)) << 4)) = z;
+                    for (int c = 0; c < 8; ++c)
+                        *reinterpret_cast<uint4 *>(buf + (rowi << 7) + ((c ^ (rowi & 7u)) << 4)) = z;
                 }
                 if (warp == kConsumerWarps - 1)
                     for (uint32_t i = TILE_ROWS * 128u + 16u * lane; i < L.buf_bytes; i += 16u * 32u)
@@ -1011,7 +1012,8 @@ __global__ void __launch_bounds__(compress_threads(NW),
             const uint32_t raw_bal = __ballot_sync(kFull, lead && kind == kRaw);
             const uint32_t esc_bal = __ballot_sync(kFull, lead && kind == kNonConst && req > req0);
             // per warp: (non-constant blocks << 20 | mid bytes), raw blocks, escalated blocks
-            if (lane == 0) sm_w[warp] = make_uint4((uint32_t)__popc(nonc_bal) << 20 | mid_w, __popc(raw_bal), __popc(esc_bal), 0);
+            if (lane == 0)
+                sm_w[warp] = make_uint4((uint32_t)__popc(nonc_bal) << 20 | mid_w, __popc(raw_bal), __popc(esc_bal), 0);
             __syncwarp();
             if (lane == 0) mbar_arrive(&encoded[st]);
 
@@ -1203,7 +1205,8 @@ __global__ void __launch_bounds__(compress_threads(NW),
 #pragma unroll
                             for (int j = 3; j < W / 8; ++j) {
                                 if (j < q)
-                                    put(8 * (dense0 + (uint32_t)(j - 3) * len + 4 * gq), prmt(Wd[j], 0, sel), sel >> 16);
+                                    put(8 * (dense0 + (uint32_t)(j - 3) * len + 4 * gq), prmt(Wd[j], 0, sel),
+                                        sel >> 16);
                             }
                         }
                     }
