@@ -660,14 +660,18 @@ __global__ void __launch_bounds__(compress_threads(NW),
             const uint64_t row0 = (uint64_t)tile * TILE_ROWS;
             if (more && F->use_tma && row0 < F->rows_full) {
                 mbar_arrive_expect_tx(&full[st], TILE_ROWS * 128u);
+                // the input is read once: its lines go first when L2 needs room,
+                // before other kernels' lines still waiting to be written back
+                uint64_t pol;
+                asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
 #pragma unroll
                 for (int i = 0; i < (int)TILE_BOXES; ++i) {
                     const uint32_t dst = smem_addr(smem + st * L.buf_stride + i * 32768);
                     const int y = (int)(row0 + 256 * i);
                     asm volatile(
-                        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, "
-                        "{%2, %3}], [%4];" ::"r"(dst),
-                        "l"(reinterpret_cast<uint64_t>(&F->tmap)), "r"(0), "r"(y), "r"(smem_addr(&full[st]))
+                        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint "
+                        "[%0], [%1, {%2, %3}], [%4], %5;" ::"r"(dst),
+                        "l"(reinterpret_cast<uint64_t>(&F->tmap)), "r"(0), "r"(y), "r"(smem_addr(&full[st])), "l"(pol)
                         : "memory");
                 }
                 copy_last |= 1u << st;
