@@ -62,9 +62,12 @@ def test_static_scratch_matches_existing_entry_point_twice_in_a_row():
     dev = torch.device("cuda:0")
     s = torch.cuda.current_stream()
     h = _vp(s.cuda_stream)
-    # Two calls in a row, the second smaller and of the other dtype, so that
-    # its tiles reuse look-back words the first call left behind.
+    # Calls in a row, each smaller than the one before, so that their tiles
+    # reuse look-back words the earlier calls left behind.  The first (500
+    # tiles) clears the words with a kernel, the others (108 and 30 tiles)
+    # with a memset.
     cases = [
+        (inputs.grf_3d((160, 160, 160), -5.0 / 3.0, 10, dtype=torch.float32), 1e-3, 128),
         (inputs.grf_3d((96, 96, 96), -5.0 / 3.0, 11, dtype=torch.float32), 1e-3, 128),
         (inputs.grf_3d((40, 50, 61), -11.0 / 3.0, 12, dtype=torch.float64), 1e-4, 256),
     ]
