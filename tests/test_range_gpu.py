@@ -45,3 +45,25 @@ def test_invalid_ranges_are_rejected():
     for first, count in [(0, 0), (nb, 1), (nb - 1, 2)]:
         with pytest.raises(szx.SzxError):
             szx.decompress_range(buf, first, count, h=h)
+
+
+@pytest.mark.gpu
+def test_long_range_with_status_matches_full_decode():
+    # a range of at least 256 tiles with a status word: the status is cleared
+    # by a kernel and the decoder launched as its programmatic dependent
+    block = 128
+    n = 300 * 64 * block + 333
+    x = np.cumsum(np.random.default_rng(4).normal(size=n)).astype(np.float32)
+    eb = inputs.rel_to_abs(x, 1e-3)
+    s = oracle.compress(x, eb, block)
+    full = oracle.decompress(s)
+    buf = torch.from_numpy(s).cuda()
+    h = szx.header(buf)
+    nb = -(-n // block)
+    first, count = 70, nb - 70 - 5
+    st = torch.full((1,), 99, dtype=torch.int32, device="cuda")
+    got = szx.decompress_range(buf, first, count, h=h, status=st)
+    torch.cuda.synchronize()
+    assert int(st.item()) == 0
+    lo, hi = first * block, min(n, (first + count) * block)
+    assert np.array_equal(got.cpu().numpy().view(np.uint32), full[lo:hi].view(np.uint32))
